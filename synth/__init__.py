@@ -1,0 +1,6 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This package draws random numbers and nothing else of the propagation method:
+no Fock matrix, residual, integrator or cumulant arithmetic lives here.
+"""
+from .generators import Problem, gen_problem, WORKLOADS, workload  # noqa: F401

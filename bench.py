@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the RT-EOM-CCSD core-hole propagation on B300.
+
+One bench step = one time step of the propagation (Eq. 9): the residual
+R(t_n), the fixed-point micro-iterations of the Adams-Moulton update, the
+cumulant integrand and C_{n+1} (Eqs. 5-6).  Metric: time steps/s, whole job
+(sum over ranks; ranks are independent replicas).  Default workload: the
+formaldehyde-shaped FP64 problem O=8, V=100, Nchol=400, dt=0.025 au, with
+the paper's micro-iteration cutoff 1e-4.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from synth import workload  # noqa: E402
+
+METRIC = "time_steps_per_s"
+UNIT = "steps/s"
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (profiling recipe table); no tensor-core FP64 path
+MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
+LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2_formaldehyde")
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--max-micro", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_micro_per_step(name, tol):
+    """Micro-iterations per step of the oracle's own run of this workload at
+    this tolerance (stored by tests/golden/make_oracle_golden.py), or None."""
+    tag = "" if tol == 1e-12 else f"_tol{tol:g}"
+    path = os.path.join(HERE, "tests", "golden", f"oracle_{name}{tag}.txt")
+    if not os.path.exists(path):
+        return None
+    d = np.loadtxt(path)
+    return float(d[1:, 5].mean())
+
+
+def time_oracle_micro_iteration(p, dt, reps, warm, t_state=None):
+    """Wall time of one oracle micro-iteration (residual + Eq. 9 update) on
+    the host cores; returns (mean seconds, threads used)."""
+    from oracle import propagate as PR
+    from oracle.spinexp import CoreHoleCCSD
+    sysb = CoreHoleCCSD.from_problem(p.eps, p.L, p.nocc, p.core)
+    D = sysb.diagonal()
+    t = t_state if t_state is not None else [x + 1e-3 for x in sysb.zeros()]
+    Rn = [r - d * x for r, d, x in zip(sysb.residual(t), D, t)]
+    times = []
+    for k in range(warm + reps):
+        t0 = time.perf_counter()
+        try:
+            PR.am_step(sysb.residual, D, t, Rn, dt, tol=0.0, max_micro=2)
+        except PR.NotConverged:
+            pass
+        if k >= warm:
+            times.append(time.perf_counter() - t0)
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count()
+    # am_step with tol 0 and max_micro=2 evaluates exactly one residual (k=1)
+    # plus two updates, then reports non-convergence
+    return float(np.mean(times)), int(threads)
+
+
+# ----------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED))
+    except Exception:
+        return {}
+
+
+def ladder_traffic_per_launch():
+    """Per-launch DRAM bytes of the ladder GEMM from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    if not os.path.exists(LADDER_PROFILE):
+        return None
+    src = os.path.join(HERE, "paper_2301_04249_b300", "csrc", "gemm_f64.cu")
+    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    vals = {}
+    for ln in open(LADDER_PROFILE):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != digest:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def fp64_dgemm_tflops(torch, dev):
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2 * 4096 ** 3 / best / 1e12
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_2301_04249_b300 as P
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p, run = workload(args.workload)
+    dt = run["dt"]
+    stream = torch.cuda.Stream(device=dev)
+    g = P.Propagator.from_problem(p, stream=stream)
+    g.propagate(args.warmup, dt, tol=args.tol, max_micro=args.max_micro)
+    info0 = g.info()
+    g.set_timing(True)
+    g.timing(reset=True)
+    launches0 = g.kernel_launches()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.propagate(args.steps, dt, tol=args.tol, max_micro=args.max_micro)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    info1 = g.info()
+    tm = g.timing()
+    launches = g.kernel_launches() - launches0
+    micro = info1["micro"] - info0["micro"]
+    state = g.get_state(with_history=False)["t"]
+    g.close()
+
+    # end to end through the public API from pinned host buffers
+    def pinned(a):
+        if a is None:
+            return None
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+    h_eps, h_L, h_t1, h_t2 = pinned(p.eps), pinned(p.L), pinned(p.t1_gs), pinned(p.t2_gs)
+    omega = pinned(np.linspace(-25.0, -15.0, 2001))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    g2 = P.Propagator(h_eps, h_L, p.nocc, p.nvir, h_t1, h_t2, core=p.core, stream=stream)
+    Cs = [g2.propagate(1, dt, tol=args.tol, max_micro=args.max_micro)[-1] for _ in range(args.steps)]
+    A = g2.spectrum(omega, 0.05)
+    g2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    h2d = sum(x.nbytes for x in (h_eps, h_L, h_t1, h_t2, omega) if x is not None)
+    d2h = 16 * 2 * args.steps + A.nbytes
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    value = world * args.steps / elapsed
+    lad = tm["ladder"]
+    peaks = measured_peaks()
+    dgemm = fp64_dgemm_tflops(torch, dev)
+    lad_avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
+    lad_flops = lad["flops"] / max(lad["launches"], 1)
+    achieved = lad_flops / lad_avg_s / 1e12 if lad["launches"] else None
+    traffic = ladder_traffic_per_launch()
+    total_flops = sum(v["flops"] for v in tm.values())
+    roofline = {"bound": "alu", "kernel": "gemm_f64 (particle-particle ladder, FP64 DFMA)",
+                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
+                "peak_source": "B300 nominal FP64 (recipe table); cuBLAS DGEMM measured live below",
+                "cublas_dgemm_tflops_measured": dgemm,
+                "frac_of_cublas_dgemm": achieved / dgemm if achieved else None,
+                "flops_per_launch": lad_flops, "avg_launch_ms": lad_avg_s * 1e3,
+                "launches": lad["launches"], "traffic": traffic}
+
+    cpu = None
+    m_ref = oracle_micro_per_step(args.workload, args.tol)
+    if not args.no_cpu_baseline:
+        blocks = P.split_blocks(state, p.nocc, p.nvir)
+        t_mi, threads = time_oracle_micro_iteration(p, dt, reps=1, warm=0, t_state=blocks)
+        m_use = m_ref if m_ref is not None else micro / args.steps
+        cpu = {"value": 1.0 / (t_mi * m_use), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"one oracle micro-iteration (residual + Eq. 9 update) of workload "
+                          f"{args.workload} timed on the host ({t_mi:.2f} s), scaled by "
+                          f"{m_use:.2f} micro-iterations per step "
+                          + ("(the oracle's own run at this tol)" if m_ref is not None
+                             else "(measured on the GPU run)")),
+               "micro_iteration_s": t_mi}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; no molecular integrals available)",
+        "config": {"workload": f"{args.workload}: O={p.nocc} V={p.nvir} Nchol={p.nchol} "
+                               f"dt={dt} tol={args.tol} precision=FP64 complex",
+                   "parallelism": f"replicas x{world} (independent core holes, no collectives)",
+                   "l2": "inputs larger than L2: the (ae|bf) ladder block alone is "
+                         f"{8 * (p.nvir + 1) ** 4 / 1e9:.2f} GB",
+                   "flops_per_step_tflop": total_flops / args.steps / 1e12},
+        "micro_iterations_per_step": micro / args.steps,
+        "micro_iterations_per_s": world * micro / elapsed,
+        "tflops_fp64": total_flops / elapsed / 1e12,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "rteom_create from pinned host arrays + per-step rteom_propagate(1) "
+                        "returning C_n + rteom_spectrum + destroy, wall clock"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+    }
+    print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    p, run = workload(args.workload)
+    m_ref = oracle_micro_per_step(args.workload, args.tol)
+    t_mi, threads = time_oracle_micro_iteration(p, run["dt"], reps=args.steps, warm=args.warmup)
+    m_use = m_ref if m_ref is not None else float("nan")
+    value = 1.0 / (t_mi * m_use)
+    sample = (f"each step: one oracle micro-iteration (residual + Eq. 9 update) of workload "
+              f"{args.workload} on the host cores ({t_mi:.2f} s mean over {args.steps}), scaled "
+              f"by the oracle's {m_use:.2f} micro-iterations per step at tol {args.tol:g}")
+    res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mi * m_use,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": f"{args.workload}: O={p.nocc} V={p.nvir} "
+                                                      f"Nchol={p.nchol} dt={run['dt']} tol={args.tol}"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

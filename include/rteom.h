@@ -1,0 +1,200 @@
+/*
+ * rteom.h -- C ABI of the B300 RT-EOM-CCSD core-hole propagation library
+ * (librteom.so).
+ *
+ * The library propagates the coupled-cluster singles and doubles amplitudes
+ * of one core-ionised (N-1)-electron reference in real time and accumulates
+ * the cumulant C(t) of the core-hole Green's function (Pathak et al.,
+ * "Real-time Equation-of-Motion Coupled-Cluster Cumulant Green's Function
+ * Method", Section 2.1 Eqs. 1-8 and Section 3 Eq. 9).  All arithmetic runs in
+ * the library's CUDA kernels on one GPU; the host only copies inputs in and
+ * results out.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - nocc (O) occupied and nvir (V) virtual spatial orbitals of the
+ *    N-electron closed-shell system, nb = O + V; O counts the core orbital.
+ *  - The ionised electron is the beta copy of spatial orbital core_index
+ *    (0 <= core_index < O).  Spin spaces of the (N-1) reference:
+ *      alpha occupied = spatial 0..O-1                         (oA = O)
+ *      beta  occupied = spatial 0..O-1 without core_index       (oB = O-1)
+ *      alpha virtual  = spatial O..nb-1                        (vA = V)
+ *      beta  virtual  = [core_index, O..nb-1] (core first)     (vB = V+1)
+ *  - "Amplitude vector": the unique spin blocks of Section 3.1.1, complex128
+ *    stored as interleaved (re, im) doubles, concatenated in this order and
+ *    each row-major:
+ *      t1a[oA][vA], t1b[oB][vB], t2aa[oA][oA][vA][vA], t2ab[oA][oB][vA][vB],
+ *      t2bb[oB][oB][vB][vB];
+ *    t2aa and t2bb are antisymmetric in (i,j) and in (a,b).  Its length in
+ *    doubles is rteom_state_size().
+ *  - Every function returns RTEOM_OK (0) or a negative RTEOM_ERR_* code and
+ *    never aborts the process; rteom_last_error() gives a message.  After
+ *    RTEOM_ERR_CUDA the context must be destroyed.
+ *  - A context is not thread-safe; distinct contexts are independent.  All
+ *    device work of a context runs on the stream given at creation.
+ *  - Host pointers are read or written only during the call; the caller
+ *    keeps ownership of every buffer it passes.
+ */
+#ifndef RTEOM_H
+#define RTEOM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTEOM_OK                 0
+#define RTEOM_ERR_ARG           -1   /* bad size, index, pointer or value          */
+#define RTEOM_ERR_OOM           -2   /* device memory exhausted                     */
+#define RTEOM_ERR_CUDA          -3   /* CUDA runtime error (context unusable)       */
+#define RTEOM_ERR_NOT_CONVERGED -4   /* micro-iteration cap reached (Eq. 9)         */
+#define RTEOM_ERR_NONFINITE     -5   /* NaN/Inf in an input or in the amplitudes    */
+#define RTEOM_ERR_STATE         -6   /* call not valid in the context's state       */
+
+/* precision forms */
+#define RTEOM_FP64        0   /* every contraction and update in FP64           */
+#define RTEOM_SPLIT_BF16  1   /* reserved: split-BF16 contractions, FP64 update */
+#define RTEOM_SPLIT_TF32  2   /* reserved: split-TF32 contractions, FP64 update */
+
+/* flags for rteom_create */
+#define RTEOM_FLAG_CUMULANT_NO_FOV 1  /* cumulant integrand without sum f_ia t_i^a,
+                                         i.e. Eq. 6 as printed; default keeps it
+                                         (the definition in Eq. 5)              */
+
+typedef struct rteom_ctx rteom_ctx;
+
+/*
+ * rteom_create -- set up one core-hole propagation (Section 3, workflow
+ * steps "read the N-electron orbitals into the (N-1) space and build the
+ * (N-1) Fock matrix"; f_pq = eps_p delta_pq - <pc||qc>, Section 2.1).
+ *
+ *  out        receives the new context (set to NULL on failure)
+ *  nocc,nvir  O >= 1, V >= 1;  nchol >= 0 Cholesky vectors
+ *  eps        host [nb] N-electron Hartree-Fock orbital energies (Ha)
+ *  L          host [nchol][nb][nb] real Cholesky vectors of the two-electron
+ *             integrals, (pq|rs) = sum_Q L[Q][p][q] L[Q][r][s]; must satisfy
+ *             L[Q][p][q] == L[Q][q][p]; may be NULL when nchol == 0
+ *  t1_gs      host [O][V] closed-shell ground-state T1, or NULL (zero)
+ *  t2_gs      host [O][O][V][V] closed-shell (alpha-beta) ground-state T2, or
+ *             NULL; t1_gs/t2_gs only enter E_N^corr of Eq. 3:
+ *             E = sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
+ *  core_index spatial index c of the ionised orbital, 0 <= c < O
+ *  precision  RTEOM_FP64 (the split forms return RTEOM_ERR_ARG until built)
+ *  flags      RTEOM_FLAG_* bits
+ *  cuda_stream cudaStream_t to run on, or NULL for a non-blocking stream
+ *             created and owned by the context
+ *
+ * The inputs are copied to device memory owned by the context (cudaMalloc);
+ * the amplitudes start at T(0) = 0 and C(0) = 0 (Section 3).  Errors:
+ * RTEOM_ERR_ARG (sizes, indices, NULL eps), RTEOM_ERR_NONFINITE (NaN/Inf in
+ * an input), RTEOM_ERR_OOM, RTEOM_ERR_CUDA.
+ */
+int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol,
+                 const double* eps, const double* L,
+                 const double* t1_gs, const double* t2_gs,
+                 int core_index, int precision, int flags, void* cuda_stream);
+
+/*
+ * rteom_propagate -- advance the amplitudes nsteps time steps of length dt
+ * with the first-order Adams-Moulton rule (Eq. 9), each solved by fixed-point
+ * micro-iterations from the predictor t^(0) = t_n, stopping when the largest
+ * |t^(k+1) - t^(k)| over all blocks is below tol, and accumulate the cumulant
+ * C_{n+1} = C_n + (i dt/2)(E_n + E_{n+1}) with E = <Phi|(H_N e^T)_C|Phi>
+ * (Eqs. 5-6).
+ *
+ *  nsteps     >= 0;  dt > 0 (au) and equal in every call of a context (the
+ *             first propagate call fixes it; a state restored with
+ *             rteom_set_state carries no dt, so the caller keeps it equal)
+ *  tol        > 0 micro-iteration cutoff (the paper uses 1e-4)
+ *  max_micro  >= 1 cap on micro-iterations per step
+ *  C_out      host [nsteps+1] complex (2*(nsteps+1) doubles) or NULL:
+ *             C at the start of this call and after each of its steps.
+ *
+ * Returns RTEOM_ERR_NOT_CONVERGED if a step hits max_micro (the context keeps
+ * the last completed step), RTEOM_ERR_NONFINITE if the amplitudes become
+ * non-finite, RTEOM_ERR_ARG for bad arguments.
+ */
+int rteom_propagate(rteom_ctx* ctx, int nsteps, double dt, double tol, int max_micro,
+                    double* C_out);
+
+/*
+ * rteom_spectrum -- core spectral function A(w) = -(1/pi) Im G^R(w)
+ * (Section 2.1) of everything propagated so far: with
+ * G_n = -i exp(-i (eps_c + E_corr) tau_n) exp(C_n) (Eq. 4), tau_n = n dt,
+ *   A(w_m) = -(1/pi) Im sum_{n=0}^{M} w_n dt G_n exp(i w_m tau_n - eta tau_n),
+ * trapezoid weights w_0 = w_M = 1/2, others 1.
+ *
+ *  omega  host [nomega] frequencies (Ha);  eta >= 0 damping (Ha)
+ *  A_out  host [nomega]
+ * Errors: RTEOM_ERR_STATE if no step has been propagated, RTEOM_ERR_ARG.
+ */
+int rteom_spectrum(rteom_ctx* ctx, const double* omega, int nomega, double eta,
+                   double* A_out);
+
+/*
+ * rteom_get_info -- scalars of the propagation.  Any output pointer may be
+ * NULL.  eps_core = eps[core_index]; e_corr = E_N^corr (Eq. 3);
+ * steps_done and micro_total count the steps and micro-iterations so far.
+ */
+int rteom_get_info(const rteom_ctx* ctx, double* eps_core, double* e_corr,
+                   long long* steps_done, long long* micro_total);
+
+/* rteom_state_size -- length in doubles of the amplitude vector (see top). */
+long long rteom_state_size(const rteom_ctx* ctx);
+
+/*
+ * rteom_get_cumulant -- copy C_0..C_{count-1} (count <= steps_done + 1) and
+ * the matching cumulant integrands E_n into host arrays of 2*count doubles
+ * each (interleaved complex); either pointer may be NULL.
+ */
+int rteom_get_cumulant(const rteom_ctx* ctx, long long count, double* C_out, double* E_out);
+
+/*
+ * rteom_get_state / rteom_set_state -- checkpoint and restart (Section 3.1.1,
+ * "Restarting the time propagation ... requires the T amplitudes").  The
+ * state is the amplitude vector t_n plus the step count; the cumulant
+ * history (C_0..C_n, E_0..E_n) travels with it so the spectrum stays
+ * complete.  t_out/t_in: host amplitude vector (rteom_state_size doubles).
+ * hist: host [2*(steps+1)] C followed by [2*(steps+1)] E, or NULL to skip
+ * (get) / to restart the history at this state with C = 0 (set).
+ * set_state also lets tests start from a chosen T(0).  Padding-free; the
+ * entries of t2aa/t2bb must be antisymmetric (not checked beyond finiteness).
+ */
+int rteom_get_state(const rteom_ctx* ctx, double* t_out, long long* steps, double* hist);
+int rteom_set_state(rteom_ctx* ctx, const double* t_in, long long steps, const double* hist);
+
+/*
+ * rteom_debug_residual -- test entry point: evaluate the full projections
+ * R_mu = <Phi_mu|(H_N e^{T1+T2})_C|Phi> (Eqs. 7-8) and the cumulant
+ * integrand E (Eq. 5) for given amplitudes, without changing the state.
+ * t_in, R_out: host amplitude vectors; E_out: host [2] (may be NULL).
+ */
+int rteom_debug_residual(rteom_ctx* ctx, const double* t_in, double* R_out, double* E_out);
+
+/*
+ * rteom_set_timing / rteom_get_timing -- per-kernel-class device timing with
+ * CUDA events on the context's stream (0 = off, the default).  Classes:
+ * 0 ladder contraction, 1 other contractions, 2 tensor permutes,
+ * 3 elementwise/update/energy.  get_timing fills ms[4] (total milliseconds),
+ * launches[4] and flops[4] (algorithmic FLOPs of the timed launches); any
+ * pointer may be NULL.  reset != 0 zeroes the counters after reading.
+ */
+int rteom_set_timing(rteom_ctx* ctx, int on);
+int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* flops, int reset);
+
+/* rteom_kernel_launches -- number of kernels this context has launched. */
+long long rteom_kernel_launches(const rteom_ctx* ctx);
+
+/* rteom_destroy -- free every device and host resource of the context. */
+void rteom_destroy(rteom_ctx* ctx);
+
+/*
+ * rteom_last_error -- message of the last failed call on ctx, or of the last
+ * failed rteom_create on this thread when ctx is NULL.  Valid until the next
+ * call on the same context/thread.
+ */
+const char* rteom_last_error(const rteom_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTEOM_H */

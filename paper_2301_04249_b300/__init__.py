@@ -1,0 +1,176 @@
+"""B300-native RT-EOM-CCSD core-hole propagation (Python binding of librteom.so).
+
+The Python layer only marshals arguments: every step of the propagation runs
+in the library's CUDA kernels.  There is no CPU fallback; a missing library or
+GPU raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: F401
+                   RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_OOM, RTEOM_ERR_STATE, RTEOM_FLAG_CUMULANT_NO_FOV,
+                   RTEOM_FP64, RTEOM_OK, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32)
+
+__all__ = ["Propagator", "RteomError", "block_shapes", "split_blocks", "join_blocks"]
+
+
+class RteomError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rteom error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def block_shapes(nocc: int, nvir: int, core: int = 0):
+    """Shapes of the unique spin blocks t1a, t1b, t2aa, t2ab, t2bb."""
+    oA, vA, oB, vB = nocc, nvir, nocc - 1, nvir + 1
+    return [(oA, vA), (oB, vB), (oA, oA, vA, vA), (oA, oB, vA, vB), (oB, oB, vB, vB)]
+
+
+def split_blocks(vec: np.ndarray, nocc: int, nvir: int):
+    """Interleaved complex amplitude vector -> list of complex block arrays."""
+    z = vec.view(np.complex128)
+    out, k = [], 0
+    for s in block_shapes(nocc, nvir):
+        n = int(np.prod(s))
+        out.append(z[k:k + n].reshape(s).copy())
+        k += n
+    return out
+
+
+def join_blocks(blocks) -> np.ndarray:
+    """List of complex block arrays -> interleaved complex amplitude vector."""
+    z = np.concatenate([np.ascontiguousarray(b, dtype=np.complex128).ravel() for b in blocks])
+    return z.view(np.float64).copy()
+
+
+class Propagator:
+    """One core-hole propagation context (rteom_create ... rteom_destroy).
+
+    eps [nb], L [nchol, nb, nb] (symmetric in the last two indices), optional
+    closed-shell ground-state t1 [O, V] / t2 [O, O, V, V] for E_N^corr.
+    ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None for a
+    stream owned by the library.
+    """
+
+    def __init__(self, eps, L, nocc: int, nvir: int, t1_gs=None, t2_gs=None, core: int = 0,
+                 precision: int = RTEOM_FP64, flags: int = 0, stream=None):
+        self._lib = _lib.load()
+        self.nocc, self.nvir, self.core = int(nocc), int(nvir), int(core)
+        eps = _f64(eps)
+        L = _f64(L)
+        nchol = 0 if L is None else int(L.shape[0])
+        t1 = _f64(t1_gs)
+        t2 = _f64(t2_gs)
+        handle = None
+        if stream is not None:
+            handle = int(getattr(stream, "cuda_stream", stream)) or None
+        ctx = ctypes.c_void_p()
+        rc = self._lib.rteom_create(ctypes.byref(ctx), self.nocc, self.nvir, nchol, _ptr(eps),
+                                    _ptr(L), _ptr(t1), _ptr(t2), self.core, int(precision),
+                                    int(flags), handle)
+        if rc != 0:
+            raise RteomError(rc, self._lib.rteom_last_error(None).decode())
+        self._ctx = ctx
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        return cls(p.eps, p.L, p.nocc, p.nvir, p.t1_gs, p.t2_gs, core=p.core, **kw)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RteomError(rc, self._lib.rteom_last_error(self._ctx).decode())
+
+    def propagate(self, nsteps: int, dt: float, tol: float = 1e-4, max_micro: int = 50):
+        """Advance nsteps; returns C at the start and after each step (complex [nsteps+1])."""
+        out = np.zeros(2 * (nsteps + 1))
+        self._check(self._lib.rteom_propagate(self._ctx, int(nsteps), float(dt), float(tol),
+                                              int(max_micro), _ptr(out)))
+        return out.view(np.complex128)
+
+    def spectrum(self, omega, eta: float):
+        w = _f64(np.atleast_1d(omega))
+        A = np.zeros(w.size)
+        self._check(self._lib.rteom_spectrum(self._ctx, _ptr(w), int(w.size), float(eta), _ptr(A)))
+        return A
+
+    def info(self):
+        e, ec = ctypes.c_double(), ctypes.c_double()
+        s, m = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self._lib.rteom_get_info(self._ctx, ctypes.byref(e), ctypes.byref(ec),
+                                             ctypes.byref(s), ctypes.byref(m)))
+        return dict(eps_core=e.value, e_corr=ec.value, steps=s.value, micro=m.value)
+
+    def state_size(self) -> int:
+        return int(self._lib.rteom_state_size(self._ctx))
+
+    def cumulant(self):
+        """(C, E) histories, complex [steps+1] each."""
+        n = self.info()["steps"] + 1
+        C, E = np.zeros(2 * n), np.zeros(2 * n)
+        self._check(self._lib.rteom_get_cumulant(self._ctx, n, _ptr(C), _ptr(E)))
+        return C.view(np.complex128), E.view(np.complex128)
+
+    def get_state(self, with_history: bool = True):
+        t = np.zeros(self.state_size())
+        steps = ctypes.c_longlong()
+        self._check(self._lib.rteom_get_state(self._ctx, _ptr(t), ctypes.byref(steps), None))
+        hist = None
+        if with_history:
+            hist = np.zeros(4 * (steps.value + 1))
+            self._check(self._lib.rteom_get_state(self._ctx, None, ctypes.byref(steps), _ptr(hist)))
+        return dict(t=t, steps=steps.value, hist=hist)
+
+    def set_state(self, t, steps: int = 0, hist=None):
+        t = _f64(t)
+        self._check(self._lib.rteom_set_state(self._ctx, _ptr(t), int(steps), _ptr(_f64(hist))))
+
+    def residual(self, blocks):
+        """Full projections R (list of blocks) and E for the given amplitude blocks."""
+        t = join_blocks(blocks)
+        R = np.zeros_like(t)
+        E = np.zeros(2)
+        self._check(self._lib.rteom_debug_residual(self._ctx, _ptr(t), _ptr(R), _ptr(E)))
+        return split_blocks(R, self.nocc, self.nvir), complex(E[0], E[1])
+
+    def set_timing(self, on: bool):
+        self._check(self._lib.rteom_set_timing(self._ctx, int(bool(on))))
+
+    def timing(self, reset: bool = False):
+        ms = (ctypes.c_double * 4)()
+        la = (ctypes.c_longlong * 4)()
+        fl = (ctypes.c_double * 4)()
+        self._check(self._lib.rteom_get_timing(self._ctx, ms, la, fl, int(reset)))
+        names = ["ladder", "contract", "permute", "elementwise"]
+        return {n: dict(ms=ms[k], launches=la[k], flops=fl[k]) for k, n in enumerate(names)}
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.rteom_kernel_launches(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.rteom_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,269 @@
+// Contraction engine implementation (see engine.h).
+#include <nvtx3/nvToolsExt.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "engine.h"
+
+namespace rteom {
+
+namespace {
+
+struct Parsed {
+  std::string a, b, c;
+};
+
+Parsed parse(const char* spec) {
+  Parsed p;
+  const char* arrow = std::strstr(spec, "->");
+  if (!arrow) throw Error(-1, std::string("contract: no '->' in spec ") + spec);
+  std::string lhs(spec, arrow - spec);
+  p.c = std::string(arrow + 2);
+  auto comma = lhs.find(',');
+  if (comma == std::string::npos) {
+    p.a = lhs;
+  } else {
+    p.a = lhs.substr(0, comma);
+    p.b = lhs.substr(comma + 1);
+  }
+  return p;
+}
+
+int64_t prod(const std::string& labels, const int64_t* dimof) {
+  int64_t n = 1;
+  for (char ch : labels) n *= dimof[(unsigned char)ch];
+  return n;
+}
+
+// Strides (in elements) of every label of a row-major tensor.
+void strides_of(const std::string& labels, const Tensor& t, int64_t* strideof) {
+  int64_t s = 1;
+  for (int k = (int)labels.size() - 1; k >= 0; --k) {
+    strideof[(unsigned char)labels[k]] = s;
+    s *= t.dim[k];
+  }
+}
+
+std::string ordered(const std::string& from, const std::string& keep) {
+  std::string r;
+  for (char ch : from)
+    if (keep.find(ch) != std::string::npos) r += ch;
+  return r;
+}
+
+}  // namespace
+
+Engine::~Engine() {
+  for (auto& p : pending_) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : free_events_) cudaEventDestroy(e);
+}
+
+cudaEvent_t Engine::get_event() {
+  if (!free_events_.empty()) {
+    cudaEvent_t e = free_events_.back();
+    free_events_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  RT_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+bool Engine::trace_on() const {
+  const char* t = std::getenv("RTEOM_TRACE");
+  return t && *t;
+}
+
+void Engine::collect_timing() {
+  if (pending_.empty()) return;
+  RT_CUDA(cudaStreamSynchronize(stream));
+  FILE* tf = trace_on() ? std::fopen(std::getenv("RTEOM_TRACE"), "a") : nullptr;
+  static const char* names[kNumClasses] = {"ladder", "contract", "permute", "elementwise"};
+  for (auto& p : pending_) {
+    float t = 0.f;
+    RT_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    ms[p.cls] += t;
+    if (tf)
+      std::fprintf(tf, "{\"class\": \"%s\", \"what\": \"%s\", \"flops\": %.6g, \"ms\": %.6g}\n",
+                   names[p.cls], p.what.c_str(), p.flops, t);
+    free_events_.push_back(p.a);
+    free_events_.push_back(p.b);
+  }
+  if (tf) std::fclose(tf);
+  pending_.clear();
+}
+
+void Engine::axpy(const char* spec, double alpha, const Tensor& X, double beta, const Tensor& Y) {
+  Parsed p = parse(spec);
+  if ((int)p.a.size() != X.nd || (int)p.c.size() != Y.nd || p.a.size() != p.c.size())
+    throw Error(-1, std::string("axpy: rank mismatch in ") + spec);
+  if (X.cplx && !Y.cplx) throw Error(-1, std::string("axpy: complex into real in ") + spec);
+  int64_t sx[256];
+  strides_of(p.a, X, sx);
+  PermDesc d;
+  d.nd = Y.nd;
+  for (int k = 0; k < Y.nd; ++k) {
+    auto pos = p.a.find(p.c[k]);
+    if (pos == std::string::npos) throw Error(-1, std::string("axpy: label missing in ") + spec);
+    if (X.dim[pos] != Y.dim[k]) throw Error(-1, std::string("axpy: dim mismatch in ") + spec);
+    d.out_dim[k] = Y.dim[k];
+    d.in_stride[k] = sx[(unsigned char)p.c[k]];
+  }
+  launch(kPermute, 0.0, [&] { permute_add(X.p, Y.p, d, X.cplx, Y.cplx, alpha, beta, stream); },
+         spec);
+}
+
+void Engine::contract(const char* spec, double alpha, const Tensor& A, const Tensor& B,
+                      double beta, const Tensor& C, KernelClass cls) {
+  Parsed p = parse(spec);
+  if ((int)p.a.size() != A.nd || (int)p.b.size() != B.nd || (int)p.c.size() != C.nd)
+    throw Error(-1, std::string("contract: rank mismatch in ") + spec);
+  if (C.cplx != (A.cplx || B.cplx))
+    throw Error(-1, std::string("contract: output type mismatch in ") + spec);
+  int64_t dimof[256];
+  std::fill(dimof, dimof + 256, -1);
+  auto setdim = [&](const std::string& l, const Tensor& t) {
+    for (size_t k = 0; k < l.size(); ++k) {
+      unsigned char ch = l[k];
+      if (dimof[ch] >= 0 && dimof[ch] != t.dim[k])
+        throw Error(-1, std::string("contract: inconsistent dim for label in ") + spec);
+      dimof[ch] = t.dim[k];
+    }
+  };
+  setdim(p.a, A);
+  setdim(p.b, B);
+  setdim(p.c, C);
+
+  std::string batch, Ml, Nl, Kl;
+  for (char ch : p.c) {
+    bool inA = p.a.find(ch) != std::string::npos, inB = p.b.find(ch) != std::string::npos;
+    if (inA && inB)
+      batch += ch;
+    else if (inA)
+      Ml += ch;
+    else if (inB)
+      Nl += ch;
+    else
+      throw Error(-1, std::string("contract: output label in neither input: ") + spec);
+  }
+  for (char ch : p.a) {
+    if (p.c.find(ch) != std::string::npos) continue;
+    if (p.b.find(ch) == std::string::npos)
+      throw Error(-1, std::string("contract: label summed over one input only: ") + spec);
+    Kl += ch;
+  }
+  for (char ch : p.b)
+    if (p.c.find(ch) == std::string::npos && p.a.find(ch) == std::string::npos)
+      throw Error(-1, std::string("contract: label summed over one input only: ") + spec);
+
+  // choose label orders of the M, N and K groups that avoid the most copying
+  std::string Mc[2] = {Ml, ordered(p.a, Ml)};
+  std::string Nc[2] = {Nl, ordered(p.b, Nl)};
+  std::string Kc[2] = {ordered(p.a, Kl), ordered(p.b, Kl)};
+  int64_t best = -1;
+  std::string bM, bN, bK;
+  bool bTA = false, bTB = false, bPA = false, bPB = false, bPC = false;
+  for (int im = 0; im < 2; ++im)
+    for (int in = 0; in < 2; ++in)
+      for (int ik = 0; ik < 2; ++ik) {
+        const std::string &M = Mc[im], &N = Nc[in], &K = Kc[ik];
+        int64_t cost = 0;
+        bool ta = false, tb = false, pa = false, pb = false, pc = false;
+        if (p.a == batch + M + K) {
+        } else if (p.a == batch + K + M) {
+          ta = true;
+        } else {
+          pa = true;
+          cost += A.numel();
+        }
+        if (p.b == batch + K + N) {
+        } else if (p.b == batch + N + K) {
+          tb = true;
+        } else {
+          pb = true;
+          cost += B.numel();
+        }
+        if (p.c != batch + M + N) {
+          pc = true;
+          cost += 2 * C.numel();
+        }
+        if (best < 0 || cost < best) {
+          best = cost;
+          bM = M;
+          bN = N;
+          bK = K;
+          bTA = ta;
+          bTB = tb;
+          bPA = pa;
+          bPB = pb;
+          bPC = pc;
+        }
+      }
+
+  const int64_t Mt = prod(bM, dimof), Nt = prod(bN, dimof), Kt = prod(bK, dimof),
+                Bt = prod(batch, dimof);
+  if (Mt > 0x7fffffff || Nt > 0x7fffffff || Kt > 0x7fffffff || Bt > 65535)
+    throw Error(-1, std::string("contract: problem too large: ") + spec);
+  int64_t mark = arena.mark();
+
+  auto permuted = [&](const Tensor& T, const std::string& from, const std::string& to) {
+    Tensor out;
+    out.cplx = T.cplx;
+    out.nd = (int)to.size();
+    for (int k = 0; k < out.nd; ++k) out.dim[k] = dimof[(unsigned char)to[k]];
+    out.p = arena.alloc(out.doubles());
+    axpy((from + "->" + to).c_str(), 1.0, T, 0.0, out);
+    return out;
+  };
+
+  const Tensor Ause = bPA ? permuted(A, p.a, batch + bM + bK) : A;
+  const Tensor Buse = bPB ? permuted(B, p.b, batch + bK + bN) : B;
+  Tensor Cuse = C;
+  if (bPC) {
+    Cuse.nd = (int)(batch + bM + bN).size();
+    std::string lab = batch + bM + bN;
+    for (int k = 0; k < Cuse.nd; ++k) Cuse.dim[k] = dimof[(unsigned char)lab[k]];
+    Cuse.p = arena.alloc(Cuse.doubles());
+  }
+
+  GemmDesc g;
+  g.M = (int)Mt;
+  g.N = (int)Nt;
+  g.K = (int)Kt;
+  g.batch = (int)Bt;
+  g.A = Ause.p;
+  g.Acplx = A.cplx;
+  g.transA = bTA;
+  g.lda = bTA ? Mt : Kt;
+  g.strideA = Mt * Kt;
+  g.B = Buse.p;
+  g.Bcplx = B.cplx;
+  g.transB = bTB;
+  g.ldb = bTB ? Kt : Nt;
+  g.strideB = Kt * Nt;
+  g.C = Cuse.p;
+  g.ldc = Nt;
+  g.strideC = Mt * Nt;
+  g.alpha = alpha;
+  g.beta = bPC ? 0.0 : beta;
+  if (int64_t w = gemm_f64_workspace(g)) g.work = arena.alloc(w);
+  double mult = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
+  double flops = mult * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+  if (cls == kLadder && !dry) nvtxRangePushA("rteom_ladder");
+  launch(cls, flops, [&] { gemm_f64(g, stream); },
+         std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
+             " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
+             " s=" + std::to_string(gemm_f64_splits(g)) + (bPA ? " pA" : "") +
+             (bPB ? " pB" : "") + (bPC ? " pC" : ""));
+  if (cls == kLadder && !dry) nvtxRangePop();
+  if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
+  arena.release(mark);
+}
+
+}  // namespace rteom

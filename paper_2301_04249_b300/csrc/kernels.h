@@ -1,0 +1,108 @@
+// Launchers of the library's CUDA kernels (host-callable, stream-ordered).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace rteom {
+
+// ---- contractions ---------------------------------------------------------
+struct GemmDesc {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const double* A = nullptr;
+  int64_t lda = 0, strideA = 0;  // strides in elements (complex counts 1)
+  bool transA = false, Acplx = false;
+  const double* B = nullptr;
+  int64_t ldb = 0, strideB = 0;
+  bool transB = false, Bcplx = false;
+  double* C = nullptr;
+  int64_t ldc = 0, strideC = 0;
+  double alpha = 1.0, beta = 0.0;
+  double* work = nullptr;  // split-K partial sums, gemm_f64_workspace() doubles
+};
+// Number of K slices the kernel will use for this shape (1 = no split).
+int gemm_f64_splits(const GemmDesc& d);
+// Scratch (doubles) a split-K launch needs; 0 when no split is used.
+int64_t gemm_f64_workspace(const GemmDesc& d);
+void gemm_f64(const GemmDesc& d, cudaStream_t st);
+
+// out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
+// contiguous with dims out_dim[0..nd-1]; strides count elements.  A real
+// input may feed a complex output (imaginary part only scaled by beta).
+struct PermDesc {
+  int nd = 0;
+  int64_t out_dim[6] = {1, 1, 1, 1, 1, 1};
+  int64_t in_stride[6] = {0, 0, 0, 0, 0, 0};
+};
+void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx, bool out_cplx,
+                 double alpha, double beta, cudaStream_t st);
+
+// ---- amplitude algebra (padded [nO][nO][nV][nV] blocks) -------------------
+// out[i,j,a,b] = c1*t2[i,j,a,b] + c2*x[i,a]*y[j,b] + c3*x[i,b]*y[j,a]
+// (t2 may be null when c1 == 0); all complex.
+void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, const double* y,
+                  double c2, double c3, int nO, int nV, cudaStream_t st);
+
+// Geometry of the padded amplitude vector: blocks t1a, t1b (nO*nV) then
+// t2aa, t2ab, t2bb (nO*nO*nV*nV), complex.  Pads: alpha virtual slot 0 and
+// beta occupied slot `core`.
+struct AmpGeom {
+  int nO, nV, core;
+  __host__ __device__ int64_t n1() const { return (int64_t)nO * nV; }
+  __host__ __device__ int64_t n2() const { return (int64_t)nO * nO * nV * nV; }
+  __host__ __device__ int64_t total() const { return 2 * n1() + 3 * n2(); }
+  __host__ __device__ int64_t off(int blk) const {
+    return blk < 2 ? blk * n1() : 2 * n1() + (blk - 2) * n2();
+  }
+};
+
+// One Adams-Moulton micro-iteration (Eq. 9) over every element:
+// tk <- [(1 + i dt D/2) tn + (i dt/2)(Rn - D tn + Rk - D tk)] / (1 - i dt D/2),
+// pads forced to zero; *maxdiff_bits = max over elements of |new - old|
+// (as IEEE bits of a non-negative double; NaN compares largest).
+// tk_in and tk_out may alias (in-place update).
+void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const double* fo_b,
+               const double* fv_b, double dt, const double* tn, const double* Rn,
+               const double* tk_in, double* tk_out, const double* Rk,
+               unsigned long long* maxdiff_bits, cudaStream_t st);
+
+// Zero the pad entries of an amplitude vector.
+void mask_pads(const AmpGeom& g, double* t, cudaStream_t st);
+
+// Cumulant integrand E(t) (Eq. 5) with a deterministic two-pass reduction.
+// partial: scratch of energy_partials() complex entries.  The second pass
+// writes E into E_hist[n+1] and C_hist[n+1] = C_hist[n] + (i dt/2)(E_hist[n] + E)
+// when update_c != 0 (else only writes E to *E_hist at index n+1).
+int energy_partials(const AmpGeom& g);
+void energy(const AmpGeom& g, const double* t, const double* ovov, const double* fov_a,
+            const double* fov_b, int include_fov, double* partial, double* E_hist, double* C_hist,
+            long long n, double dt, int update_c, cudaStream_t st);
+
+// Pack an unpadded host-layout amplitude vector (device copy) into padded
+// blocks (pads zeroed), and the reverse.  O, V are the spatial counts.
+void pack_amplitudes(const AmpGeom& g, const double* unpadded, double* padded, cudaStream_t st);
+void unpack_amplitudes(const AmpGeom& g, const double* padded, double* unpadded, cudaStream_t st);
+
+// ---- set-up (once per context) ----------------------------------------------
+// Slot-space Cholesky blocks from L [nchol][nb][nb]:
+// Loo[Q][i][j], Lov[Q][i][a], Lvv[Q][a][b] with virtual slot 0 = core.
+void gather_cholesky(const double* L, int nchol, int nO, int nV, int core, double* Loo,
+                     double* Lov, double* Lvv, cudaStream_t st);
+// (N-1) Fock matrices per spin (Section 2.1), as slot blocks and diagonals.
+void build_fock(const double* eps, const double* L, int nchol, int nO, int nV, int core,
+                double* foo_a, double* fov_a, double* fvv_a, double* foo_b, double* fov_b,
+                double* fvv_b, double* fo_a, double* fv_a, double* fo_b, double* fv_b,
+                cudaStream_t st);
+// Closed-shell E_N^corr (Eq. 3) into *out (device), deterministic.
+void closed_shell_ecorr(const double* ovov, const double* t1, const double* t2, int O, int V,
+                        double* partial, double* out, cudaStream_t st);
+
+// ---- spectrum ----------------------------------------------------------------
+void spectrum(const double* C, long long M, double dt, double shift, const double* omega,
+              int nomega, double eta, double* A, cudaStream_t st);
+
+// Largest |x| over n doubles as IEEE bits (non-negative), for finiteness checks.
+void maxabs_bits(const double* x, int64_t n, unsigned long long* out, cudaStream_t st);
+
+}  // namespace rteom

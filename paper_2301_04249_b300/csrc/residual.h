@@ -1,0 +1,31 @@
+// Spin-explicit CCSD projections R_mu = <Phi_mu|(H_N e^{T1+T2})_C|Phi>
+// (Eqs. 7-8) of the core-ionised reference, on padded slot-space blocks.
+#pragma once
+
+#include "engine.h"
+
+namespace rteom {
+
+// Device operands shared by every residual evaluation (owned elsewhere).
+// Slot spaces: occupied slots 0..nO-1 = spatial 0..O-1; virtual slot 0 =
+// the core orbital, slot a >= 1 = spatial O + a - 1.  The same integral
+// arrays serve both spins; only the Fock matrix is spin dependent.
+struct ResidualOperands {
+  int nO = 0, nV = 0, core = 0;
+  // chemists' integrals (pq|rs) stored [p][q][r][s] over the named slot classes
+  const double *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *ovov = nullptr,
+               *ovvv = nullptr;
+  const double* vvvv = nullptr;  // ladder layout [e][f][a][b] = (ae|bf)
+  // (N-1) Fock slot blocks per spin (0 = alpha, 1 = beta), real and complex
+  const double *foo[2] = {nullptr, nullptr}, *fov[2] = {nullptr, nullptr},
+               *fvv[2] = {nullptr, nullptr};
+  const double *foo_c[2] = {nullptr, nullptr}, *fov_c[2] = {nullptr, nullptr},
+               *fvv_c[2] = {nullptr, nullptr};
+};
+
+// R = full projections for amplitudes t (both padded amplitude vectors,
+// layout of AmpGeom).  Scratch comes from E.arena; pad entries of R are
+// unspecified.  Issues only stream-ordered work (capturable).
+void compute_residual(Engine& E, const ResidualOperands& op, const double* t, double* R);
+
+}  // namespace rteom

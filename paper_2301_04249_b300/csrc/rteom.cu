@@ -1,0 +1,595 @@
+// C ABI of the RT-EOM-CCSD core-hole propagation (include/rteom.h).
+//
+// A context owns the device copies of the problem, the integral blocks built
+// from the Cholesky vectors, the amplitude buffers of the Adams-Moulton
+// micro-iteration (Eq. 9) and the cumulant history (Eqs. 5-6).  Each residual
+// evaluation is one CUDA graph (captured on first use); the host reads one
+// 8-byte convergence word per micro-iteration.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/rteom.h"
+#include "common.cuh"
+#include "engine.h"
+#include "kernels.h"
+#include "residual.h"
+
+using namespace rteom;
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+struct rteom_ctx {
+  int O = 0, V = 0, nchol = 0, core = 0, precision = 0, flags = 0;
+  int nO = 0, nV = 0;
+  AmpGeom g{0, 0, 0};
+  Engine E;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+
+  ResidualOperands op;
+  double *foo[2], *fov[2], *fvv[2], *fo[2], *fv[2];
+  double* ovov = nullptr;
+  double *T_N = nullptr, *R_N = nullptr, *T_K = nullptr, *R_K = nullptr;
+  double *histC = nullptr, *histE = nullptr;
+  long long hist_cap = 0;
+  double* partial = nullptr;
+  double* scalars = nullptr;  // [0] E_corr, [1..4] debug energy slots
+  unsigned long long* maxdiff = nullptr;
+  unsigned long long* h_maxdiff = nullptr;  // pinned
+  double* arena_base = nullptr;
+  int64_t arena_doubles = 0;
+
+  double eps_core = 0.0, e_corr = 0.0, dt = 0.0;
+  long long steps = 0, micro_total = 0;
+  long long graph_kernels = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
+  std::string err;
+
+  double* dmalloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(e == cudaErrorMemoryAllocation ? RTEOM_ERR_OOM : RTEOM_ERR_CUDA,
+                  "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    allocs.push_back(p);
+    return static_cast<double*>(p);
+  }
+  void dfree(void* p) {
+    for (auto& q : allocs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  ~rteom_ctx() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& gx : graph)
+      if (gx) cudaGraphExecDestroy(gx);
+    for (void* p : allocs)
+      if (p) cudaFree(p);
+    if (h_maxdiff) cudaFreeHost(h_maxdiff);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+int fail(rteom_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+template <class F>
+int guarded(rteom_ctx* c, F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    if (c) c->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return RTEOM_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return RTEOM_ERR_CUDA;
+  }
+}
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+void run_residual(rteom_ctx* c, int which) {
+  const double* t = which == 0 ? c->T_N : c->T_K;
+  double* R = which == 0 ? c->R_N : c->R_K;
+  if (c->E.timing) {  // eager, so every kernel is bracketed by events
+    compute_residual(c->E, c->op, t, R);
+    return;
+  }
+  if (!c->graph[which]) {
+    long long before = c->E.launches;
+    cudaGraph_t gr;
+    RT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      compute_residual(c->E, c->op, t, R);
+    } catch (...) {
+      cudaStreamEndCapture(c->stream, &gr);
+      if (gr) cudaGraphDestroy(gr);
+      throw;
+    }
+    RT_CUDA(cudaStreamEndCapture(c->stream, &gr));
+    cudaError_t e = cudaGraphInstantiate(&c->graph[which], gr, 0);
+    cudaGraphDestroy(gr);
+    RT_CUDA(e);
+    c->graph_kernels = c->E.launches - before;
+    c->E.launches = before;
+  }
+  RT_CUDA(cudaGraphLaunch(c->graph[which], c->stream));
+  c->E.launches += c->graph_kernels;
+}
+
+void ensure_hist(rteom_ctx* c, long long need) {
+  if (need <= c->hist_cap) return;
+  long long cap = c->hist_cap ? c->hist_cap : 1024;
+  while (cap < need) cap *= 2;
+  double* nC = c->dmalloc(16 * cap);
+  double* nE = c->dmalloc(16 * cap);
+  RT_CUDA(cudaMemsetAsync(nC, 0, 16 * cap, c->stream));
+  RT_CUDA(cudaMemsetAsync(nE, 0, 16 * cap, c->stream));
+  if (c->hist_cap) {
+    RT_CUDA(cudaMemcpyAsync(nC, c->histC, 16 * c->hist_cap, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA(cudaMemcpyAsync(nE, c->histE, 16 * c->hist_cap, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    c->dfree(c->histC);
+    c->dfree(c->histE);
+  }
+  c->histC = nC;
+  c->histE = nE;
+  c->hist_cap = cap;
+}
+
+long long unpadded_size(const rteom_ctx* c) {  // complex elements
+  long long oA = c->O, vA = c->V, oB = c->O - 1, vB = c->V + 1;
+  return oA * vA + oB * vB + oA * oA * vA * vA + oA * oB * vA * vB + oB * oB * vB * vB;
+}
+
+void energy_into(rteom_ctx* c, const double* t, double* Ehist, double* Chist, long long n,
+                 int update_c) {
+  c->E.launch(kElementwise, 0.0, [&] {
+    energy(c->g, t, c->ovov, c->fov[0], c->fov[1], !(c->flags & RTEOM_FLAG_CUMULANT_NO_FOV),
+           c->partial, Ehist, Chist, n, c->dt, update_c, c->stream);
+  });
+}
+
+void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs,
+           const double* t2_gs) {
+  const int O = c->O, V = c->V, nb = O + V, nchol = c->nchol;
+  const int nO = c->nO, nV = c->nV;
+  cudaStream_t st = c->stream;
+  Engine& E = c->E;
+  E.stream = st;
+
+  // inputs
+  double* d_eps = c->dmalloc(8 * nb);
+  RT_CUDA(cudaMemcpyAsync(d_eps, eps, 8 * nb, cudaMemcpyHostToDevice, st));
+  const size_t Lbytes = 8ull * nchol * nb * nb;
+  double* d_L = c->dmalloc(Lbytes);
+  if (nchol) RT_CUDA(cudaMemcpyAsync(d_L, L, Lbytes, cudaMemcpyHostToDevice, st));
+
+  // slot-space Cholesky blocks and Fock matrices
+  double* Loo = c->dmalloc(8ull * nchol * nO * nO);
+  double* Lov = c->dmalloc(8ull * nchol * nO * nV);
+  double* Lvv = c->dmalloc(8ull * nchol * nV * nV);
+  E.launch(kElementwise, 0.0,
+           [&] { gather_cholesky(d_L, nchol, nO, nV, c->core, Loo, Lov, Lvv, st); });
+  for (int s = 0; s < 2; ++s) {
+    c->foo[s] = c->dmalloc(8ull * nO * nO);
+    c->fov[s] = c->dmalloc(8ull * nO * nV);
+    c->fvv[s] = c->dmalloc(8ull * nV * nV);
+    c->fo[s] = c->dmalloc(8ull * nO);
+    c->fv[s] = c->dmalloc(8ull * nV);
+  }
+  E.launch(kElementwise, 0.0, [&] {
+    build_fock(d_eps, d_L, nchol, nO, nV, c->core, c->foo[0], c->fov[0], c->fvv[0], c->foo[1],
+               c->fov[1], c->fvv[1], c->fo[0], c->fv[0], c->fo[1], c->fv[1], st);
+  });
+  ResidualOperands& op = c->op;
+  op.nO = nO;
+  op.nV = nV;
+  op.core = c->core;
+  for (int s = 0; s < 2; ++s) {
+    op.foo[s] = c->foo[s];
+    op.fov[s] = c->fov[s];
+    op.fvv[s] = c->fvv[s];
+    double* fc_oo = c->dmalloc(16ull * nO * nO);
+    double* fc_ov = c->dmalloc(16ull * nO * nV);
+    double* fc_vv = c->dmalloc(16ull * nV * nV);
+    E.axpy("pq->pq", 1.0, make_tensor(c->foo[s], false, {nO, nO}), 0.0,
+           make_tensor(fc_oo, true, {nO, nO}));
+    E.axpy("pq->pq", 1.0, make_tensor(c->fov[s], false, {nO, nV}), 0.0,
+           make_tensor(fc_ov, true, {nO, nV}));
+    E.axpy("pq->pq", 1.0, make_tensor(c->fvv[s], false, {nV, nV}), 0.0,
+           make_tensor(fc_vv, true, {nV, nV}));
+    op.foo_c[s] = fc_oo;
+    op.fov_c[s] = fc_ov;
+    op.fvv_c[s] = fc_vv;
+  }
+
+  // chemists' integral blocks (pq|rs) = sum_Q L_pq L_rs (Section 3.1.1)
+  auto Lt = [&](double* p, int a, int b) { return make_tensor(p, false, {nchol, a, b}); };
+  double* oooo = c->dmalloc(8ull * nO * nO * nO * nO);
+  double* ooov = c->dmalloc(8ull * nO * nO * nO * nV);
+  double* oovv = c->dmalloc(8ull * nO * nO * nV * nV);
+  double* ovov = c->dmalloc(8ull * nO * nV * nO * nV);
+  double* ovvv = c->dmalloc(8ull * nO * nV * nV * nV);
+  double* vvvv = c->dmalloc(8ull * nV * nV * nV * nV);
+  // scratch arena for set-up contractions and, later, the residual
+  E.dry = true;
+  E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
+  compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
+                   reinterpret_cast<double*>(uintptr_t(4096)));
+  int64_t need = E.arena.peak_bytes() / 8;
+  int64_t setup_need = (int64_t)nV * nV * nV * nV + 64;  // (ae|bf) before its permute
+  if (setup_need > need) need = setup_need;
+  E.dry = false;
+  c->arena_doubles = need + 1024;
+  c->arena_base = c->dmalloc(8ull * c->arena_doubles);
+  E.arena.init(c->arena_base, c->arena_doubles);
+
+  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Loo, nO, nO), Lt(Loo, nO, nO), 0.0,
+             make_tensor(oooo, false, {nO, nO, nO, nO}));
+  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Loo, nO, nO), Lt(Lov, nO, nV), 0.0,
+             make_tensor(ooov, false, {nO, nO, nO, nV}));
+  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Loo, nO, nO), Lt(Lvv, nV, nV), 0.0,
+             make_tensor(oovv, false, {nO, nO, nV, nV}));
+  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lov, nO, nV), 0.0,
+             make_tensor(ovov, false, {nO, nV, nO, nV}));
+  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lvv, nV, nV), 0.0,
+             make_tensor(ovvv, false, {nO, nV, nV, nV}));
+  // ladder layout [e][f][a][b] = (ae|bf) = sum_Q L_ea L_fb
+  E.contract("Qea,Qfb->efab", 1.0, Lt(Lvv, nV, nV), Lt(Lvv, nV, nV), 0.0,
+             make_tensor(vvvv, false, {nV, nV, nV, nV}));
+  op.oooo = oooo;
+  op.ooov = ooov;
+  op.oovv = oovv;
+  op.ovov = ovov;
+  op.ovvv = ovvv;
+  op.vvvv = vvvv;
+  c->ovov = ovov;
+
+  // E_N^corr (Eq. 3) from the closed-shell ground-state amplitudes
+  c->partial = c->dmalloc(16ull * 2048);
+  c->scalars = c->dmalloc(8ull * 16);
+  RT_CUDA(cudaMemsetAsync(c->scalars, 0, 8 * 16, st));
+  double *d_t1 = nullptr, *d_t2 = nullptr;
+  if (t1_gs) {
+    d_t1 = c->dmalloc(8ull * O * V);
+    RT_CUDA(cudaMemcpyAsync(d_t1, t1_gs, 8ull * O * V, cudaMemcpyHostToDevice, st));
+  }
+  if (t2_gs) {
+    d_t2 = c->dmalloc(8ull * O * O * V * V);
+    RT_CUDA(cudaMemcpyAsync(d_t2, t2_gs, 8ull * O * O * V * V, cudaMemcpyHostToDevice, st));
+  }
+  if (t1_gs || t2_gs)
+    E.launch(kElementwise, 0.0,
+             [&] { closed_shell_ecorr(ovov, d_t1, d_t2, O, V, c->partial, c->scalars, st); });
+  RT_CUDA(cudaMemcpyAsync(&c->e_corr, c->scalars, 8, cudaMemcpyDeviceToHost, st));
+  RT_CUDA(cudaMemcpyAsync(&c->eps_core, d_eps + c->core, 8, cudaMemcpyDeviceToHost, st));
+  RT_CUDA(cudaStreamSynchronize(st));
+  // inputs no longer needed on the device
+  for (void* p : {(void*)d_L, (void*)Loo, (void*)Lov, (void*)Lvv, (void*)d_t1, (void*)d_t2})
+    if (p) c->dfree(p);
+
+  // amplitudes T(0) = 0 and the history C_0 = E_0 = 0
+  const size_t ab = 16ull * c->g.total();
+  c->T_N = c->dmalloc(ab);
+  c->R_N = c->dmalloc(ab);
+  c->T_K = c->dmalloc(ab);
+  c->R_K = c->dmalloc(ab);
+  for (double* p : {c->T_N, c->R_N, c->T_K, c->R_K}) RT_CUDA(cudaMemsetAsync(p, 0, ab, st));
+  ensure_hist(c, 1);
+  c->maxdiff = reinterpret_cast<unsigned long long*>(c->dmalloc(64));
+  void* hp = nullptr;
+  RT_CUDA(cudaMallocHost(&hp, 64));
+  c->h_maxdiff = static_cast<unsigned long long*>(hp);
+  RT_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* eps,
+                 const double* L, const double* t1_gs, const double* t2_gs, int core_index,
+                 int precision, int flags, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return RTEOM_ERR_ARG;
+  }
+  *out = nullptr;
+  auto bad = [&](int code, const std::string& m) {
+    g_create_error = m;
+    return code;
+  };
+  if (nocc < 1 || nvir < 1 || nchol < 0) return bad(RTEOM_ERR_ARG, "need nocc >= 1, nvir >= 1, nchol >= 0");
+  if (core_index < 0 || core_index >= nocc) return bad(RTEOM_ERR_ARG, "core_index outside the occupied orbitals");
+  if (!eps || (nchol > 0 && !L)) return bad(RTEOM_ERR_ARG, "eps (and L when nchol > 0) must be given");
+  if (precision != RTEOM_FP64)
+    return bad(RTEOM_ERR_ARG, "only RTEOM_FP64 is available in this build");
+  if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
+  const size_t nb = size_t(nocc) + nvir;
+  if ((double)(nvir + 1) * (nvir + 1) * (nvir + 1) * (nvir + 1) > 6.0e9)
+    return bad(RTEOM_ERR_ARG, "nvir too large for the cached (ae|bf) ladder block of this build");
+  if (!all_finite(eps, nb) || (nchol && !all_finite(L, size_t(nchol) * nb * nb)) ||
+      (t1_gs && !all_finite(t1_gs, size_t(nocc) * nvir)) ||
+      (t2_gs && !all_finite(t2_gs, size_t(nocc) * nocc * nvir * nvir)))
+    return bad(RTEOM_ERR_NONFINITE, "non-finite value in an input array");
+  if (nchol) {
+    double mx = 0.0;
+    for (size_t k = 0; k < size_t(nchol) * nb * nb; ++k) mx = std::fmax(mx, std::fabs(L[k]));
+    for (int q = 0; q < nchol; ++q)
+      for (size_t p = 0; p < nb; ++p)
+        for (size_t r = p + 1; r < nb; ++r)
+          if (std::fabs(L[(q * nb + p) * nb + r] - L[(q * nb + r) * nb + p]) > 1e-12 * mx)
+            return bad(RTEOM_ERR_ARG, "Cholesky vectors must be symmetric: L[q][p][r] == L[q][r][p]");
+  }
+  std::unique_ptr<rteom_ctx> c(new rteom_ctx());
+  c->O = nocc;
+  c->V = nvir;
+  c->nchol = nchol;
+  c->core = core_index;
+  c->precision = precision;
+  c->flags = flags;
+  c->nO = nocc;
+  c->nV = nvir + 1;
+  c->g = AmpGeom{c->nO, c->nV, core_index};
+  int rc = guarded(c.get(), [&] {
+    if (cuda_stream) {
+      c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      RT_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    setup(c.get(), eps, L, t1_gs, t2_gs);
+    return RTEOM_OK;
+  });
+  if (rc != RTEOM_OK) {
+    g_create_error = c->err;
+    return rc;
+  }
+  *out = c.release();
+  return RTEOM_OK;
+}
+
+int rteom_propagate(rteom_ctx* c, int nsteps, double dt, double tol, int max_micro,
+                    double* C_out) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt) || !(tol > 0) || max_micro < 1)
+    return fail(c, RTEOM_ERR_ARG, "need nsteps >= 0, dt > 0, tol > 0, max_micro >= 1");
+  if (c->dt > 0 && std::fabs(dt - c->dt) > 1e-15 * std::fabs(c->dt))
+    return fail(c, RTEOM_ERR_ARG, "dt must stay the same across calls of one context");
+  return guarded(c, [&] {
+    c->dt = dt;
+    const long long start = c->steps;
+    ensure_hist(c, start + nsteps + 1);
+    cudaStream_t st = c->stream;
+    for (int n = 0; n < nsteps; ++n) {
+      // R(t_n); the first micro-iteration starts from t^(0) = t_n
+      run_residual(c, 0);
+      bool converged = false;
+      int k = 0;
+      for (; k < max_micro; ++k) {
+        if (k > 0) run_residual(c, 1);
+        RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 8, st));
+        const double* tk_in = k == 0 ? c->T_N : c->T_K;
+        const double* Rk = k == 0 ? c->R_N : c->R_K;
+        c->E.launch(kElementwise, 0.0, [&] {
+          am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], dt, c->T_N, c->R_N, tk_in,
+                    c->T_K, Rk, c->maxdiff, st);
+        });
+        RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(cudaStreamSynchronize(st));
+        double d = bits_to_double(*c->h_maxdiff);
+        if (!std::isfinite(d))
+          return fail(c, RTEOM_ERR_NONFINITE,
+                      "amplitudes became non-finite at step " + std::to_string(c->steps));
+        if (d < tol) {
+          converged = true;
+          break;
+        }
+      }
+      if (!converged)
+        return fail(c, RTEOM_ERR_NOT_CONVERGED,
+                    "micro-iterations did not reach tol at step " + std::to_string(c->steps));
+      RT_CUDA(cudaMemcpyAsync(c->T_N, c->T_K, 16ull * c->g.total(), cudaMemcpyDeviceToDevice, st));
+      energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
+      c->steps += 1;
+      c->micro_total += k + 1;
+    }
+    if (C_out)
+      RT_CUDA(cudaMemcpyAsync(C_out, c->histC + 2 * start, 16ull * (nsteps + 1),
+                              cudaMemcpyDeviceToHost, st));
+    RT_CUDA(cudaStreamSynchronize(st));
+    if (c->E.timing) c->E.collect_timing();
+    return RTEOM_OK;
+  });
+}
+
+int rteom_spectrum(rteom_ctx* c, const double* omega, int nomega, double eta, double* A_out) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (nomega < 0 || (nomega > 0 && (!omega || !A_out)) || !(eta >= 0))
+    return fail(c, RTEOM_ERR_ARG, "need nomega >= 0, omega/A_out, eta >= 0");
+  if (c->steps < 1) return fail(c, RTEOM_ERR_STATE, "no step propagated yet");
+  if (nomega == 0) return RTEOM_OK;
+  if (!all_finite(omega, nomega)) return fail(c, RTEOM_ERR_NONFINITE, "non-finite omega");
+  return guarded(c, [&] {
+    double* d_w = c->dmalloc(8ull * nomega);
+    double* d_A = c->dmalloc(8ull * nomega);
+    RT_CUDA(cudaMemcpyAsync(d_w, omega, 8ull * nomega, cudaMemcpyHostToDevice, c->stream));
+    c->E.launch(kElementwise, 0.0, [&] {
+      spectrum(c->histC, c->steps, c->dt, c->eps_core + c->e_corr, d_w, nomega, eta, d_A,
+               c->stream);
+    });
+    RT_CUDA(cudaMemcpyAsync(A_out, d_A, 8ull * nomega, cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    c->dfree(d_w);
+    c->dfree(d_A);
+    return RTEOM_OK;
+  });
+}
+
+int rteom_get_info(const rteom_ctx* c, double* eps_core, double* e_corr, long long* steps_done,
+                   long long* micro_total) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (eps_core) *eps_core = c->eps_core;
+  if (e_corr) *e_corr = c->e_corr;
+  if (steps_done) *steps_done = c->steps;
+  if (micro_total) *micro_total = c->micro_total;
+  return RTEOM_OK;
+}
+
+long long rteom_state_size(const rteom_ctx* c) { return c ? 2 * unpadded_size(c) : -1; }
+
+int rteom_get_cumulant(const rteom_ctx* c0, long long count, double* C_out, double* E_out) {
+  rteom_ctx* c = const_cast<rteom_ctx*>(c0);
+  if (!c) return RTEOM_ERR_ARG;
+  if (count < 0 || count > c->steps + 1) return fail(c, RTEOM_ERR_ARG, "count > steps_done + 1");
+  return guarded(c, [&] {
+    if (C_out && count)
+      RT_CUDA(cudaMemcpyAsync(C_out, c->histC, 16ull * count, cudaMemcpyDeviceToHost, c->stream));
+    if (E_out && count)
+      RT_CUDA(cudaMemcpyAsync(E_out, c->histE, 16ull * count, cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    return RTEOM_OK;
+  });
+}
+
+int rteom_get_state(const rteom_ctx* c0, double* t_out, long long* steps, double* hist) {
+  rteom_ctx* c = const_cast<rteom_ctx*>(c0);
+  if (!c) return RTEOM_ERR_ARG;
+  return guarded(c, [&] {
+    if (steps) *steps = c->steps;
+    if (t_out) {
+      double* tmp = c->dmalloc(16ull * unpadded_size(c));
+      c->E.launch(kElementwise, 0.0, [&] { unpack_amplitudes(c->g, c->T_N, tmp, c->stream); });
+      RT_CUDA(cudaMemcpyAsync(t_out, tmp, 16ull * unpadded_size(c), cudaMemcpyDeviceToHost,
+                              c->stream));
+      RT_CUDA(cudaStreamSynchronize(c->stream));
+      c->dfree(tmp);
+    }
+    if (hist) {
+      const long long n = c->steps + 1;
+      RT_CUDA(cudaMemcpyAsync(hist, c->histC, 16ull * n, cudaMemcpyDeviceToHost, c->stream));
+      RT_CUDA(cudaMemcpyAsync(hist + 2 * n, c->histE, 16ull * n, cudaMemcpyDeviceToHost, c->stream));
+      RT_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return RTEOM_OK;
+  });
+}
+
+int rteom_set_state(rteom_ctx* c, const double* t_in, long long steps, const double* hist) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (!t_in || steps < 0) return fail(c, RTEOM_ERR_ARG, "need t_in and steps >= 0");
+  if (!all_finite(t_in, 2 * unpadded_size(c)))
+    return fail(c, RTEOM_ERR_NONFINITE, "non-finite amplitude");
+  if (hist && !all_finite(hist, 4 * (steps + 1)))
+    return fail(c, RTEOM_ERR_NONFINITE, "non-finite history");
+  return guarded(c, [&] {
+    double* tmp = c->dmalloc(16ull * unpadded_size(c));
+    RT_CUDA(cudaMemcpyAsync(tmp, t_in, 16ull * unpadded_size(c), cudaMemcpyHostToDevice,
+                            c->stream));
+    c->E.launch(kElementwise, 0.0, [&] { pack_amplitudes(c->g, tmp, c->T_N, c->stream); });
+    ensure_hist(c, steps + 1);
+    if (hist) {
+      const long long n = steps + 1;
+      RT_CUDA(cudaMemcpyAsync(c->histC, hist, 16ull * n, cudaMemcpyHostToDevice, c->stream));
+      RT_CUDA(cudaMemcpyAsync(c->histE, hist + 2 * n, 16ull * n, cudaMemcpyHostToDevice, c->stream));
+    } else {
+      // a restart without history: C = 0 and E = E(t) at this step
+      RT_CUDA(cudaMemsetAsync(c->histC, 0, 16ull * (steps + 1), c->stream));
+      RT_CUDA(cudaMemsetAsync(c->histE, 0, 16ull * (steps + 1), c->stream));
+      energy_into(c, c->T_N, c->histE, c->histC, steps - 1, 0);
+    }
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    c->dfree(tmp);
+    c->steps = steps;
+    return RTEOM_OK;
+  });
+}
+
+int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double* E_out) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (!t_in || !R_out) return fail(c, RTEOM_ERR_ARG, "need t_in and R_out");
+  if (!all_finite(t_in, 2 * unpadded_size(c)))
+    return fail(c, RTEOM_ERR_NONFINITE, "non-finite amplitude");
+  return guarded(c, [&] {
+    const size_t ub = 16ull * unpadded_size(c);
+    double* tmp = c->dmalloc(ub);
+    RT_CUDA(cudaMemcpyAsync(tmp, t_in, ub, cudaMemcpyHostToDevice, c->stream));
+    c->E.launch(kElementwise, 0.0, [&] { pack_amplitudes(c->g, tmp, c->T_K, c->stream); });
+    compute_residual(c->E, c->op, c->T_K, c->R_K);
+    c->E.launch(kElementwise, 0.0, [&] { unpack_amplitudes(c->g, c->R_K, tmp, c->stream); });
+    RT_CUDA(cudaMemcpyAsync(R_out, tmp, ub, cudaMemcpyDeviceToHost, c->stream));
+    if (E_out) {
+      // scalars[2..3] receive E (index n+1 = 1 of a two-entry history at scalars+0)
+      energy_into(c, c->T_K, c->scalars, c->scalars, 0, 0);
+      RT_CUDA(cudaMemcpyAsync(E_out, c->scalars + 2, 16, cudaMemcpyDeviceToHost, c->stream));
+    }
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    c->dfree(tmp);
+    if (c->E.timing) c->E.collect_timing();
+    return RTEOM_OK;
+  });
+}
+
+int rteom_set_timing(rteom_ctx* c, int on) {
+  if (!c) return RTEOM_ERR_ARG;
+  c->E.timing = on != 0;
+  return RTEOM_OK;
+}
+
+int rteom_get_timing(rteom_ctx* c, double* ms, long long* launches, double* flops, int reset) {
+  if (!c) return RTEOM_ERR_ARG;
+  return guarded(c, [&] {
+    c->E.collect_timing();
+    for (int k = 0; k < kNumClasses; ++k) {
+      if (ms) ms[k] = c->E.ms[k];
+      if (launches) launches[k] = c->E.tlaunch[k];
+      if (flops) flops[k] = c->E.tflops[k];
+      if (reset) {
+        c->E.ms[k] = 0;
+        c->E.tlaunch[k] = 0;
+        c->E.tflops[k] = 0;
+      }
+    }
+    return RTEOM_OK;
+  });
+}
+
+long long rteom_kernel_launches(const rteom_ctx* c) { return c ? c->E.launches : -1; }
+
+void rteom_destroy(rteom_ctx* c) { delete c; }
+
+const char* rteom_last_error(const rteom_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,601 @@
+// HBM-bound kernels of the propagation: tensor permutes, amplitude algebra,
+// the Adams-Moulton update (Eq. 9), the cumulant integrand (Eqs. 5-6), the
+// spectral transform, set-up gathers, and padded/unpadded conversions.
+//
+// Every reduction is deterministic: fixed grids, fixed per-thread order,
+// shared-memory trees, and bitwise max for the convergence measure, so the
+// same inputs give the same bits whatever else runs on the GPU.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rteom {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int per_sm = 8) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  int64_t cap = 148LL * per_sm;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ---------------------------------------------------------------- permute
+// CPI / CPO: input / output complex.  A real input into a complex output
+// scales the real part and leaves beta * imaginary part.
+template <bool CPI, bool CPO>
+__global__ void permute_kernel(const double* __restrict__ in, double* __restrict__ out,
+                               PermDesc d, double alpha, double beta, int64_t total) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = o, off = 0;
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+      if (k < d.nd) {
+        int64_t idx = rem % d.out_dim[k];
+        rem /= d.out_dim[k];
+        off += idx * d.in_stride[k];
+      }
+    }
+    if constexpr (CPO) {
+      double2 v = CPI ? reinterpret_cast<const double2*>(in)[off] : make_double2(in[off], 0.0);
+      double2* po = reinterpret_cast<double2*>(out) + o;
+      double2 r;
+      if (beta == 0.0) {
+        r = make_double2(alpha * v.x, alpha * v.y);
+      } else {
+        double2 c = *po;
+        r = make_double2(fma(beta, c.x, alpha * v.x), fma(beta, c.y, alpha * v.y));
+      }
+      *po = r;
+    } else {
+      double v = alpha * in[off];
+      if (beta != 0.0) v = fma(beta, out[o], v);
+      out[o] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- t2 + t1 t1
+__global__ void t2_t1t1_kernel(double2* __restrict__ out, const double2* __restrict__ t2,
+                               double c1, const double2* __restrict__ x,
+                               const double2* __restrict__ y, double c2, double c3, int nO,
+                               int nV) {
+  int64_t n = (int64_t)nO * nO * nV * nV;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int b = e % nV;
+    int a = (e / nV) % nV;
+    int j = (e / ((int64_t)nV * nV)) % nO;
+    int i = e / ((int64_t)nV * nV * nO);
+    double2 r = make_double2(0.0, 0.0);
+    if (t2 != nullptr) {
+      double2 t = t2[e];
+      r = make_double2(c1 * t.x, c1 * t.y);
+    }
+    if (c2 != 0.0) {
+      double2 p = cmul(x[i * nV + a], y[j * nV + b]);
+      r.x = fma(c2, p.x, r.x);
+      r.y = fma(c2, p.y, r.y);
+    }
+    if (c3 != 0.0) {
+      double2 p = cmul(x[i * nV + b], y[j * nV + a]);
+      r.x = fma(c3, p.x, r.x);
+      r.y = fma(c3, p.y, r.y);
+    }
+    out[e] = r;
+  }
+}
+
+// ---------------------------------------------------------------- amplitude geometry
+struct Elem {
+  int blk, i, j, a, b;
+};
+
+__device__ __forceinline__ Elem decode(const AmpGeom& g, int64_t e) {
+  Elem r;
+  int64_t n1 = g.n1(), n2 = g.n2();
+  if (e < 2 * n1) {
+    r.blk = (int)(e / n1);
+    int64_t q = e - r.blk * n1;
+    r.i = (int)(q / g.nV);
+    r.a = (int)(q % g.nV);
+    r.j = r.b = 0;
+  } else {
+    int64_t q = e - 2 * n1;
+    r.blk = 2 + (int)(q / n2);
+    q -= (int64_t)(r.blk - 2) * n2;
+    r.b = (int)(q % g.nV);
+    r.a = (int)((q / g.nV) % g.nV);
+    r.j = (int)((q / ((int64_t)g.nV * g.nV)) % g.nO);
+    r.i = (int)(q / ((int64_t)g.nV * g.nV * g.nO));
+  }
+  return r;
+}
+
+// Spins of (i,a) and (j,b) for each block: t1a, t1b, t2aa, t2ab, t2bb.
+__device__ __forceinline__ int spin_ia(int blk) { return (blk == 1 || blk == 4) ? 1 : 0; }
+__device__ __forceinline__ int spin_jb(int blk) { return (blk == 3 || blk == 4) ? 1 : 0; }
+
+__device__ __forceinline__ bool is_pad(const AmpGeom& g, const Elem& x) {
+  // alpha virtual slot 0 (the core is occupied in alpha) and beta occupied
+  // slot `core` (the ionised electron) do not exist.
+  int s1 = spin_ia(x.blk);
+  if (s1 == 0 && x.a == 0) return true;
+  if (s1 == 1 && x.i == g.core) return true;
+  if (x.blk >= 2) {
+    int s2 = spin_jb(x.blk);
+    if (s2 == 0 && x.b == 0) return true;
+    if (s2 == 1 && x.j == g.core) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ unsigned long long umax_warp(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
+                                 const double* __restrict__ fv_a, const double* __restrict__ fo_b,
+                                 const double* __restrict__ fv_b, double dt,
+                                 const double2* __restrict__ tn, const double2* __restrict__ Rn,
+                                 const double2* tk_in, double2* tk_out,
+                                 const double2* __restrict__ Rk, unsigned long long* maxdiff) {
+  __shared__ unsigned long long red[kThreads / 32];
+  unsigned long long m = 0ull;
+  int64_t total = g.total();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    Elem x = decode(g, e);
+    double2 old = tk_in[e];
+    double2 nw = make_double2(0.0, 0.0);
+    if (!is_pad(g, x)) {
+      int s1 = spin_ia(x.blk);
+      const double* fo1 = s1 ? fo_b : fo_a;
+      const double* fv1 = s1 ? fv_b : fv_a;
+      double D = fv1[x.a] - fo1[x.i];
+      if (x.blk >= 2) {
+        int s2 = spin_jb(x.blk);
+        D += (s2 ? fv_b : fv_a)[x.b] - (s2 ? fo_b : fo_a)[x.j];
+      }
+      double h = 0.5 * dt;
+      double2 t0 = tn[e];
+      double2 rn = Rn[e], rk = Rk[e];
+      // R' = R - D t for both points
+      double px = (rn.x - D * t0.x) + (rk.x - D * old.x);
+      double py = (rn.y - D * t0.y) + (rk.y - D * old.y);
+      // num = (1 + i h D) t0 + i h (R'n + R'k)
+      double nx = t0.x - h * D * t0.y - h * py;
+      double ny = t0.y + h * D * t0.x + h * px;
+      // divide by (1 - i h D): multiply by (1 + i h D) / (1 + (h D)^2)
+      double hd = h * D;
+      double inv = 1.0 / (1.0 + hd * hd);
+      nw.x = (nx - hd * ny) * inv;
+      nw.y = (ny + hd * nx) * inv;
+    }
+    tk_out[e] = nw;
+    double d = hypot(nw.x - old.x, nw.y - old.y);
+    unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(d));
+    if (d != d) bits = 0x7ff8000000000000ull;
+    m = bits > m ? bits : m;
+  }
+  m = umax_warp(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long v = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0ull;
+    v = umax_warp(v);
+    if (threadIdx.x == 0) atomicMax(maxdiff, v);
+  }
+}
+
+__global__ void mask_kernel(AmpGeom g, double2* t) {
+  int64_t total = g.total();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (is_pad(g, decode(g, e))) t[e] = make_double2(0.0, 0.0);
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sh[threadIdx.x].x += sh[threadIdx.x + s].x;
+      sh[threadIdx.x].y += sh[threadIdx.x + s].y;
+    }
+    __syncthreads();
+  }
+  double2 r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void energy_pass1(AmpGeom g, const double2* __restrict__ t,
+                             const double* __restrict__ ovov, const double* __restrict__ fov_a,
+                             const double* __restrict__ fov_b, int include_fov,
+                             double2* __restrict__ partial) {
+  __shared__ double2 sh[kThreads];
+  const int nO = g.nO, nV = g.nV;
+  const double2* t1a = t;
+  const double2* t1b = t + g.n1();
+  const double2* t2aa = t + 2 * g.n1();
+  const double2* t2ab = t2aa + g.n2();
+  const double2* t2bb = t2ab + g.n2();
+  double2 acc = make_double2(0.0, 0.0);
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (include_fov) {
+    for (int64_t e = tid; e < g.n1(); e += stride) {
+      double fa = fov_a[e], fb = fov_b[e];
+      acc.x += fa * t1a[e].x + fb * t1b[e].x;
+      acc.y += fa * t1a[e].y + fb * t1b[e].y;
+    }
+  }
+  for (int64_t e = tid; e < g.n2(); e += stride) {
+    int b = e % nV;
+    int a = (e / nV) % nV;
+    int j = (e / ((int64_t)nV * nV)) % nO;
+    int i = e / ((int64_t)nV * nV * nO);
+    // (ia|jb) and (ib|ja) from ovov[p][q][r][s] = (pq|rs)
+    double I1 = ovov[(((int64_t)i * nV + a) * nO + j) * nV + b];
+    double I2 = ovov[(((int64_t)i * nV + b) * nO + j) * nV + a];
+    double2 saa = t2aa[e], sab = t2ab[e], sbb = t2bb[e];
+    double2 ta_ia = t1a[i * nV + a], ta_jb = t1a[j * nV + b];
+    double2 tb_ia = t1b[i * nV + a], tb_jb = t1b[j * nV + b];
+    double2 paa = cmul(ta_ia, ta_jb), pbb = cmul(tb_ia, tb_jb), pab = cmul(ta_ia, tb_jb);
+    // 1/2 I (t2aa + t2bb) + I t2ab + 1/2 (I1 - I2)(t1a t1a + t1b t1b) + I t1a t1b
+    acc.x += 0.5 * I1 * (saa.x + sbb.x) + I1 * sab.x + 0.5 * (I1 - I2) * (paa.x + pbb.x) +
+             I1 * pab.x;
+    acc.y += 0.5 * I1 * (saa.y + sbb.y) + I1 * sab.y + 0.5 * (I1 - I2) * (paa.y + pbb.y) +
+             I1 * pab.y;
+  }
+  double2 s = block_sum2(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void energy_pass2(const double2* __restrict__ partial, int np, double2* E_hist,
+                             double2* C_hist, long long n, double dt, int update_c) {
+  __shared__ double2 sh[kThreads];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    acc.x += partial[k].x;
+    acc.y += partial[k].y;
+  }
+  double2 E = block_sum2(acc, sh);
+  if (threadIdx.x == 0) {
+    E_hist[n + 1] = E;
+    if (update_c) {
+      double2 Ep = E_hist[n];
+      double2 Cp = C_hist[n];
+      // C_{n+1} = C_n + (i dt / 2)(E_n + E_{n+1})
+      double sx = Ep.x + E.x, sy = Ep.y + E.y;
+      C_hist[n + 1] = make_double2(Cp.x - 0.5 * dt * sy, Cp.y + 0.5 * dt * sx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pack / unpack
+// Unpadded spin-block index of a padded element, or -1 for a pad.
+__device__ __forceinline__ int64_t unpadded_index(const AmpGeom& g, const Elem& x) {
+  if (is_pad(g, x)) return -1;
+  const int64_t oA = g.nO, vA = g.nV - 1, oB = g.nO - 1, vB = g.nV;
+  auto occ_u = [&](int s, int i) -> int64_t { return s ? (i < g.core ? i : i - 1) : i; };
+  auto vir_u = [&](int s, int a) -> int64_t { return s ? a : a - 1; };
+  int64_t o1a = 0, o1b = oA * vA, o2aa = o1b + oB * vB, o2ab = o2aa + oA * oA * vA * vA,
+          o2bb = o2ab + oA * oB * vA * vB;
+  switch (x.blk) {
+    case 0: return o1a + occ_u(0, x.i) * vA + vir_u(0, x.a);
+    case 1: return o1b + occ_u(1, x.i) * vB + vir_u(1, x.a);
+    case 2: return o2aa + ((occ_u(0, x.i) * oA + occ_u(0, x.j)) * vA + vir_u(0, x.a)) * vA + vir_u(0, x.b);
+    case 3: return o2ab + ((occ_u(0, x.i) * oB + occ_u(1, x.j)) * vA + vir_u(0, x.a)) * vB + vir_u(1, x.b);
+    default: return o2bb + ((occ_u(1, x.i) * oB + occ_u(1, x.j)) * vB + vir_u(1, x.a)) * vB + vir_u(1, x.b);
+  }
+}
+
+__global__ void pack_kernel(AmpGeom g, const double2* __restrict__ u, double2* __restrict__ p) {
+  int64_t total = g.total();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = unpadded_index(g, decode(g, e));
+    p[e] = k < 0 ? make_double2(0.0, 0.0) : u[k];
+  }
+}
+
+__global__ void unpack_kernel(AmpGeom g, const double2* __restrict__ p, double2* __restrict__ u) {
+  int64_t total = g.total();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = unpadded_index(g, decode(g, e));
+    if (k >= 0) u[k] = p[e];
+  }
+}
+
+// ---------------------------------------------------------------- set-up
+__device__ __forceinline__ int vmap(int a, int nO, int core) { return a == 0 ? core : nO + a - 1; }
+
+__global__ void gather_L_kernel(const double* __restrict__ L, int nchol, int nO, int nV, int core,
+                                double* Loo, double* Lov, double* Lvv) {
+  const int nb = nO + nV - 1;
+  int64_t per = (int64_t)nO * nO + (int64_t)nO * nV + (int64_t)nV * nV;
+  int64_t total = per * nchol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int Q = (int)(e / per);
+    int64_t r = e - (int64_t)Q * per;
+    const double* LQ = L + (int64_t)Q * nb * nb;
+    if (r < (int64_t)nO * nO) {
+      int i = r / nO, j = r % nO;
+      Loo[(int64_t)Q * nO * nO + r] = LQ[(int64_t)i * nb + j];
+    } else if (r < (int64_t)nO * nO + (int64_t)nO * nV) {
+      r -= (int64_t)nO * nO;
+      int i = r / nV, a = r % nV;
+      Lov[(int64_t)Q * nO * nV + r] = LQ[(int64_t)i * nb + vmap(a, nO, core)];
+    } else {
+      r -= (int64_t)nO * nO + (int64_t)nO * nV;
+      int a = r / nV, b = r % nV;
+      Lvv[(int64_t)Q * nV * nV + r] = LQ[(int64_t)vmap(a, nO, core) * nb + vmap(b, nO, core)];
+    }
+  }
+}
+
+// f^a_pq = eps_p d_pq - (pq|cc);  f^b_pq = f^a_pq + (pc|cq)
+__device__ double fock_elem(const double* eps, const double* L, int nchol, int nb, int core,
+                            int p, int q, int spin) {
+  double J = 0.0, K = 0.0;
+  const int64_t nn = (int64_t)nb * nb;
+  for (int Q = 0; Q < nchol; ++Q) {
+    const double* LQ = L + Q * nn;
+    J = fma(LQ[(int64_t)p * nb + q], LQ[(int64_t)core * nb + core], J);
+    K = fma(LQ[(int64_t)p * nb + core], LQ[(int64_t)core * nb + q], K);
+  }
+  double f = (p == q ? eps[p] : 0.0) - J;
+  if (spin) f += K;
+  return f;
+}
+
+__global__ void fock_kernel(const double* __restrict__ eps, const double* __restrict__ L,
+                            int nchol, int nO, int nV, int core, double* foo_a, double* fov_a,
+                            double* fvv_a, double* foo_b, double* fov_b, double* fvv_b) {
+  const int nb = nO + nV - 1;
+  int64_t per = (int64_t)nO * nO + (int64_t)nO * nV + (int64_t)nV * nV;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int spin = e >= per;
+    int64_t r = e - spin * per;
+    double *foo = spin ? foo_b : foo_a, *fov = spin ? fov_b : fov_a, *fvv = spin ? fvv_b : fvv_a;
+    if (r < (int64_t)nO * nO) {
+      int i = r / nO, j = r % nO;
+      foo[r] = fock_elem(eps, L, nchol, nb, core, i, j, spin);
+    } else if (r < (int64_t)nO * nO + (int64_t)nO * nV) {
+      r -= (int64_t)nO * nO;
+      int i = r / nV, a = r % nV;
+      fov[r] = fock_elem(eps, L, nchol, nb, core, i, vmap(a, nO, core), spin);
+    } else {
+      r -= (int64_t)nO * nO + (int64_t)nO * nV;
+      int a = r / nV, b = r % nV;
+      fvv[r] = fock_elem(eps, L, nchol, nb, core, vmap(a, nO, core), vmap(b, nO, core), spin);
+    }
+  }
+}
+
+__global__ void diag_kernel(const double* foo_a, const double* fvv_a, const double* foo_b,
+                            const double* fvv_b, int nO, int nV, double* fo_a, double* fv_a,
+                            double* fo_b, double* fv_b) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nO) {
+    fo_a[k] = foo_a[k * nO + k];
+    fo_b[k] = foo_b[k * nO + k];
+  }
+  if (k < nV) {
+    fv_a[k] = fvv_a[k * nV + k];
+    fv_b[k] = fvv_b[k * nV + k];
+  }
+}
+
+__global__ void ecorr_pass1(const double* __restrict__ ovov, const double* __restrict__ t1,
+                            const double* __restrict__ t2, int O, int V,
+                            double2* __restrict__ partial) {
+  __shared__ double2 sh[kThreads];
+  const int nO = O, nV = V + 1;
+  double acc = 0.0;
+  int64_t n = (int64_t)O * O * V * V;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int b = e % V;
+    int a = (e / V) % V;
+    int j = (e / ((int64_t)V * V)) % O;
+    int i = e / ((int64_t)V * V * O);
+    double iajb = ovov[(((int64_t)i * nV + a + 1) * nO + j) * nV + b + 1];
+    double ibja = ovov[(((int64_t)i * nV + b + 1) * nO + j) * nV + a + 1];
+    double tt = (t2 ? t2[e] : 0.0) + (t1 ? t1[i * V + a] * t1[j * V + b] : 0.0);
+    acc += (2.0 * iajb - ibja) * tt;
+  }
+  double2 s = block_sum2(make_double2(acc, 0.0), sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void ecorr_pass2(const double2* partial, int np, double* out) {
+  __shared__ double2 sh[kThreads];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = threadIdx.x; k < np; k += blockDim.x) acc.x += partial[k].x;
+  double2 s = block_sum2(acc, sh);
+  if (threadIdx.x == 0) *out = s.x;
+}
+
+// ---------------------------------------------------------------- spectrum
+// A(w) = -(1/pi) Im sum_n w_n dt G_n exp(i w tau_n - eta tau_n),
+// G_n = -i exp(-i shift tau_n) exp(C_n), shift = eps_c + E_corr.
+__global__ void spectrum_kernel(const double2* __restrict__ C, long long M, double dt,
+                                double shift, const double* __restrict__ omega, double eta,
+                                double* __restrict__ A) {
+  __shared__ double2 sh[kThreads];
+  const double w = omega[blockIdx.x];
+  double2 acc = make_double2(0.0, 0.0);
+  for (long long n = threadIdx.x; n <= M; n += blockDim.x) {
+    double tau = dt * (double)n;
+    double2 c = C[n];
+    double mag = exp(c.x - eta * tau);
+    double s, co;
+    sincos(c.y + (w - shift) * tau, &s, &co);
+    double wt = (n == 0 || n == M) ? 0.5 : 1.0;
+    // -i * (co + i s) = s - i co
+    acc.x += wt * mag * s;
+    acc.y -= wt * mag * co;
+  }
+  double2 S = block_sum2(acc, sh);
+  if (threadIdx.x == 0) A[blockIdx.x] = -(dt / 3.14159265358979323846) * S.y;
+}
+
+__global__ void maxabs_kernel(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+  __shared__ unsigned long long red[kThreads / 32];
+  unsigned long long m = 0ull;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = x[e];
+    unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(v));
+    if (v != v) bits = 0x7ff8000000000000ull;
+    m = bits > m ? bits : m;
+  }
+  m = umax_warp(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long v = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0ull;
+    v = umax_warp(v);
+    if (threadIdx.x == 0) atomicMax(out, v);
+  }
+}
+
+}  // namespace
+
+// ============================================================== launchers
+void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx, bool out_cplx,
+                 double alpha, double beta, cudaStream_t st) {
+  int64_t total = 1;
+  for (int k = 0; k < d.nd; ++k) total *= d.out_dim[k];
+  if (total == 0) return;
+  if (in_cplx && !out_cplx) throw Error(-1, "permute_add: complex input into real output");
+  int grid = grid_for(total, 16);
+  if (in_cplx)
+    permute_kernel<true, true><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
+  else if (out_cplx)
+    permute_kernel<false, true><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
+  else
+    permute_kernel<false, false><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
+  RT_CHECK_LAUNCH();
+}
+
+void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, const double* y,
+                  double c2, double c3, int nO, int nV, cudaStream_t st) {
+  int64_t n = (int64_t)nO * nO * nV * nV;
+  if (n == 0) return;
+  t2_t1t1_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
+      reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(t2), c1,
+      reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(y), c2, c3, nO, nV);
+  RT_CHECK_LAUNCH();
+}
+
+void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const double* fo_b,
+               const double* fv_b, double dt, const double* tn, const double* Rn,
+               const double* tk_in, double* tk_out, const double* Rk,
+               unsigned long long* maxdiff_bits, cudaStream_t st) {
+  am_update_kernel<<<grid_for(g.total(), 16), kThreads, 0, st>>>(
+      g, fo_a, fv_a, fo_b, fv_b, dt, reinterpret_cast<const double2*>(tn),
+      reinterpret_cast<const double2*>(Rn), reinterpret_cast<const double2*>(tk_in),
+      reinterpret_cast<double2*>(tk_out), reinterpret_cast<const double2*>(Rk), maxdiff_bits);
+  RT_CHECK_LAUNCH();
+}
+
+void mask_pads(const AmpGeom& g, double* t, cudaStream_t st) {
+  mask_kernel<<<grid_for(g.total(), 16), kThreads, 0, st>>>(g, reinterpret_cast<double2*>(t));
+  RT_CHECK_LAUNCH();
+}
+
+int energy_partials(const AmpGeom& g) { return grid_for(g.n2() > g.n1() ? g.n2() : g.n1(), 4); }
+
+void energy(const AmpGeom& g, const double* t, const double* ovov, const double* fov_a,
+            const double* fov_b, int include_fov, double* partial, double* E_hist, double* C_hist,
+            long long n, double dt, int update_c, cudaStream_t st) {
+  int np = energy_partials(g);
+  energy_pass1<<<np, kThreads, 0, st>>>(g, reinterpret_cast<const double2*>(t), ovov, fov_a,
+                                        fov_b, include_fov, reinterpret_cast<double2*>(partial));
+  RT_CHECK_LAUNCH();
+  energy_pass2<<<1, kThreads, 0, st>>>(reinterpret_cast<const double2*>(partial), np,
+                                       reinterpret_cast<double2*>(E_hist),
+                                       reinterpret_cast<double2*>(C_hist), n, dt, update_c);
+  RT_CHECK_LAUNCH();
+}
+
+void pack_amplitudes(const AmpGeom& g, const double* unpadded, double* padded, cudaStream_t st) {
+  pack_kernel<<<grid_for(g.total(), 16), kThreads, 0, st>>>(
+      g, reinterpret_cast<const double2*>(unpadded), reinterpret_cast<double2*>(padded));
+  RT_CHECK_LAUNCH();
+}
+
+void unpack_amplitudes(const AmpGeom& g, const double* padded, double* unpadded, cudaStream_t st) {
+  unpack_kernel<<<grid_for(g.total(), 16), kThreads, 0, st>>>(
+      g, reinterpret_cast<const double2*>(padded), reinterpret_cast<double2*>(unpadded));
+  RT_CHECK_LAUNCH();
+}
+
+void gather_cholesky(const double* L, int nchol, int nO, int nV, int core, double* Loo,
+                     double* Lov, double* Lvv, cudaStream_t st) {
+  int64_t total = ((int64_t)nO * nO + (int64_t)nO * nV + (int64_t)nV * nV) * nchol;
+  if (total == 0) return;
+  gather_L_kernel<<<grid_for(total, 16), kThreads, 0, st>>>(L, nchol, nO, nV, core, Loo, Lov, Lvv);
+  RT_CHECK_LAUNCH();
+}
+
+void build_fock(const double* eps, const double* L, int nchol, int nO, int nV, int core,
+                double* foo_a, double* fov_a, double* fvv_a, double* foo_b, double* fov_b,
+                double* fvv_b, double* fo_a, double* fv_a, double* fo_b, double* fv_b,
+                cudaStream_t st) {
+  int64_t per = (int64_t)nO * nO + (int64_t)nO * nV + (int64_t)nV * nV;
+  fock_kernel<<<grid_for(2 * per, 16), kThreads, 0, st>>>(eps, L, nchol, nO, nV, core, foo_a,
+                                                          fov_a, fvv_a, foo_b, fov_b, fvv_b);
+  RT_CHECK_LAUNCH();
+  int n = nO > nV ? nO : nV;
+  diag_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(foo_a, fvv_a, foo_b, fvv_b, nO,
+                                                                  nV, fo_a, fv_a, fo_b, fv_b);
+  RT_CHECK_LAUNCH();
+}
+
+void closed_shell_ecorr(const double* ovov, const double* t1, const double* t2, int O, int V,
+                        double* partial, double* out, cudaStream_t st) {
+  int64_t n = (int64_t)O * O * V * V;
+  int np = grid_for(n, 4);
+  ecorr_pass1<<<np, kThreads, 0, st>>>(ovov, t1, t2, O, V, reinterpret_cast<double2*>(partial));
+  RT_CHECK_LAUNCH();
+  ecorr_pass2<<<1, kThreads, 0, st>>>(reinterpret_cast<const double2*>(partial), np, out);
+  RT_CHECK_LAUNCH();
+}
+
+void spectrum(const double* C, long long M, double dt, double shift, const double* omega,
+              int nomega, double eta, double* A, cudaStream_t st) {
+  if (nomega <= 0) return;
+  spectrum_kernel<<<nomega, kThreads, 0, st>>>(reinterpret_cast<const double2*>(C), M, dt, shift,
+                                               omega, eta, A);
+  RT_CHECK_LAUNCH();
+}
+
+void maxabs_bits(const double* x, int64_t n, unsigned long long* out, cudaStream_t st) {
+  if (n == 0) return;
+  maxabs_kernel<<<grid_for(n, 8), kThreads, 0, st>>>(x, n, out);
+  RT_CHECK_LAUNCH();
+}
+
+}  // namespace rteom

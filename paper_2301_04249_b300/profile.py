@@ -1,0 +1,45 @@
+"""Evaluate CCSD residuals of a named workload eagerly, for profilers.
+
+  python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde] [--residuals 2]
+
+Each evaluation launches every kernel of one residual on the library's
+stream outside CUDA graphs, with the particle-particle ladder GEMMs inside
+the NVTX range "rteom_ladder" (select them with
+`ncu --nvtx --nvtx-include "rteom_ladder/"`).  Prints the per-class timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), ".."))
+
+import paper_2301_04249_b300 as P  # noqa: E402
+from synth import workload  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c2_formaldehyde")
+    ap.add_argument("--residuals", type=int, default=2)
+    a = ap.parse_args()
+    p, _ = workload(a.workload)
+    rng = np.random.default_rng(0)
+    with P.Propagator.from_problem(p) as g:
+        shapes = P.block_shapes(p.nocc, p.nvir)
+        t = [0.01 * (rng.standard_normal(s) + 1j * rng.standard_normal(s)) for s in shapes]
+        for k in (2, 4):
+            t[k] = t[k] - t[k].transpose(1, 0, 2, 3)
+            t[k] = t[k] - t[k].transpose(0, 1, 3, 2)
+        g.set_timing(True)
+        for _ in range(a.residuals):
+            g.residual(t)
+        print(json.dumps(g.timing()))
+
+
+if __name__ == "__main__":
+    main()

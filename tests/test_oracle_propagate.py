@@ -144,3 +144,23 @@ def test_transform_closed_form():
     A2 = PR.spectrum(G2, dt2, omega, eta)
     lor = (eta / np.pi) / ((omega - eps_c - e_corr) ** 2 + eta ** 2)
     assert np.abs(A2 - lor).max() < 2e-3 * lor.max()
+
+
+def test_closed_shell_ecorr_equals_spin_orbital_energy():
+    """E_N^corr of Eq. 3 (closed-shell formula) equals the spin-orbital CC
+    energy 1/4 sum <ij||ab> tau of the N-electron reference for the
+    spin-adapted amplitudes t^{ab}_{ij}(aa) = t_ijab - t_ijba, t(ab) = t_ijab."""
+    O, V = 3, 3
+    p = gen_problem(O, V, 6, 13)
+    h, v, occN = H.spinorb_hamiltonian(p.eps, p.L, O)
+    nb = p.nb
+    vir = [H.spinorb_index(nb, q, s) for s in (0, 1) for q in range(O, nb)]
+    f = H.reference_fock(h, v, occN)
+    t1, t2 = p.t1_gs, p.t2_gs
+    assert np.allclose(t2, t2.transpose(1, 0, 3, 2))
+    taa = t2 - t2.transpose(0, 1, 3, 2)
+    t1so, t2so = SA.blocks_to_spinorb([t1, t1, taa, t2, taa], O, O, V, V)
+    fr, vr = SA.reorder(f, v, occN, vir)
+    E_so = SA.residual(fr, vr, 2 * O, t1so, t2so)[0]
+    E_cs = PR.closed_shell_ecorr(p.L, O, t1, t2)
+    assert abs(E_so - E_cs) < 1e-12 * max(1.0, abs(E_cs))

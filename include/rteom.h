@@ -184,6 +184,37 @@ int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* fl
 /* rteom_kernel_launches -- number of kernels this context has launched. */
 long long rteom_kernel_launches(const rteom_ctx* ctx);
 
+/*
+ * rteom_ecorr_noalloc -- the closed-shell correlation energy E_N^corr that
+ * rteom_create computes (sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b),
+ * (pq|rs) = sum_Q L[Q][p][q] L[Q][r][s]), for callers that must not allocate
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * programs whose device memory is owned entirely by their own pool or
+ * framework allocator, or that run where a cudaMalloc/cudaFree (which may
+ * synchronise the device) is not allowed.  It allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call.
+ *
+ *  nocc, nvir, nchol  as for rteom_create; nocc*nocc <= 4096 (nocc <= 64)
+ *  L, t1_gs, t2_gs    DEVICE pointers, layouts as for rteom_create (t1_gs,
+ *                     t2_gs may be NULL: zero); L may be NULL if nchol == 0
+ *  e_corr             DEVICE pointer to one double, written asynchronously
+ *  cuda_stream        cudaStream_t, or NULL for the legacy default stream
+ *  err, err_len       optional host buffer for an error message (may be NULL)
+ *
+ * Scratch: one partial sum per occupied pair lives in a static device array
+ * of 4096 doubles (32 KiB) that every GPU loading the library keeps until the
+ * process exits.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.  All calls share the array
+ * and each overwrites the partials it reads, so calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race and must be serialised.
+ * Errors: RTEOM_ERR_ARG (sizes, including nocc*nocc > 4096, or NULL
+ * pointers; checked before any launch), RTEOM_ERR_CUDA.
+ */
+int rteom_ecorr_noalloc(int nocc, int nvir, int nchol, const double* L,
+                        const double* t1_gs, const double* t2_gs, double* e_corr,
+                        void* cuda_stream, char* err, int err_len);
+
 /* rteom_destroy -- free every device and host resource of the context. */
 void rteom_destroy(rteom_ctx* ctx);
 

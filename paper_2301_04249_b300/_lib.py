@@ -39,6 +39,8 @@ SIGNATURES = {
     "rteom_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rteom_get_timing": (ctypes.c_int, [_vp, _dp, _llp, _dp, ctypes.c_int]),
     "rteom_kernel_launches": (ctypes.c_longlong, [_vp]),
+    "rteom_ecorr_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                           _vp, _vp, ctypes.c_char_p, ctypes.c_int]),
     "rteom_destroy": (None, [_vp]),
     "rteom_last_error": (ctypes.c_char_p, [_vp]),
 }

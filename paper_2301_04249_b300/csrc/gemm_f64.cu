@@ -6,11 +6,13 @@
 // complex when either operand is.  op(A) is [M][K] read from A stored
 // [M][K] (lda) or, transposed, [K][M]; likewise op(B) is [K][N] from [K][N]
 // or [N][K].  alpha and beta are real.  On B300 the FP64 pipe issues about
-// two DFMA per clock per SM, so the kernel only has to keep that pipe busy:
-// a 64x64 (or 32x64) output tile per 256-thread block, 8-deep K slices
-// staged in shared memory, each thread accumulating a 4x4 (2x4) sub-tile in
-// registers.  Grids are sized by the output and batch; bounds are checked
-// on every load and store.
+// two DFMA per clock per SM, so the kernel only has to keep that pipe busy
+// and waste no lanes: an output tile of BM x BN per 256-thread block (64x64,
+// 32x64, 16x64, 8x128, 64x16 or 16x16, picked so that thin outputs do not
+// compute padding), 8-deep K slices staged in shared memory, each thread
+// accumulating a TM x TN sub-tile in registers; long K with few output tiles
+// is split into slices whose partial products are summed in slice order.
+// Bounds are checked on every load and store.
 #include <algorithm>
 
 #include "common.cuh"
@@ -66,11 +68,12 @@ __device__ __forceinline__ Val<CP> load_val(const double* base, int64_t idx, boo
 
 constexpr int BK = 8;
 
-template <bool AC, bool BC, int BM, int BN>
+template <bool AC, bool BC, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   constexpr bool CC = AC || BC;
-  constexpr int TM = BM / 16;  // rows per thread
-  constexpr int TN = BN / 16;  // cols per thread
+  constexpr int RM = BM / TM;  // thread rows; thread (tx, ty) owns rows ty + RM*i
+  constexpr int RN = BN / TN;  // thread cols; and cols tx + RN*j
+  static_assert(RM * RN == 256, "tile must map onto 256 threads");
   __shared__ Val<AC> As[BK][BM];
   __shared__ Val<BC> Bs[BK][BN];
 
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   const int kend = min(g.K, kbeg + g.kslice);
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % RN, ty = threadIdx.x / RN;
 
   double acc_r[TM][TN], acc_i[TM][TN];
 #pragma unroll
@@ -130,9 +133,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
       Val<AC> a[TM];
       Val<BC> bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + RM * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + RN * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -158,11 +161,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
 
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    int m = m0 + ty + 16 * i;
+    int m = m0 + ty + RM * i;
     if (m >= g.M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      int n = n0 + tx + 16 * j;
+      int n = n0 + tx + RN * j;
       if (n >= g.N) continue;
       int64_t o = (int64_t)m * g.ldc + n;
       if constexpr (CC) {
@@ -215,29 +218,52 @@ __global__ void splitk_reduce(const double* __restrict__ P, double* C, int M, in
   }
 }
 
+// Output tile shapes, chosen from the output's extents.
+struct Tile {
+  int bm, bn;
+};
+
+Tile pick_tile(int M, int N) {
+  if (M <= 8 && N > 16) return {8, 128};
+  if (M <= 16 && N <= 16) return {16, 16};
+  if (M <= 16) return {16, 64};
+  if (N <= 16) return {64, 16};
+  if (M <= 32) return {32, 64};
+  return {64, 64};
+}
+
 template <bool AC, bool BC>
 void launch_typed(const GemmArgs& g, int batch, int splits, cudaStream_t st) {
-  // Choose the tile so that the grid covers the 148 SMs several times.
-  int64_t tiles64 = (int64_t)((g.N + 63) / 64) * ((g.M + 63) / 64) * batch * splits;
-  if (tiles64 >= 4 * 148 || g.M > 32) {
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, batch * splits);
-    gemm_kernel<AC, BC, 64, 64><<<grid, 256, 0, st>>>(g);
-  } else {
-    dim3 grid((g.N + 63) / 64, (g.M + 31) / 32, batch * splits);
-    gemm_kernel<AC, BC, 32, 64><<<grid, 256, 0, st>>>(g);
-  }
+  const Tile t = pick_tile(g.M, g.N);
+  dim3 grid((g.N + t.bn - 1) / t.bn, (g.M + t.bm - 1) / t.bm, batch * splits);
+  if (t.bm == 64 && t.bn == 64)
+    gemm_kernel<AC, BC, 64, 64, 4, 4><<<grid, 256, 0, st>>>(g);
+  else if (t.bm == 32)
+    gemm_kernel<AC, BC, 32, 64, 2, 4><<<grid, 256, 0, st>>>(g);
+  else if (t.bm == 16 && t.bn == 64)
+    gemm_kernel<AC, BC, 16, 64, 1, 4><<<grid, 256, 0, st>>>(g);
+  else if (t.bm == 8)
+    gemm_kernel<AC, BC, 8, 128, 1, 4><<<grid, 256, 0, st>>>(g);
+  else if (t.bn == 16 && t.bm == 64)
+    gemm_kernel<AC, BC, 64, 16, 4, 1><<<grid, 256, 0, st>>>(g);
+  else
+    gemm_kernel<AC, BC, 16, 16, 1, 1><<<grid, 256, 0, st>>>(g);
 }
 
 }  // namespace
 
 int gemm_f64_splits(const GemmDesc& d) {
-  if (d.M <= 0 || d.N <= 0 || d.K < 1024) return 1;
-  int64_t tiles = (int64_t)((d.N + 63) / 64) * ((d.M + 63) / 64) * d.batch;
-  const int64_t target = 8 * 148;  // blocks: about four resident waves of two per SM
+  // Split K when the output alone gives too few blocks to balance 148 SMs
+  // (the FP64 pipe is the bottleneck, so only the block count matters); each
+  // slice keeps at least 128 of K.
+  if (d.M <= 0 || d.N <= 0 || d.K < 256) return 1;
+  const Tile t = pick_tile(d.M, d.N);
+  int64_t tiles = (int64_t)((d.N + t.bn - 1) / t.bn) * ((d.M + t.bm - 1) / t.bm) * d.batch;
+  const int64_t target = 8 * 148;
   if (tiles >= target) return 1;
   int64_t s = (target + tiles - 1) / tiles;
-  s = std::min<int64_t>(s, d.K / 512);
-  s = std::min<int64_t>(s, 16);
+  s = std::min<int64_t>(s, d.K / 128);
+  s = std::min<int64_t>(s, 1024);
   if ((int64_t)d.batch * s > 65535) s = 65535 / d.batch;
   return (int)std::max<int64_t>(s, 1);
 }
@@ -250,7 +276,7 @@ int64_t gemm_f64_workspace(const GemmDesc& d) {
 
 void gemm_f64(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  if ((d.M + 31) / 32 > 65535 || d.batch > 65535)
+  if ((d.M + 7) / 8 > 65535 || d.batch > 65535)
     throw Error(-1, "gemm_f64: grid too large");
   const int splits = gemm_f64_splits(d);
   if (splits > 1 && d.work == nullptr) throw Error(-1, "gemm_f64: split-K needs a workspace");

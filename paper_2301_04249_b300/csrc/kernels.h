@@ -44,6 +44,18 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
 void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, const double* y,
                   double c2, double c3, int nO, int nV, cudaStream_t st);
 
+// Antisymmetric pair packing of same-spin blocks.  Pairs are listed as
+// (p < q) in row-major order: pair index k <-> (p, q), npair = n(n-1)/2.
+// pack: out[P][Q] = t2[i,j,a,b] for P = (i<j), Q = (a<b)  (complex).
+void pack_pairs(const double* t2, double* out, int nO, int nV, cudaStream_t st);
+// R[i,j,a,b] += alpha*Rp[P][Q]; R[j,i,a,b] -= ...; R[i,j,b,a] -= ...;
+// R[j,i,b,a] += ...  (complex; the four targets of one (P,Q) are distinct).
+void unpack_pairs_antisym(const double* Rp, double* R, int nO, int nV, double alpha,
+                          cudaStream_t st);
+// Wm[(e<f)][(a<b)] = W[e][f][a][b] - W[f][e][a][b] from the ladder block
+// W[e][f][a][b] = (ae|bf) (real).
+void pack_ladder_antisym(const double* W, double* Wm, int nV, cudaStream_t st);
+
 // Geometry of the padded amplitude vector: blocks t1a, t1b (nO*nV) then
 // t2aa, t2ab, t2bb (nO*nO*nV*nV), complex.  Pads: alpha virtual slot 0 and
 // beta occupied slot `core`.

@@ -52,6 +52,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   const Tensor ooov = R_(op.ooov, {nO, nO, nO, nV});
   const Tensor oovv = R_(op.oovv, {nO, nO, nV, nV});
   const Tensor ovov = R_(op.ovov, {nO, nV, nO, nV});
+  const Tensor ovov_as = R_(op.ovov_as, {nO, nV, nO, nV});
   const Tensor ovvv = R_(op.ovvv, {nO, nV, nV, nV});
   const Tensor vvvv = R_(op.vvvv, {nV, nV, nV, nV});
   Tensor fov[2], foo_c[2], fov_c[2], fvv_c[2];
@@ -175,8 +176,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     ein("jf,mfbe->mbej", -1.0, t1[s], ovvv, 1.0, W);
     ein("nb,njme->mbej", -1.0, t1[s], ooov, 1.0, W);
     ein("nb,mjne->mbej", 1.0, t1[s], ooov, 1.0, W);
-    ein("jnfb,menf->mbej", -1.0, X, ovov, 1.0, W);
-    ein("jnfb,mfne->mbej", 1.0, X, ovov, 1.0, W);
+    ein("jnfb,menf->mbej", -1.0, X, ovov_as, 1.0, W);
     ein("jnbf,menf->mbej", 0.5, t2su[s], ovov, 1.0, W);
     (void)u;
     return W;
@@ -188,8 +188,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     axpy("mejb->mbej", 1.0, ovov, 0.0, W);
     ein("jf,mebf->mbej", 1.0, t1[s], ovvv, 1.0, W);
     ein("nb,njme->mbej", -1.0, t1[s], ooov, 1.0, W);
-    ein("jnbf,menf->mbej", 0.5, t2su[s], ovov, 1.0, W);
-    ein("jnbf,mfne->mbej", -0.5, t2su[s], ovov, 1.0, W);
+    ein("jnbf,menf->mbej", 0.5, t2su[s], ovov_as, 1.0, W);
     ein("jnfb,menf->mbej", -1.0, X, ovov, 1.0, W);
     return W;
   };
@@ -223,7 +222,19 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     axpy("ijab->ijab", -1.0, x, 1.0, R);
     axpy("jiab->ijab", 1.0, x, 1.0, R);
     ein("mnab,mnij->ijab", 0.5, tau_ss[s], Wss[s], 1.0, R);
-    E.contract("ijef,efab->ijab", 1.0, tau_ss[s], vvvv, 1.0, R, kLadder);
+    // ladder over antisymmetric pairs: sum_{e<f} tau_ij^ef [(ae|bf) - (af|be)]
+    // for i<j, a<b, scattered to the four (i,j,a,b) sign patterns
+    {
+      const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
+      if (npo > 0 && npv > 0) {
+        Tensor tp = newc({npo, npv});
+        Tensor Rp = newc({npo, npv});
+        E.launch(kElementwise, 0.0, [&] { pack_pairs(tau_ss[s].p, tp.p, nO, nV, E.stream); });
+        E.contract("pq,qr->pr", 1.0, tp, R_(op.vvvv_as, {npv, npv}), 0.0, Rp, kLadder);
+        E.launch(kElementwise, 0.0,
+                 [&] { unpack_pairs_antisym(Rp.p, R.p, nO, nV, 1.0, E.stream); });
+      }
+    }
     Tensor Z = newc({nO, nO, nV, nO});
     ein("ijef,mfae->ijam", 1.0, tau_ss[s], ovvv, 0.0, Z);
     ein("mb,ijam->ijab", 1.0, t1[s], Z, 0.0, x);

@@ -15,7 +15,10 @@ struct ResidualOperands {
   // chemists' integrals (pq|rs) stored [p][q][r][s] over the named slot classes
   const double *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *ovov = nullptr,
                *ovvv = nullptr;
+  const double* ovov_as = nullptr;  // [m][e][n][f] = (me|nf) - (mf|ne)
   const double* vvvv = nullptr;  // ladder layout [e][f][a][b] = (ae|bf)
+  // same-spin ladder block [(e<f)][(a<b)] = (ae|bf) - (af|be)
+  const double* vvvv_as = nullptr;
   // (N-1) Fock slot blocks per spin (0 = alpha, 1 = beta), real and complex
   const double *foo[2] = {nullptr, nullptr}, *fov[2] = {nullptr, nullptr},
                *fvv[2] = {nullptr, nullptr};

@@ -266,6 +266,20 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   // ladder layout [e][f][a][b] = (ae|bf) = sum_Q L_ea L_fb
   E.contract("Qea,Qfb->efab", 1.0, Lt(Lvv, nV, nV), Lt(Lvv, nV, nV), 0.0,
              make_tensor(vvvv, false, {nV, nV, nV, nV}));
+  // antisymmetrised (me|nf) - (mf|ne), shared by the W_mbej builds
+  double* ovov_as = c->dmalloc(8ull * nO * nV * nO * nV);
+  {
+    const Tensor src = make_tensor(ovov, false, {nO, nV, nO, nV});
+    const Tensor dst = make_tensor(ovov_as, false, {nO, nV, nO, nV});
+    E.axpy("menf->menf", 1.0, src, 0.0, dst);
+    E.axpy("mfne->menf", -1.0, src, 1.0, dst);
+  }
+  op.ovov_as = ovov_as;
+  // packed antisymmetric ladder block for the same-spin T2 blocks
+  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  double* vvvv_as = c->dmalloc(8ull * (npv > 0 ? npv * npv : 1));
+  E.launch(kElementwise, 0.0, [&] { pack_ladder_antisym(vvvv, vvvv_as, nV, st); });
+  op.vvvv_as = vvvv_as;
   op.oooo = oooo;
   op.ooov = ooov;
   op.oovv = oovv;

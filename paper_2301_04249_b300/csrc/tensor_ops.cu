@@ -93,6 +93,73 @@ __global__ void t2_t1t1_kernel(double2* __restrict__ out, const double2* __restr
   }
 }
 
+// ---------------------------------------------------------------- antisymmetric pairs
+// Pair k of n items in the order (0,1),(0,2),...,(0,n-1),(1,2),...: row p
+// starts at p*(2n-p-1)/2.  Decoded with a short scan (n is small).
+__device__ __forceinline__ void pair_of(int64_t k, int n, int& p, int& q) {
+  int64_t start = 0;
+  p = 0;
+  while (p < n - 1 && start + (n - 1 - p) <= k) {
+    start += n - 1 - p;
+    ++p;
+  }
+  q = p + 1 + (int)(k - start);
+}
+
+__global__ void pack_pairs_kernel(const double2* __restrict__ t2, double2* __restrict__ out,
+                                  int nO, int nV) {
+  const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npo * npv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, a, b;
+    pair_of(e / npv, nO, i, j);
+    pair_of(e % npv, nV, a, b);
+    out[e] = t2[(((int64_t)i * nO + j) * nV + a) * nV + b];
+  }
+}
+
+__global__ void unpack_pairs_kernel(const double2* __restrict__ Rp, double2* R, int nO, int nV,
+                                    double alpha) {
+  const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npo * npv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, a, b;
+    pair_of(e / npv, nO, i, j);
+    pair_of(e % npv, nV, a, b);
+    double2 v = Rp[e];
+    v.x *= alpha;
+    v.y *= alpha;
+    auto at = [&](int p, int q, int r, int s) -> double2& {
+      return R[(((int64_t)p * nO + q) * nV + r) * nV + s];
+    };
+    double2& r0 = at(i, j, a, b);
+    r0.x += v.x;
+    r0.y += v.y;
+    double2& r1 = at(j, i, a, b);
+    r1.x -= v.x;
+    r1.y -= v.y;
+    double2& r2 = at(i, j, b, a);
+    r2.x -= v.x;
+    r2.y -= v.y;
+    double2& r3 = at(j, i, b, a);
+    r3.x += v.x;
+    r3.y += v.y;
+  }
+}
+
+__global__ void pack_ladder_kernel(const double* __restrict__ W, double* __restrict__ Wm, int nV) {
+  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npv * npv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int ef, fe, a, b;
+    pair_of(e / npv, nV, ef, fe);
+    pair_of(e % npv, nV, a, b);
+    const int64_t v2 = (int64_t)nV * nV;
+    Wm[e] = W[((int64_t)ef * nV + fe) * v2 + (int64_t)a * nV + b] -
+            W[((int64_t)fe * nV + ef) * v2 + (int64_t)a * nV + b];
+  }
+}
+
 // ---------------------------------------------------------------- amplitude geometry
 struct Elem {
   int blk, i, j, a, b;
@@ -506,6 +573,30 @@ void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, con
   t2_t1t1_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
       reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(t2), c1,
       reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(y), c2, c3, nO, nV);
+  RT_CHECK_LAUNCH();
+}
+
+void pack_pairs(const double* t2, double* out, int nO, int nV, cudaStream_t st) {
+  int64_t n = (int64_t)nO * (nO - 1) / 2 * ((int64_t)nV * (nV - 1) / 2);
+  if (n == 0) return;
+  pack_pairs_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
+      reinterpret_cast<const double2*>(t2), reinterpret_cast<double2*>(out), nO, nV);
+  RT_CHECK_LAUNCH();
+}
+
+void unpack_pairs_antisym(const double* Rp, double* R, int nO, int nV, double alpha,
+                          cudaStream_t st) {
+  int64_t n = (int64_t)nO * (nO - 1) / 2 * ((int64_t)nV * (nV - 1) / 2);
+  if (n == 0) return;
+  unpack_pairs_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
+      reinterpret_cast<const double2*>(Rp), reinterpret_cast<double2*>(R), nO, nV, alpha);
+  RT_CHECK_LAUNCH();
+}
+
+void pack_ladder_antisym(const double* W, double* Wm, int nV, cudaStream_t st) {
+  int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  if (npv == 0) return;
+  pack_ladder_kernel<<<grid_for(npv * npv, 16), kThreads, 0, st>>>(W, Wm, nV);
   RT_CHECK_LAUNCH();
 }
 

@@ -35,6 +35,7 @@ from synth import workload  # noqa: E402
 METRIC = "time_steps_per_s"
 UNIT = "steps/s"
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (profiling recipe table); no tensor-core FP64 path
+TF32_PER_BF16_NOMINAL = 1.1 / 2.25  # dense TF32 / dense BF16, nominal B300 figures
 MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
 
@@ -49,6 +50,7 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 form")
     return ap.parse_args()
 
 
@@ -193,6 +195,40 @@ def fp64_dgemm_tflops(torch, dev):
     return 2 * 4096 ** 3 / best / 1e12
 
 
+def split_summary(split, args, fp64_value, world, C_fp64, peaks):
+    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of the
+    split-TF32 form measured on the same workload and step counts."""
+    if split is None:
+        return None
+    tm = split["tm"]
+    lad = tm["ladder"]
+    v = world * args.steps / split["elapsed"]
+    bf16 = peaks.get("bf16_tflops")
+    tf32_peak = bf16 * TF32_PER_BF16_NOMINAL if bf16 else None
+    avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
+    fl = lad["flops"] / max(lad["launches"], 1)
+    ach = fl / avg_s / 1e12 if lad["launches"] else None
+    n = min(len(C_fp64), len(split["C"]))
+    dC = float(np.abs(np.asarray(split["C"])[:n] - np.asarray(C_fp64)[:n]).max())
+    total_tc = sum(x["flops"] for x in tm.values())
+    return {"split_tf32": {
+        "value": v, "unit": UNIT, "ms_per_step": 1e3 * split["elapsed"] / args.steps,
+        "speedup_vs_fp64": v / fp64_value,
+        "micro_iterations_per_step": split["micro"] / args.steps,
+        "max_abs_dC_vs_fp64": dC,
+        "gpu_launches": split["launches"],
+        "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, ladder)",
+                     "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": ach / tf32_peak if (ach and tf32_peak) else None,
+                     "peak_source": "measured BF16 x nominal TF32/BF16 ratio (of measured)",
+                     "flops_per_launch_executed": fl, "avg_launch_ms": avg_s * 1e3,
+                     "launches": lad["launches"],
+                     "note": "executed = 3 split products x 2 x M x N x K (algorithmic)"},
+        "executed_tflops_all_contractions": total_tc / split["elapsed"] / 1e12,
+        "time_by_class_ms": {k: x["ms"] for k, x in tm.items()},
+    }}
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -241,6 +277,7 @@ def run_ours(args):
     launches = g.kernel_launches() - launches0
     micro = info1["micro"] - info0["micro"]
     state = g.get_state(with_history=False)["t"]
+    fp64_hist, _ = g.cumulant()
     g.close()
 
     # end to end through the public API from pinned host buffers
@@ -267,6 +304,32 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+
+    # the split-TF32 form on the same inputs, same step counts
+    split = None
+    if not args.no_split:
+        gs = P.Propagator.from_problem(p, stream=stream, precision=P.RTEOM_SPLIT_TF32)
+        gs.propagate(args.warmup, dt, tol=args.tol, max_micro=args.max_micro)
+        i0 = gs.info()
+        gs.set_timing(True)
+        gs.timing(reset=True)
+        l0 = gs.kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        gs.propagate(args.steps, dt, tol=args.tol, max_micro=args.max_micro)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        el_s = f0.elapsed_time(f1) / 1e3
+        tms = gs.timing()
+        i1 = gs.info()
+        Cs_split, _ = gs.cumulant()
+        launches_split = gs.kernel_launches() - l0
+        gs.close()
+        split = dict(elapsed=el_s, tm=tms, micro=i1["micro"] - i0["micro"], C=Cs_split,
+                     launches=launches_split)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -327,6 +390,7 @@ def run_ours(args):
                         "returning C_n + rteom_spectrum + destroy, wall clock"},
         "gpu_launches": launches,
         "clocks": clocks,
+        "forms": split_summary(split, args, value, world, fp64_hist, peaks),
         "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
     print(json.dumps(res), flush=True)

@@ -52,8 +52,13 @@ extern "C" {
 
 /* precision forms */
 #define RTEOM_FP64        0   /* every contraction and update in FP64           */
-#define RTEOM_SPLIT_BF16  1   /* reserved: split-BF16 contractions, FP64 update */
-#define RTEOM_SPLIT_TF32  2   /* reserved: split-TF32 contractions, FP64 update */
+#define RTEOM_SPLIT_BF16  1   /* reserved (not built): split-BF16 contractions  */
+#define RTEOM_SPLIT_TF32  2   /* contractions of at least 5e7 FLOP on the tensor
+                                 cores as split-TF32 products (x = hi + lo,
+                                 hi*hi + hi*lo + lo*hi) with FP32 accumulation
+                                 over slices of at most 512 of K, slices summed
+                                 in FP64; every other step (small contractions,
+                                 Adams-Moulton update, cumulant, phases) FP64 */
 
 /* flags for rteom_create */
 #define RTEOM_FLAG_CUMULANT_NO_FOV 1  /* cumulant integrand without sum f_ia t_i^a,
@@ -78,7 +83,7 @@ typedef struct rteom_ctx rteom_ctx;
  *             NULL; t1_gs/t2_gs only enter E_N^corr of Eq. 3:
  *             E = sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
  *  core_index spatial index c of the ionised orbital, 0 <= c < O
- *  precision  RTEOM_FP64 (the split forms return RTEOM_ERR_ARG until built)
+ *  precision  RTEOM_FP64 or RTEOM_SPLIT_TF32 (RTEOM_SPLIT_BF16: RTEOM_ERR_ARG)
  *  flags      RTEOM_FLAG_* bits
  *  cuda_stream cudaStream_t to run on, or NULL for a non-blocking stream
  *             created and owned by the context

@@ -37,6 +37,7 @@ struct Tensor {
   int nd = 0;
   int64_t dim[kMaxDims] = {0, 0, 0, 0, 0, 0};
   bool cplx = false;
+  bool constant = false;  // contents fixed for the context's lifetime (integrals)
 
   int64_t numel() const {
     int64_t n = 1;

@@ -222,8 +222,29 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     return out;
   };
 
-  const Tensor Ause = bPA ? permuted(A, p.a, batch + bM + bK) : A;
-  const Tensor Buse = bPB ? permuted(B, p.b, batch + bK + bN) : B;
+  double mult0 = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
+  const bool use_tc =
+      tensor_cores && mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt >= tc_min_flops;
+
+  // tensor-core operands of constant tensors may already be packed
+  auto key = [&](const char* role, const Tensor& T) {
+    return std::string(role) + "|" + spec + "|" + std::to_string((uintptr_t)T.p) + "|" +
+           std::to_string(Mt) + "," + std::to_string(Nt) + "," + std::to_string(Kt) + "," +
+           std::to_string(Bt);
+  };
+  const Packed* cA = nullptr;
+  const Packed* cB = nullptr;
+  if (use_tc && A.constant) {
+    auto it = tc_cache_.find(key("A", A));
+    if (it != tc_cache_.end()) cA = &it->second;
+  }
+  if (use_tc && B.constant) {
+    auto it = tc_cache_.find(key("B", B));
+    if (it != tc_cache_.end()) cB = &it->second;
+  }
+
+  const Tensor Ause = (bPA && !cA) ? permuted(A, p.a, batch + bM + bK) : A;
+  const Tensor Buse = (bPB && !cB) ? permuted(B, p.b, batch + bK + bN) : B;
   Tensor Cuse = C;
   if (bPC) {
     Cuse.nd = (int)(batch + bM + bN).size();
@@ -252,17 +273,52 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   g.strideC = Mt * Nt;
   g.alpha = alpha;
   g.beta = bPC ? 0.0 : beta;
-  if (int64_t w = gemm_f64_workspace(g)) g.work = arena.alloc(w);
-  double mult = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
-  double flops = mult * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+  double flops = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+  const std::string label =
+      trace_on() ? std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
+                       " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
+                       (use_tc ? std::string(" tc") + (cA ? " cA" : "") + (cB ? " cB" : "")
+                               : " s=" + std::to_string(gemm_f64_splits(g))) +
+                       (bPA ? " pA" : "") + (bPB ? " pB" : "") + (bPC ? " pC" : "")
+                 : std::string();
   if (cls == kLadder && !dry) nvtxRangePushA("rteom_ladder");
-  launch(cls, flops, [&] { gemm_f64(g, stream); },
-         std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
-             " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
-             " s=" + std::to_string(gemm_f64_splits(g)) + (bPA ? " pA" : "") +
-             (bPB ? " pB" : "") + (bPC ? " pC" : ""));
-  if (cls == kLadder && !dry) nvtxRangePop();
+  if (!use_tc) {
+    if (int64_t w = gemm_f64_workspace(g)) g.work = arena.alloc(w);
+    launch(cls, flops, [&] { gemm_f64(g, stream); }, label);
+  } else {
+    const TcLayout L = gemm_tc_layout(g);
+    auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t elems,
+                       bool is_a) -> Packed {
+      if (cached) return *cached;
+      Packed pk;
+      const bool store = T.constant && tc_cache_fill && !dry && persistent_alloc;
+      if (store) {
+        pk.hi = persistent_alloc(elems);
+        pk.lo = persistent_alloc(elems);
+      } else {
+        pk.hi = reinterpret_cast<float*>(arena.alloc((elems + 1) / 2));
+        pk.lo = reinterpret_cast<float*>(arena.alloc((elems + 1) / 2));
+      }
+      launch(kPermute, 0.0,
+             [&] {
+               if (is_a)
+                 gemm_tc_pack_a(g, pk.hi, pk.lo, stream);
+               else
+                 gemm_tc_pack_b(g, pk.hi, pk.lo, stream);
+             },
+             "tc pack");
+      if (store) tc_cache_[key(role, T)] = pk;
+      return pk;
+    };
+    const Packed pa = operand("A", A, cA, L.a_elems, true);
+    const Packed pb = operand("B", B, cB, L.b_elems, false);
+    float* D = reinterpret_cast<float*>(arena.alloc((L.d_elems + 1) / 2));
+    launch(cls, 3.0 * flops,
+           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, D, tc_err, stream); }, label);
+    launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, D, stream); }, "tc finalize");
+  }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
+  if (cls == kLadder && !dry) nvtxRangePop();
   arena.release(mark);
 }
 

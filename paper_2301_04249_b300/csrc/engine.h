@@ -4,6 +4,8 @@
 // arena, launch counting and per-class CUDA-event timing.
 #pragma once
 
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -20,6 +22,16 @@ class Engine {
   Arena arena;
   bool dry = false;  // plan only: allocate scratch, launch nothing
   long long launches = 0;
+  // split precision: contractions of at least tc_min_flops run on the tensor
+  // cores (split TF32, FP32 accumulation); tc_err collects pipeline timeouts
+  bool tensor_cores = false;
+  double tc_min_flops = 5e7;
+  int* tc_err = nullptr;
+  // Packed tensor-core operands of constant tensors, keyed by tensor, spec
+  // and role.  Entries are created only while tc_cache_fill is set (an eager
+  // pass at set-up); later evaluations, captured graphs included, read them.
+  bool tc_cache_fill = false;
+  std::function<float*(int64_t)> persistent_alloc;  // floats, owned by the context
 
   // timing (eager execution only)
   bool timing = false;
@@ -67,6 +79,10 @@ class Engine {
     std::string what;
   };
   bool trace_on() const;
+  struct Packed {
+    float *hi, *lo;
+  };
+  std::map<std::string, Packed> tc_cache_;
   std::vector<Pending> pending_;
   std::vector<cudaEvent_t> free_events_;
   cudaEvent_t get_event();

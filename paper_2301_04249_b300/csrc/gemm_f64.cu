@@ -250,9 +250,118 @@ void launch_typed(const GemmArgs& g, int batch, int splits, cudaStream_t st) {
     gemm_kernel<AC, BC, 16, 16, 1, 1><<<grid, 256, 0, st>>>(g);
 }
 
+// ---- matrix-vector shapes (M == 1 or N == 1), deterministic
+// Output j of the vector product y_j = sum_k x(k) * Mat(k, j).  When the
+// output index is contiguous in Mat, one thread per output walks k (loads
+// coalesced across threads); when k is contiguous, one warp per output
+// strides k and reduces with a fixed shuffle tree.
+template <bool XC, bool MC>
+__device__ __forceinline__ void cmad(double& re, double& im, const double* x, int64_t xi,
+                                     const double* m, int64_t mi) {
+  const double xr = XC ? x[2 * xi] : x[xi], xim = XC ? x[2 * xi + 1] : 0.0;
+  const double mr = MC ? m[2 * mi] : m[mi], mim = MC ? m[2 * mi + 1] : 0.0;
+  re = fma(xr, mr, re);
+  if (XC && MC) re = fma(-xim, mim, re);
+  if (XC) im = fma(xim, mr, im);
+  if (MC) im = fma(xr, mim, im);
+}
+
+struct GemvArgs {
+  const double* x;  // vector, element k at x[k * sx]
+  int64_t sx;
+  const double* m;  // matrix, element (k, j) at m[k * sk + j * sj]
+  int64_t sk, sj;
+  double* y;        // output j at y[j * sy]
+  int64_t sy;
+  int n, K;         // outputs, reduction length
+  double alpha, beta;
+};
+
+template <bool XC, bool MC>
+__global__ void gemv_thread_kernel(GemvArgs a) {
+  constexpr bool YC = XC || MC;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  double re = 0.0, im = 0.0;
+  for (int k = 0; k < a.K; ++k) cmad<XC, MC>(re, im, a.x, k * a.sx, a.m, k * a.sk + j * a.sj);
+  double* y = a.y + (YC ? 2 : 1) * (int64_t)j * a.sy;
+  y[0] = a.beta == 0.0 ? a.alpha * re : fma(a.beta, y[0], a.alpha * re);
+  if (YC) y[1] = a.beta == 0.0 ? a.alpha * im : fma(a.beta, y[1], a.alpha * im);
+}
+
+template <bool XC, bool MC>
+__global__ void gemv_warp_kernel(GemvArgs a) {
+  constexpr bool YC = XC || MC;
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (j >= a.n) return;
+  double re = 0.0, im = 0.0;
+  for (int k = lane; k < a.K; k += 32)
+    cmad<XC, MC>(re, im, a.x, k * a.sx, a.m, k * a.sk + j * a.sj);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    double* y = a.y + (YC ? 2 : 1) * (int64_t)j * a.sy;
+    y[0] = a.beta == 0.0 ? a.alpha * re : fma(a.beta, y[0], a.alpha * re);
+    if (YC) y[1] = a.beta == 0.0 ? a.alpha * im : fma(a.beta, y[1], a.alpha * im);
+  }
+}
+
+template <bool XC, bool MC>
+void launch_gemv(const GemvArgs& a, cudaStream_t st) {
+  if (a.sj == 1) {
+    gemv_thread_kernel<XC, MC><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  } else {
+    gemv_warp_kernel<XC, MC><<<(a.n + 7) / 8, 256, 0, st>>>(a);
+  }
+}
+
+void gemv_f64(const GemmDesc& d, cudaStream_t st) {
+  GemvArgs a;
+  bool xc, mc;
+  if (d.M == 1) {  // y[n] = sum_k A[0,k] B[k,n]
+    a.x = d.A;
+    a.sx = d.transA ? d.lda : 1;
+    xc = d.Acplx;
+    a.m = d.B;
+    mc = d.Bcplx;
+    a.sk = d.transB ? 1 : d.ldb;
+    a.sj = d.transB ? d.ldb : 1;
+    a.y = d.C;
+    a.sy = 1;
+    a.n = d.N;
+  } else {  // N == 1: y[m] = sum_k A[m,k] B[k,0]
+    a.x = d.B;
+    a.sx = d.transB ? 1 : d.ldb;
+    xc = d.Bcplx;
+    a.m = d.A;
+    mc = d.Acplx;
+    a.sk = d.transA ? d.lda : 1;
+    a.sj = d.transA ? 1 : d.lda;
+    a.y = d.C;
+    a.sy = d.ldc;
+    a.n = d.M;
+  }
+  a.K = d.K;
+  a.alpha = d.alpha;
+  a.beta = d.beta;
+  if (xc && mc)
+    launch_gemv<true, true>(a, st);
+  else if (xc)
+    launch_gemv<true, false>(a, st);
+  else if (mc)
+    launch_gemv<false, true>(a, st);
+  else
+    launch_gemv<false, false>(a, st);
+}
+
 }  // namespace
 
 int gemm_f64_splits(const GemmDesc& d) {
+  if (d.batch == 1 && (d.M == 1 || d.N == 1)) return 1;  // matrix-vector path
   // Split K when the output alone gives too few blocks to balance 148 SMs
   // (the FP64 pipe is the bottleneck, so only the block count matters); each
   // slice keeps at least 128 of K.
@@ -278,6 +387,11 @@ void gemm_f64(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   if ((d.M + 7) / 8 > 65535 || d.batch > 65535)
     throw Error(-1, "gemm_f64: grid too large");
+  if (d.batch == 1 && (d.M == 1 || d.N == 1)) {
+    gemv_f64(d, st);
+    RT_CHECK_LAUNCH();
+    return;
+  }
   const int splits = gemm_f64_splits(d);
   if (splits > 1 && d.work == nullptr) throw Error(-1, "gemm_f64: split-K needs a workspace");
   GemmArgs g;

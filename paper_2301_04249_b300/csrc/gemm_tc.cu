@@ -1,0 +1,569 @@
+// Split-TF32 tensor-core GEMM on tcgen05 (sm_103a) for the contraction engine.
+//
+// Every engine GEMM C = alpha op(A) op(B) + beta C (A, B real or complex
+// FP64) becomes one real GEMM D = A' B'^T:
+//   real x real        A' = A,                 B'^T = B
+//   complex x real     A' = [Re A ; Im A] (rows), B'^T = B
+//   real x complex     A' = A,                 B'^T = [Re B | Im B] (columns)
+//   complex x complex  A' = [Re A | Im A] (K),  B'^T = [[Re B, Im B], [-Im B, Re B]]
+// Each operand is packed once per call by `tc_pack` into TF32 hi/lo parts
+// (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)), laid out as 128-row x 32-col
+// tiles of 8x4 core matrices (K-major, no swizzle), each tile contiguous so a
+// stage is four 16 KB bulk copies.  The product hi*hi + hi*lo + lo*hi is
+// accumulated in FP32 in tensor memory; K may be split across CTAs.  The
+// epilogue writes FP32 slabs; `tc_finalize` sums the slabs of each output in
+// slice order (deterministic) and maps them to the FP64 (complex) output with
+// alpha and beta.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues the bulk copies, warp 1 owns
+// the tensor-memory allocation and lane 0 issues the MMAs, warps 2-5 drain
+// the accumulator (warp w reads lanes 32*(w%4)..+31).  Every mbarrier wait is
+// bounded by a clock budget; on expiry the CTA records an error code, lets its
+// copies land, frees its tensor memory and returns.
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rteom {
+
+namespace tc {
+
+constexpr int BM = 128;   // rows of A' per tile (TMEM lanes)
+constexpr int BK = 32;    // K per stage (tf32 elements, 128 bytes)
+constexpr int TILE_ELEMS = BM * BK;            // 4096 floats
+constexpr uint32_t TILE_BYTES = TILE_ELEMS * 4;  // 16 KB
+constexpr int THREADS = 192;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices adjacent along K), stride-dimension byte
+// offset (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: F32 accumulator, TF32 A and B, both
+// K-major, N = bn, M = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32(int bn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct KArgs {
+  const float *Ahi, *Alo, *Bhi, *Blo;  // packed tiles: [batch][rowtile][ktile][4096]
+  int64_t sA, sB;                      // per-batch element strides of the packed operands
+  int KT;                              // k-tiles per row tile
+  int ktiles_per_split;
+  int splits;
+  float* D;          // slabs [batch*splits][Mp][Np]
+  int Mp, Np;        // padded extents of the slab
+  uint32_t lbo, sbo;
+  int* err;          // set to a non-zero code when a wait runs out
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr uint32_t A_BYTES = TILE_BYTES;
+  constexpr uint32_t B_BYTES = (uint32_t)BN * BK * 4;
+  constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* issued = abort_flag + 1;  // bulk-load stages issued by the producer
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
+  const int z = blockIdx.z;
+  const int b = z / g.splits, sp = z % g.splits;
+  const int kt0 = sp * g.ktiles_per_split;
+  const int kt1 = min(g.KT, kt0 + g.ktiles_per_split);
+  const int nk = kt1 - kt0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    *issued = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: stage s holds Ahi, Alo, Bhi, Blo of one k-tile
+    const float* Ahi = g.Ahi + b * g.sA + (int64_t)m_tile * g.KT * TILE_ELEMS;
+    const float* Alo = g.Alo + b * g.sA + (int64_t)m_tile * g.KT * TILE_ELEMS;
+    const float* Bhi = g.Bhi + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
+    const float* Blo = g.Blo + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % STAGES;
+      if (k >= STAGES && !mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicExch(g.err, 1);
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const int kt = kt0 + k;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      bulk_load(st, Ahi + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
+      bulk_load(st + A_BYTES, Alo + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
+      bulk_load(st + 2 * A_BYTES, Bhi + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
+      bulk_load(st + 2 * A_BYTES + B_BYTES, Blo + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
+      *issued = k + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 K-steps of 8 per stage, three hi/lo products each
+    const uint32_t idesc = idesc_tf32(BN);
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % STAGES;
+      if (!mbar_wait(&full[s], (k / STAGES) & 1)) {
+        *abort_flag = 1;
+        atomicExch(g.err, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t a_hi = base, a_lo = base + A_BYTES;
+      const uint32_t b_hi = base + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+#pragma unroll
+      for (int j = 0; j < BK / 8; ++j) {
+        const uint32_t off = j * 256;  // two 16-byte core matrices along K
+        const uint64_t ah = smem_desc(a_hi + off, g.lbo, g.sbo);
+        const uint64_t al = smem_desc(a_lo + off, g.lbo, g.sbo);
+        const uint64_t bh = smem_desc(b_hi + off, g.lbo, g.sbo);
+        const uint64_t bl = smem_desc(b_lo + off, g.lbo, g.sbo);
+        mma_tf32(tmem, ah, bh, idesc, (k > 0 || j > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accum);
+  } else if (warp >= 2) {
+    // epilogue: row r of the tile lives in TMEM lane r
+    const int q = warp % 4;
+    const int row = 32 * q + lane;
+    const bool ok = nk > 0 && mbar_wait(accum, 0);
+    tc_fence_after();
+    if (!ok) {
+      if (nk > 0) atomicExch(g.err, 3);
+    } else {
+      float* Drow = g.D + ((int64_t)z * g.Mp + (int64_t)m_tile * BM + row) * g.Np +
+                    (int64_t)n_tile * BN;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32), r);
+        float4* dst = reinterpret_cast<float4*>(Drow + c * 32);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+          dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                               __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+      }
+    }
+  }
+  // teardown: if a stage was abandoned, let its copies land before exiting
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    const int n = *issued;
+    for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
+      mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, BN);
+  }
+}
+
+// ---------------------------------------------------------------- packing
+// Source element (r, c) of a logical operand matrix, read with strides.
+struct PackArgs {
+  const double* src;
+  bool cplx;
+  int64_t s_r, s_c, s_b;  // element strides of logical rows, columns, batch
+  int R, C;               // logical extents of the source operand (rows x K)
+  int mode;               // see PackMode
+  int Rp, Kp;             // packed (padded) extents: rows multiple of rowtile, K of 32
+  int rowtile;            // 128 for A', BN for B'
+  float *hi, *lo;
+  int64_t s_out;          // elements per batch entry of the packed output
+};
+
+// Packed row r' / column k' -> (source row, source column, part, sign).
+enum PackMode {
+  kPlain = 0,       // real source
+  kStackRows = 1,   // complex: rows [Re; Im]
+  kStackK = 2,      // complex: K [Re | Im]
+  kBcc = 3,         // complex B of a complex x complex product
+};
+
+__global__ void tc_pack_kernel(PackArgs p, int batch) {
+  const int64_t per = (int64_t)p.Rp * p.Kp;
+  const int KT = p.Kp / BK;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const int64_t q = e - (int64_t)b * per;
+    const int rp = (int)(q / p.Kp), kp = (int)(q % p.Kp);
+    int r = rp, c = kp, part = 0;
+    double sign = 1.0;
+    bool valid = true;
+    switch (p.mode) {
+      case kPlain:
+        valid = rp < p.R && kp < p.C;
+        break;
+      case kStackRows:
+        part = rp >= p.R;
+        r = rp - part * p.R;
+        valid = rp < 2 * p.R && kp < p.C;
+        break;
+      case kStackK:
+        part = kp >= p.C;
+        c = kp - part * p.C;
+        valid = rp < p.R && kp < 2 * p.C;
+        break;
+      default: {  // kBcc: rows n' (output columns), K' = [K | K]
+        const int ro = rp >= p.R, ko = kp >= p.C;
+        r = rp - ro * p.R;
+        c = kp - ko * p.C;
+        valid = rp < 2 * p.R && kp < 2 * p.C;
+        // [[Re, Im], [-Im, Re]] indexed by (k-half, n-half): part = Im when halves differ
+        part = ro != ko;
+        sign = (ko && !ro) ? -1.0 : 1.0;
+      }
+    }
+    double x = 0.0;
+    if (valid) {
+      const int64_t off = b * p.s_b + r * p.s_r + c * p.s_c;
+      x = p.cplx ? p.src[2 * off + part] : p.src[off];
+      x *= sign;
+    }
+    float hi = __uint_as_float(__float_as_uint(0.0f));
+    {
+      float xf = (float)x;
+      uint32_t h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(xf));
+      hi = __uint_as_float(h);
+    }
+    float lo;
+    {
+      float rf = (float)(x - (double)hi);
+      uint32_t l;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rf));
+      lo = __uint_as_float(l);
+    }
+    // tiled core-matrix layout
+    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+    const int kt = kp / BK, kk = kp % BK;
+    const int64_t dst = (int64_t)b * p.s_out + ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
+                        ((rr / 8) * 8 + kk / 4) * 32 + (rr % 8) * 4 + (kk % 4);
+    p.hi[dst] = hi;
+    p.lo[dst] = lo;
+  }
+}
+
+// ---------------------------------------------------------------- finalize
+struct FinArgs {
+  const float* D;  // [batch*splits][Mp][Np]
+  int Mp, Np, splits;
+  int M, N;        // logical output extents
+  int mode;        // 0 real, 1 stacked rows (C re/im = row halves), 2 stacked columns
+  double* C;
+  bool cplx;
+  int64_t ldc, sC;
+  double alpha, beta;
+};
+
+__global__ void tc_finalize_kernel(FinArgs f, int batch) {
+  const int64_t per = (int64_t)f.M * f.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const int64_t q = e - (int64_t)b * per;
+    const int m = (int)(q / f.N), n = (int)(q % f.N);
+    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldc + n);
+    const int parts = f.cplx ? 2 : 1;
+    for (int part = 0; part < parts; ++part) {
+      int mr = m, nr = n;
+      if (f.mode == 1) mr = m + part * f.M;
+      if (f.mode == 2) nr = n + part * f.N;
+      double s = 0.0;
+      for (int z = 0; z < f.splits; ++z)
+        s += (double)f.D[(((int64_t)b * f.splits + z) * f.Mp + mr) * f.Np + nr];
+      const double v = f.alpha * s;
+      c[part] = f.beta == 0.0 ? v : fma(f.beta, c[part], v);
+    }
+  }
+}
+
+constexpr int kBN = 128;
+constexpr int kStages = 3;
+constexpr int kMaxKtPerSplit = 16;  // FP32 partial sums over at most 512 of K
+constexpr size_t kSmemBytes = kStages * (2 * TILE_BYTES + 2 * (size_t)kBN * BK * 4) + 128;
+
+inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Plan {
+  int mode;  // 0 RR, 1 CR, 2 RC, 3 CC
+  int Mp, Np, Kp, KT, splits, kps;
+  int64_t a_elems, b_elems, d_elems;  // per operand part (hi or lo), and slabs
+};
+
+Plan plan(const GemmDesc& d) {
+  Plan p;
+  p.mode = (d.Acplx ? 1 : 0) + (d.Bcplx ? 2 : 0);
+  const int Ar = p.mode == 1 ? 2 * d.M : d.M;
+  const int Ak = p.mode == 3 ? 2 * d.K : d.K;
+  const int Br = (p.mode & 2) ? 2 * d.N : d.N;
+  p.Mp = roundup(std::max(Ar, 1), BM);
+  p.Np = roundup(std::max(Br, 1), kBN);
+  p.Kp = roundup(std::max(Ak, 1), BK);
+  p.KT = p.Kp / BK;
+  const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / kBN) * d.batch;
+  int splits = (p.KT + kMaxKtPerSplit - 1) / kMaxKtPerSplit;
+  while (tiles * splits < 148 && splits < p.KT) ++splits;
+  p.kps = (p.KT + splits - 1) / splits;
+  p.splits = (p.KT + p.kps - 1) / p.kps;  // every split owns at least one k-tile
+  p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
+  p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
+  p.d_elems = (int64_t)p.splits * p.Mp * p.Np * d.batch;
+  return p;
+}
+
+}  // namespace tc
+
+TcLayout gemm_tc_layout(const GemmDesc& d) {
+  tc::Plan p = tc::plan(d);
+  TcLayout l;
+  l.a_elems = p.a_elems;
+  l.b_elems = p.b_elems;
+  l.d_elems = p.d_elems;
+  l.padded_flops = 3LL * 2 * (int64_t)p.Mp * p.Np * p.Kp * d.batch;
+  return l;
+}
+
+void gemm_tc_init() {
+  RT_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<tc::kBN, tc::kStages>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc::kSmemBytes));
+}
+
+namespace {
+int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
+}  // namespace
+
+void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
+  using namespace tc;
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const Plan p = plan(d);
+  PackArgs pa{};
+  pa.src = d.A;
+  pa.cplx = d.Acplx;
+  pa.s_r = d.transA ? 1 : d.lda;
+  pa.s_c = d.transA ? d.lda : 1;
+  pa.s_b = d.strideA;
+  pa.R = d.M;
+  pa.C = d.K;
+  pa.mode = p.mode == 1 ? kStackRows : (p.mode == 3 ? kStackK : kPlain);
+  pa.Rp = p.Mp;
+  pa.Kp = p.Kp;
+  pa.rowtile = BM;
+  pa.hi = hi;
+  pa.lo = lo;
+  pa.s_out = (int64_t)p.Mp * p.Kp;
+  tc_pack_kernel<<<grid_of(p.a_elems), 256, 0, st>>>(pa, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
+  using namespace tc;
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const Plan p = plan(d);
+  PackArgs pb{};
+  pb.src = d.B;
+  pb.cplx = d.Bcplx;
+  pb.s_r = d.transB ? d.ldb : 1;  // rows of B' are the output columns n
+  pb.s_c = d.transB ? 1 : d.ldb;
+  pb.s_b = d.strideB;
+  pb.R = d.N;
+  pb.C = d.K;
+  pb.mode = p.mode == 2 ? kStackRows : (p.mode == 3 ? kBcc : kPlain);
+  pb.Rp = p.Np;
+  pb.Kp = p.Kp;
+  pb.rowtile = kBN;
+  pb.hi = hi;
+  pb.lo = lo;
+  pb.s_out = (int64_t)p.Np * p.Kp;
+  tc_pack_kernel<<<grid_of(p.b_elems), 256, 0, st>>>(pb, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,
+                 const float* Blo, float* D, int* err, cudaStream_t st) {
+  using namespace tc;
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const Plan p = plan(d);
+  if (p.Mp / BM > 65535 || (int64_t)d.batch * p.splits > 65535)
+    throw Error(-1, "gemm_tc: grid too large");
+  KArgs g{};
+  g.Ahi = Ahi;
+  g.Alo = Alo;
+  g.Bhi = Bhi;
+  g.Blo = Blo;
+  g.sA = (int64_t)p.Mp * p.Kp;
+  g.sB = (int64_t)p.Np * p.Kp;
+  g.KT = p.KT;
+  g.ktiles_per_split = p.kps;
+  g.splits = p.splits;
+  g.D = D;
+  g.Mp = p.Mp;
+  g.Np = p.Np;
+  g.lbo = 128;   // core matrices adjacent along K
+  g.sbo = 1024;  // 8-row groups
+  g.err = err;
+  dim3 grid(p.Np / kBN, p.Mp / BM, d.batch * p.splits);
+  tc_gemm_kernel<kBN, kStages><<<grid, THREADS, kSmemBytes, st>>>(g);
+  RT_CHECK_LAUNCH();
+}
+
+void gemm_tc_finalize(const GemmDesc& d, const float* D, cudaStream_t st) {
+  using namespace tc;
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const Plan p = plan(d);
+  FinArgs fa{};
+  fa.D = D;
+  fa.Mp = p.Mp;
+  fa.Np = p.Np;
+  fa.splits = p.splits;
+  fa.M = d.M;
+  fa.N = d.N;
+  fa.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
+  fa.C = d.C;
+  fa.cplx = d.Acplx || d.Bcplx;
+  fa.ldc = d.ldc;
+  fa.sC = d.strideC;
+  fa.alpha = d.alpha;
+  fa.beta = d.beta;
+  tc_finalize_kernel<<<grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+}  // namespace rteom

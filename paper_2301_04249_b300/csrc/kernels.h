@@ -27,6 +27,23 @@ int gemm_f64_splits(const GemmDesc& d);
 int64_t gemm_f64_workspace(const GemmDesc& d);
 void gemm_f64(const GemmDesc& d, cudaStream_t st);
 
+// Split-TF32 tensor-core GEMM (tcgen05) with the same contract as gemm_f64,
+// in four launches: pack A and pack B into TF32 hi/lo tiles (a_elems /
+// b_elems floats each part), the tcgen05 MMA kernel into FP32 slabs
+// (d_elems floats; FP32 accumulation over slices of at most 512 of K; err set
+// non-zero if a pipeline wait ran out), and the finalize that sums the slices
+// in FP64 into C with alpha/beta.  gemm_tc_init() once per process first.
+struct TcLayout {
+  int64_t a_elems, b_elems, d_elems, padded_flops;
+};
+TcLayout gemm_tc_layout(const GemmDesc& d);
+void gemm_tc_init();
+void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st);
+void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st);
+void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,
+                 const float* Blo, float* D, int* err, cudaStream_t st);
+void gemm_tc_finalize(const GemmDesc& d, const float* D, cudaStream_t st);
+
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
 // contiguous with dims out_dim[0..nd-1]; strides count elements.  A real
 // input may feed a complex output (imaginary part only scaled by beta).

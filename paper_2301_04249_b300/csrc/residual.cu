@@ -29,8 +29,10 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   auto T1 = [&](double* p) { return make_tensor(p, true, {nO, nV}); };
   auto new2 = [&]() { return A.tensor(true, {nO, nO, nV, nV}); };
   auto newc = [&](std::initializer_list<int64_t> d) { return A.tensor(true, d); };
-  auto R_ = [&](const double* p, std::initializer_list<int64_t> d) {
-    return make_tensor(const_cast<double*>(p), false, d);
+  auto R_ = [&](const double* p, std::initializer_list<int64_t> d) {  // integrals, Fock
+    Tensor t = make_tensor(const_cast<double*>(p), false, d);
+    t.constant = true;
+    return t;
   };
   auto C_ = [&](const double* p, std::initializer_list<int64_t> d) {
     return make_tensor(const_cast<double*>(p), true, d);

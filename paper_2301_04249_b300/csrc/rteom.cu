@@ -6,6 +6,7 @@
 // evaluation is one CUDA graph (captured on first use); the host reads one
 // 8-byte convergence word per micro-iteration.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -242,6 +243,8 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   double* vvvv = c->dmalloc(8ull * nV * nV * nV * nV);
   // scratch arena for set-up contractions and, later, the residual
   E.dry = true;
+  E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;  // plan the residual's scratch as it will run
+  if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
   E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
   compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
                    reinterpret_cast<double*>(uintptr_t(4096)));
@@ -249,6 +252,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   int64_t setup_need = (int64_t)nV * nV * nV * nV + 64;  // (ae|bf) before its permute
   if (setup_need > need) need = setup_need;
   E.dry = false;
+  E.tensor_cores = false;  // set-up contractions in FP64
   c->arena_doubles = need + 1024;
   c->arena_base = c->dmalloc(8ull * c->arena_doubles);
   E.arena.init(c->arena_base, c->arena_doubles);
@@ -320,10 +324,27 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   for (double* p : {c->T_N, c->R_N, c->T_K, c->R_K}) RT_CUDA(cudaMemsetAsync(p, 0, ab, st));
   ensure_hist(c, 1);
   c->maxdiff = reinterpret_cast<unsigned long long*>(c->dmalloc(64));
+  RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 64, st));
   void* hp = nullptr;
   RT_CUDA(cudaMallocHost(&hp, 64));
   c->h_maxdiff = static_cast<unsigned long long*>(hp);
   RT_CUDA(cudaStreamSynchronize(st));
+  // split precision: tensor-core contractions inside the residual only (the
+  // set-up integrals above stay FP64); pipeline timeouts land in maxdiff[1].
+  // One eager residual on T(0) packs every constant tensor-core operand once.
+  if (c->precision == RTEOM_SPLIT_TF32) {
+    gemm_tc_init();
+    E.tensor_cores = true;
+    if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
+    E.tc_err = reinterpret_cast<int*>(c->maxdiff + 1);
+    E.persistent_alloc = [c](int64_t floats) {
+      return reinterpret_cast<float*>(c->dmalloc(4ull * (floats > 0 ? floats : 1)));
+    };
+    E.tc_cache_fill = true;
+    compute_residual(E, c->op, c->T_N, c->R_N);
+    E.tc_cache_fill = false;
+    RT_CUDA(cudaStreamSynchronize(st));
+  }
 }
 
 }  // namespace
@@ -346,8 +367,8 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   if (nocc < 1 || nvir < 1 || nchol < 0) return bad(RTEOM_ERR_ARG, "need nocc >= 1, nvir >= 1, nchol >= 0");
   if (core_index < 0 || core_index >= nocc) return bad(RTEOM_ERR_ARG, "core_index outside the occupied orbitals");
   if (!eps || (nchol > 0 && !L)) return bad(RTEOM_ERR_ARG, "eps (and L when nchol > 0) must be given");
-  if (precision != RTEOM_FP64)
-    return bad(RTEOM_ERR_ARG, "only RTEOM_FP64 is available in this build");
+  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32)
+    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64 or RTEOM_SPLIT_TF32");
   if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) * (nvir + 1) * (nvir + 1) > 6.0e9)
@@ -419,8 +440,12 @@ int rteom_propagate(rteom_ctx* c, int nsteps, double dt, double tol, int max_mic
           am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], dt, c->T_N, c->R_N, tk_in,
                     c->T_K, Rk, c->maxdiff, st);
         });
-        RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
         RT_CUDA(cudaStreamSynchronize(st));
+        if (c->h_maxdiff[1] != 0)
+          return fail(c, RTEOM_ERR_CUDA,
+                      "tensor-core pipeline wait timed out (code " +
+                          std::to_string((long long)c->h_maxdiff[1]) + ")");
         double d = bits_to_double(*c->h_maxdiff);
         if (!std::isfinite(d))
           return fail(c, RTEOM_ERR_NONFINITE,
@@ -562,6 +587,7 @@ int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double
     compute_residual(c->E, c->op, c->T_K, c->R_K);
     c->E.launch(kElementwise, 0.0, [&] { unpack_amplitudes(c->g, c->R_K, tmp, c->stream); });
     RT_CUDA(cudaMemcpyAsync(R_out, tmp, ub, cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, c->stream));
     if (E_out) {
       // scalars[2..3] receive E (index n+1 = 1 of a two-entry history at scalars+0)
       energy_into(c, c->T_K, c->scalars, c->scalars, 0, 0);
@@ -570,6 +596,8 @@ int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double
     RT_CUDA(cudaStreamSynchronize(c->stream));
     c->dfree(tmp);
     if (c->E.timing) c->E.collect_timing();
+    if (c->h_maxdiff[1] != 0)
+      return fail(c, RTEOM_ERR_CUDA, "tensor-core pipeline wait timed out");
     return RTEOM_OK;
   });
 }

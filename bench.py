@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--max-micro", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 form")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=16)
     return ap.parse_args()
 
 
@@ -229,6 +231,63 @@ def split_summary(split, args, fp64_value, world, C_fp64, peaks):
     }}
 
 
+def serving_mix(n_req):
+    """Scaled core-hole request mix (seeds 4000 + r): O ~ U{4..8}, V ~ U{20..48},
+    Nchol = 4V, steps ~ U{20..80}, dt = 0.025 au."""
+    from synth import gen_problem
+    rng = np.random.default_rng(4)
+    out = []
+    for r in range(n_req):
+        O = int(rng.integers(4, 9))
+        V = int(rng.integers(20, 49))
+        steps = int(rng.integers(20, 81))
+        out.append((gen_problem(O, V, 4 * V, 4000 + r), steps))
+    return out
+
+
+def run_serving(P, precision, n_req, tol):
+    """Serve the mix with Poisson arrivals at twice the mean service rate;
+    returns latency percentiles, makespan and the serial (one at a time)
+    reference measured on the same requests."""
+    mix = serving_mix(n_req)
+    dt = 0.025
+    # serial reference: every request alone, back to back (also its service time)
+    serial = []
+    with P.Server(max_active=1, precision=precision) as s:
+        for p, n in mix:
+            t0 = time.perf_counter()
+            rid = s.submit(p, n, dt, tol=tol)
+            s.wait(rid, 600.0)
+            serial.append(time.perf_counter() - t0)
+    mean_service = float(np.mean(serial))
+    rate = 2.0 / mean_service
+    arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, n_req))
+    arrivals -= arrivals[0]
+    with P.Server(max_active=8, precision=precision) as s:
+        t0 = time.perf_counter()
+        ids = []
+        for (p, n), ta in zip(mix, arrivals):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0005)
+            ids.append(s.submit(p, n, dt, tol=tol))
+        for rid in ids:
+            s.wait(rid, 600.0)
+        makespan = time.perf_counter() - t0
+        polls = [s.poll(rid) for rid in ids]
+        st = s.stats()
+    lat = np.array([t[3][2] - t[3][0] for t in polls])
+    wait = np.array([t[3][1] - t[3][0] for t in polls])
+    steps = sum(n for _, n in mix)
+    return {"requests": n_req, "done": st["done"], "failed": st["failed"],
+            "arrival_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "p50_queue_wait_s": float(np.percentile(wait, 50)), "makespan_s": makespan,
+            "throughput_steps_per_s": steps / makespan,
+            "serial_steps_per_s": steps / float(np.sum(serial)),
+            "speedup_vs_serial": float(np.sum(serial)) / makespan,
+            "mean_service_s": mean_service}
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -337,6 +396,14 @@ def run_ours(args):
         return
 
     value = world * args.steps / elapsed
+    serving = None
+    if not args.no_serving:
+        serving = {"workload": "scaled core-hole mix: 16 requests, O~U{4..8}, V~U{20..48}, "
+                               "Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x the "
+                               "mean service rate, 8 slots",
+                   "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
+                   "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
+                                             args.tol)}
     lad = tm["ladder"]
     peaks = measured_peaks()
     dgemm = fp64_dgemm_tflops(torch, dev)
@@ -391,6 +458,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "forms": split_summary(split, args, value, world, fp64_hist, peaks),
+        "serving": serving,
         "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
     print(json.dumps(res), flush=True)

@@ -189,6 +189,77 @@ int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* fl
 /* rteom_kernel_launches -- number of kernels this context has launched. */
 long long rteom_kernel_launches(const rteom_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Continuous-batching server.  Core holes are independent (Section 3: the
+ * core-hole calculations "are unique and can run simultaneously"), so one
+ * GPU propagates many of them at once.  A scheduler thread owned by the
+ * server admits queued requests first come, first served, while a slot is
+ * free and the request's estimated device memory fits the budget; each
+ * admitted request gets its own context and stream and is advanced by
+ * non-blocking polls, so the work of different requests overlaps on the
+ * device and late arrivals join as soon as slots and memory free up.  Results
+ * are bitwise identical to a lone rteom_propagate of the same request.  A
+ * failing request (bad input, NOT_CONVERGED, ...) is isolated.
+ * The server functions are thread-safe.
+ * ------------------------------------------------------------------------- */
+#define RTEOM_REQ_QUEUED    0
+#define RTEOM_REQ_RUNNING   1
+#define RTEOM_REQ_DONE      2
+#define RTEOM_REQ_FAILED    3
+#define RTEOM_REQ_CANCELLED 4
+
+typedef struct rteom_server rteom_server;
+
+/*
+ * rteom_server_create -- start a server on the current CUDA device.
+ *  mem_budget_bytes  device memory the running requests may hold (0: 80 % of
+ *                    the free memory at creation)
+ *  max_active        slots: requests running at once (>= 1)
+ *  precision         RTEOM_FP64 or RTEOM_SPLIT_TF32 for every request
+ */
+int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_active,
+                        int precision);
+
+/*
+ * rteom_server_submit -- queue one propagation: the arguments of
+ * rteom_create and rteom_propagate (host arrays are copied; the caller may
+ * free them on return).  *request_id receives the request's id.
+ */
+int rteom_server_submit(rteom_server* s, int nocc, int nvir, int nchol, const double* eps,
+                        const double* L, const double* t1_gs, const double* t2_gs,
+                        int core_index, int flags, int nsteps, double dt, double tol,
+                        int max_micro, long long* request_id);
+
+/*
+ * rteom_server_poll -- state of a request.  status: RTEOM_REQ_*; error: the
+ * RTEOM_ERR_* code of a failed request; C_out (host, 2*(nsteps+1) doubles or
+ * NULL) receives C_0..C_nsteps once the request is DONE; times (host [3] or
+ * NULL): submit, admit and completion times in seconds since the server
+ * started (-1 when not reached).  Unknown id: RTEOM_ERR_ARG.
+ */
+int rteom_server_poll(rteom_server* s, long long id, int* status, int* error, double* C_out,
+                      double* times);
+
+/* rteom_server_wait -- block until the request is done, failed or cancelled
+ * (timeout_s <= 0: no limit); RTEOM_ERR_STATE on timeout. */
+int rteom_server_wait(rteom_server* s, long long id, double timeout_s);
+
+/* rteom_server_cancel -- cancel a queued or running request. */
+int rteom_server_cancel(rteom_server* s, long long id);
+
+/* rteom_server_stats -- queued/running/done/failed counts, device bytes held
+ * by running requests, and time steps completed by finished requests; any
+ * pointer may be NULL. */
+int rteom_server_stats(rteom_server* s, long long* queued, long long* running, long long* done,
+                       long long* failed, double* mem_in_use, double* steps_done);
+
+/* rteom_server_estimate_bytes -- the admission estimate of a request's peak
+ * device memory for this shape and precision. */
+double rteom_server_estimate_bytes(int nocc, int nvir, int nchol, int precision);
+
+/* rteom_server_destroy -- cancel what is left, stop the thread, free all. */
+void rteom_server_destroy(rteom_server* s);
+
 /*
  * rteom_ecorr_noalloc -- the closed-shell correlation energy E_N^corr that
  * rteom_create computes (sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b),

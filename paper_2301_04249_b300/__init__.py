@@ -13,9 +13,10 @@ import numpy as np
 from . import _lib
 from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: F401
                    RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_OOM, RTEOM_ERR_STATE, RTEOM_FLAG_CUMULANT_NO_FOV,
-                   RTEOM_FP64, RTEOM_OK, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32)
+                   RTEOM_FP64, RTEOM_OK, RTEOM_REQ_CANCELLED, RTEOM_REQ_DONE, RTEOM_REQ_FAILED,
+                   RTEOM_REQ_QUEUED, RTEOM_REQ_RUNNING, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32)
 
-__all__ = ["Propagator", "RteomError", "block_shapes", "split_blocks", "join_blocks"]
+__all__ = ["Propagator", "Server", "RteomError", "block_shapes", "split_blocks", "join_blocks"]
 
 
 class RteomError(RuntimeError):
@@ -162,6 +163,86 @@ class Propagator:
         if getattr(self, "_ctx", None):
             self._lib.rteom_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server (rteom_server_*): many core-hole
+    propagations at once on the current GPU, admitted by device memory."""
+
+    def __init__(self, mem_budget_bytes: float = 0.0, max_active: int = 8,
+                 precision: int = RTEOM_FP64):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = self._lib.rteom_server_create(ctypes.byref(h), float(mem_budget_bytes),
+                                           int(max_active), int(precision))
+        if rc != 0:
+            raise RteomError(rc, "rteom_server_create failed")
+        self._h = h
+        self._nsteps = {}
+
+    def submit(self, p, nsteps: int, dt: float, tol: float = 1e-4, max_micro: int = 50,
+               flags: int = 0) -> int:
+        """Queue a problem (synth.Problem-like: eps, L, nocc, nvir, t1_gs, t2_gs, core)."""
+        eps, L = _f64(p.eps), _f64(p.L)
+        t1, t2 = _f64(p.t1_gs), _f64(p.t2_gs)
+        nchol = 0 if L is None else int(L.shape[0])
+        rid = ctypes.c_longlong()
+        rc = self._lib.rteom_server_submit(self._h, int(p.nocc), int(p.nvir), nchol, _ptr(eps),
+                                           _ptr(L), _ptr(t1), _ptr(t2), int(p.core), int(flags),
+                                           int(nsteps), float(dt), float(tol), int(max_micro),
+                                           ctypes.byref(rid))
+        if rc != 0:
+            raise RteomError(rc, "rteom_server_submit failed")
+        self._nsteps[rid.value] = int(nsteps)
+        return rid.value
+
+    def poll(self, rid: int):
+        """(status, error, C or None, (t_submit, t_admit, t_done))."""
+        st, er = ctypes.c_int(), ctypes.c_int()
+        C = np.zeros(2 * (self._nsteps[rid] + 1))
+        t = np.zeros(3)
+        rc = self._lib.rteom_server_poll(self._h, int(rid), ctypes.byref(st), ctypes.byref(er),
+                                         _ptr(C), _ptr(t))
+        if rc != 0:
+            raise RteomError(rc, "unknown request")
+        return st.value, er.value, (C.view(np.complex128) if st.value == RTEOM_REQ_DONE else None), \
+            tuple(t)
+
+    def wait(self, rid: int, timeout_s: float = 0.0) -> bool:
+        return self._lib.rteom_server_wait(self._h, int(rid), float(timeout_s)) == 0
+
+    def cancel(self, rid: int):
+        self._lib.rteom_server_cancel(self._h, int(rid))
+
+    def stats(self):
+        q, r, d, f = (ctypes.c_longlong() for _ in range(4))
+        m, s = ctypes.c_double(), ctypes.c_double()
+        self._lib.rteom_server_stats(self._h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(d),
+                                     ctypes.byref(f), ctypes.byref(m), ctypes.byref(s))
+        return dict(queued=q.value, running=r.value, done=d.value, failed=f.value,
+                    mem_in_use=m.value, steps_done=s.value)
+
+    @staticmethod
+    def estimate_bytes(nocc, nvir, nchol, precision=RTEOM_FP64) -> float:
+        return float(_lib.load().rteom_server_estimate_bytes(int(nocc), int(nvir), int(nchol),
+                                                            int(precision)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rteom_server_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -18,6 +18,11 @@ RTEOM_FP64 = 0
 RTEOM_SPLIT_BF16 = 1
 RTEOM_SPLIT_TF32 = 2
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
+RTEOM_REQ_QUEUED = 0
+RTEOM_REQ_RUNNING = 1
+RTEOM_REQ_DONE = 2
+RTEOM_REQ_FAILED = 3
+RTEOM_REQ_CANCELLED = 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _llp = ctypes.POINTER(ctypes.c_longlong)
@@ -39,6 +44,19 @@ SIGNATURES = {
     "rteom_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rteom_get_timing": (ctypes.c_int, [_vp, _dp, _llp, _dp, ctypes.c_int]),
     "rteom_kernel_launches": (ctypes.c_longlong, [_vp]),
+    "rteom_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int]),
+    "rteom_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                           _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, _llp]),
+    "rteom_server_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _dp, _dp]),
+    "rteom_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_double]),
+    "rteom_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "rteom_server_stats": (ctypes.c_int, [_vp, _llp, _llp, _llp, _llp, _dp, _dp]),
+    "rteom_server_estimate_bytes": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int]),
+    "rteom_server_destroy": (None, [_vp]),
     "rteom_ecorr_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
                                            _vp, _vp, ctypes.c_char_p, ctypes.c_int]),
     "rteom_destroy": (None, [_vp]),

@@ -52,6 +52,18 @@ struct rteom_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
   std::string err;
 
+  // Non-blocking stepping (the blocking rteom_propagate and the server both
+  // drive it): phase 0 = next step not started, 1 = waiting for the status
+  // word of micro-iteration k, 2 = all requested steps done.
+  struct Run {
+    int phase = 2;
+    int target = 0, done = 0, k = 0, max_micro = 1;
+    double tol = 0.0;
+    cudaEvent_t ev = nullptr;
+  } run;
+
+  size_t bytes_allocated = 0;
+  std::vector<size_t> alloc_sizes;
   double* dmalloc(size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -62,17 +74,21 @@ struct rteom_ctx {
                   "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
     allocs.push_back(p);
+    alloc_sizes.push_back(bytes);
+    bytes_allocated += bytes;
     return static_cast<double*>(p);
   }
   void dfree(void* p) {
-    for (auto& q : allocs)
-      if (q == p) {
-        cudaFree(q);
-        q = nullptr;
+    for (size_t k = 0; k < allocs.size(); ++k)
+      if (allocs[k] == p) {
+        cudaFree(allocs[k]);
+        allocs[k] = nullptr;
+        bytes_allocated -= alloc_sizes[k];
       }
   }
   ~rteom_ctx() {
     if (stream) cudaStreamSynchronize(stream);
+    if (run.ev) cudaEventDestroy(run.ev);
     for (auto& gx : graph)
       if (gx) cudaGraphExecDestroy(gx);
     for (void* p : allocs)
@@ -349,6 +365,111 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
 
 }  // namespace
 
+// ---- non-blocking stepping (shared by rteom_propagate and the server) ------
+int rteom_internal_begin(rteom_ctx* c, int nsteps, double dt, double tol, int max_micro) {
+  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt) || !(tol > 0) || max_micro < 1)
+    return fail(c, RTEOM_ERR_ARG, "need nsteps >= 0, dt > 0, tol > 0, max_micro >= 1");
+  if (c->dt > 0 && std::fabs(dt - c->dt) > 1e-15 * std::fabs(c->dt))
+    return fail(c, RTEOM_ERR_ARG, "dt must stay the same across calls of one context");
+  return guarded(c, [&] {
+    c->dt = dt;
+    ensure_hist(c, c->steps + nsteps + 1);
+    if (!c->run.ev) RT_CUDA(cudaEventCreateWithFlags(&c->run.ev, cudaEventDisableTiming));
+    c->run.phase = nsteps > 0 ? 0 : 2;
+    c->run.target = nsteps;
+    c->run.done = 0;
+    c->run.k = 0;
+    c->run.tol = tol;
+    c->run.max_micro = max_micro;
+    return RTEOM_OK;
+  });
+}
+
+// Launch micro-iteration k of the current step (residual when k > 0, the
+// Adams-Moulton update, the status-word copy) and record the run event.
+static void launch_micro(rteom_ctx* c, int k) {
+  cudaStream_t st = c->stream;
+  if (k > 0) run_residual(c, 1);
+  RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 8, st));
+  const double* tk_in = k == 0 ? c->T_N : c->T_K;
+  const double* Rk = k == 0 ? c->R_N : c->R_K;
+  c->E.launch(kElementwise, 0.0, [&] {
+    am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], c->dt, c->T_N, c->R_N, tk_in, c->T_K,
+              Rk, c->maxdiff, st);
+  });
+  RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
+  RT_CUDA(cudaEventRecord(c->run.ev, st));
+}
+
+// Advance without blocking.  *finished: all requested steps done; *waiting:
+// the device still owes the status word of the pending micro-iteration.
+int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
+  *finished = false;
+  *waiting = 0;
+  return guarded(c, [&]() -> int {
+    auto& r = c->run;
+    if (r.phase == 2) {
+      *finished = true;
+      return RTEOM_OK;
+    }
+    if (r.phase == 0) {  // R(t_n); the first micro-iteration starts from t^(0) = t_n
+      run_residual(c, 0);
+      r.k = 0;
+      launch_micro(c, 0);
+      r.phase = 1;
+      *waiting = 1;
+      return RTEOM_OK;
+    }
+    cudaError_t q = cudaEventQuery(r.ev);
+    if (q == cudaErrorNotReady) {
+      *waiting = 1;
+      return RTEOM_OK;
+    }
+    RT_CUDA(q);
+    if (c->h_maxdiff[1] != 0) {
+      r.phase = 2;
+      return fail(c, RTEOM_ERR_CUDA,
+                  "tensor-core pipeline wait timed out (code " +
+                      std::to_string((long long)c->h_maxdiff[1]) + ")");
+    }
+    const double d = bits_to_double(c->h_maxdiff[0]);
+    if (!std::isfinite(d)) {
+      r.phase = 2;
+      return fail(c, RTEOM_ERR_NONFINITE,
+                  "amplitudes became non-finite at step " + std::to_string(c->steps));
+    }
+    if (d < r.tol) {  // converged: accept t^(k+1), cumulant step
+      cudaStream_t st = c->stream;
+      RT_CUDA(cudaMemcpyAsync(c->T_N, c->T_K, 16ull * c->g.total(), cudaMemcpyDeviceToDevice, st));
+      energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
+      c->steps += 1;
+      c->micro_total += r.k + 1;
+      r.done += 1;
+      if (r.done >= r.target) {
+        r.phase = 2;
+        *finished = true;
+      } else {
+        r.phase = 0;
+      }
+      return RTEOM_OK;
+    }
+    if (r.k + 1 >= r.max_micro) {
+      r.phase = 2;
+      return fail(c, RTEOM_ERR_NOT_CONVERGED,
+                  "micro-iterations did not reach tol at step " + std::to_string(c->steps));
+    }
+    r.k += 1;
+    launch_micro(c, r.k);
+    *waiting = 1;
+    return RTEOM_OK;
+  });
+}
+
+cudaStream_t rteom_internal_stream(rteom_ctx* c) { return c->stream; }
+double rteom_internal_device_bytes(const rteom_ctx* c) {
+  return (double)c->bytes_allocated;
+}
+
 extern "C" {
 
 int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* eps,
@@ -417,56 +538,27 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
 int rteom_propagate(rteom_ctx* c, int nsteps, double dt, double tol, int max_micro,
                     double* C_out) {
   if (!c) return RTEOM_ERR_ARG;
-  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt) || !(tol > 0) || max_micro < 1)
-    return fail(c, RTEOM_ERR_ARG, "need nsteps >= 0, dt > 0, tol > 0, max_micro >= 1");
-  if (c->dt > 0 && std::fabs(dt - c->dt) > 1e-15 * std::fabs(c->dt))
-    return fail(c, RTEOM_ERR_ARG, "dt must stay the same across calls of one context");
-  return guarded(c, [&] {
-    c->dt = dt;
-    const long long start = c->steps;
-    ensure_hist(c, start + nsteps + 1);
-    cudaStream_t st = c->stream;
-    for (int n = 0; n < nsteps; ++n) {
-      // R(t_n); the first micro-iteration starts from t^(0) = t_n
-      run_residual(c, 0);
-      bool converged = false;
-      int k = 0;
-      for (; k < max_micro; ++k) {
-        if (k > 0) run_residual(c, 1);
-        RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 8, st));
-        const double* tk_in = k == 0 ? c->T_N : c->T_K;
-        const double* Rk = k == 0 ? c->R_N : c->R_K;
-        c->E.launch(kElementwise, 0.0, [&] {
-          am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], dt, c->T_N, c->R_N, tk_in,
-                    c->T_K, Rk, c->maxdiff, st);
-        });
-        RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
-        RT_CUDA(cudaStreamSynchronize(st));
-        if (c->h_maxdiff[1] != 0)
-          return fail(c, RTEOM_ERR_CUDA,
-                      "tensor-core pipeline wait timed out (code " +
-                          std::to_string((long long)c->h_maxdiff[1]) + ")");
-        double d = bits_to_double(*c->h_maxdiff);
-        if (!std::isfinite(d))
-          return fail(c, RTEOM_ERR_NONFINITE,
-                      "amplitudes became non-finite at step " + std::to_string(c->steps));
-        if (d < tol) {
-          converged = true;
-          break;
-        }
-      }
-      if (!converged)
-        return fail(c, RTEOM_ERR_NOT_CONVERGED,
-                    "micro-iterations did not reach tol at step " + std::to_string(c->steps));
-      RT_CUDA(cudaMemcpyAsync(c->T_N, c->T_K, 16ull * c->g.total(), cudaMemcpyDeviceToDevice, st));
-      energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
-      c->steps += 1;
-      c->micro_total += k + 1;
+  const long long start = c->steps;
+  int rc = rteom_internal_begin(c, nsteps, dt, tol, max_micro);
+  if (rc != RTEOM_OK) return rc;
+  bool finished = false;
+  while (!finished) {
+    int waiting = 0;
+    rc = rteom_internal_poll(c, &finished, &waiting);
+    if (rc != RTEOM_OK) return rc;
+    if (waiting) {
+      rc = guarded(c, [&] {
+        RT_CUDA(cudaEventSynchronize(c->run.ev));
+        return RTEOM_OK;
+      });
+      if (rc != RTEOM_OK) return rc;
     }
+  }
+  return guarded(c, [&] {
     if (C_out)
       RT_CUDA(cudaMemcpyAsync(C_out, c->histC + 2 * start, 16ull * (nsteps + 1),
-                              cudaMemcpyDeviceToHost, st));
-    RT_CUDA(cudaStreamSynchronize(st));
+                              cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(cudaStreamSynchronize(c->stream));
     if (c->E.timing) c->E.collect_timing();
     return RTEOM_OK;
   });

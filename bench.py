@@ -38,6 +38,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (profiling recipe table); no tensor-core
 TF32_PER_BF16_NOMINAL = 1.1 / 2.25  # dense TF32 / dense BF16, nominal B300 figures
 MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
+LADDER_TC_PROFILE = os.path.join(HERE, "profiles", "ladder_tc_tf32_c2.txt")
 
 
 def parse_args():
@@ -160,15 +161,15 @@ def measured_peaks():
         return {}
 
 
-def ladder_traffic_per_launch():
-    """Per-launch DRAM bytes of the ladder GEMM from the committed ncu summary,
+def ladder_traffic_per_launch(profile=LADDER_PROFILE, source="gemm_f64.cu"):
+    """Per-launch DRAM bytes of a ladder kernel from its committed ncu summary,
     valid only while the kernel source is unchanged."""
-    if not os.path.exists(LADDER_PROFILE):
+    if not os.path.exists(profile):
         return None
-    src = os.path.join(HERE, "paper_2301_04249_b300", "csrc", "gemm_f64.cu")
+    src = os.path.join(HERE, "paper_2301_04249_b300", "csrc", source)
     digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     vals = {}
-    for ln in open(LADDER_PROFILE):
+    for ln in open(profile):
         if ":" in ln:
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
@@ -206,28 +207,36 @@ def split_summary(split, args, fp64_value, world, C_fp64, peaks):
     lad = tm["ladder"]
     v = world * args.steps / split["elapsed"]
     bf16 = peaks.get("bf16_tflops")
+    hbm = peaks.get("hbm_gbs")
     tf32_peak = bf16 * TF32_PER_BF16_NOMINAL if bf16 else None
     avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
     fl = lad["flops"] / max(lad["launches"], 1)
+    by = lad["bytes"] / max(lad["launches"], 1)
     ach = fl / avg_s / 1e12 if lad["launches"] else None
+    ach_gbs = by / avg_s / 1e9 if lad["launches"] else None
     n = min(len(C_fp64), len(split["C"]))
     dC = float(np.abs(np.asarray(split["C"])[:n] - np.asarray(C_fp64)[:n]).max())
-    total_tc = sum(x["flops"] for x in tm.values())
     return {"split_tf32": {
         "value": v, "unit": UNIT, "ms_per_step": 1e3 * split["elapsed"] / args.steps,
         "speedup_vs_fp64": v / fp64_value,
         "micro_iterations_per_step": split["micro"] / args.steps,
         "max_abs_dC_vs_fp64": dC,
         "gpu_launches": split["launches"],
-        "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, ladder)",
-                     "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                     "frac": ach / tf32_peak if (ach and tf32_peak) else None,
-                     "peak_source": "measured BF16 x nominal TF32/BF16 ratio (of measured)",
-                     "flops_per_launch_executed": fl, "avg_launch_ms": avg_s * 1e3,
+        "roofline": {"bound": "hbm", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, ladder)",
+                     "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": ach_gbs / hbm if (ach_gbs and hbm) else None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                     "traffic": ladder_traffic_per_launch(LADDER_TC_PROFILE, "gemm_tc.cu"),
+                     "bytes_per_launch": by, "avg_launch_ms": avg_s * 1e3,
                      "launches": lad["launches"],
-                     "note": "executed = 3 split products x 2 x M x N x K (algorithmic)"},
-        "executed_tflops_all_contractions": total_tc / split["elapsed"] / 1e12,
-        "time_by_class_ms": {k: x["ms"] for k, x in tm.items()},
+                     "tensor": {"achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                                "frac": ach / tf32_peak if (ach and tf32_peak) else None,
+                                "peak_source": "measured BF16 x nominal TF32/BF16 ratio",
+                                "flops_per_launch_executed": fl},
+                     "note": "bytes: packed hi/lo operands read once + FP32 split-K slabs; at "
+                             "this size 85 FLOP/B, below the TF32 ridge, so HBM binds; "
+                             "traffic is the alpha-beta launch (the largest), bytes_per_launch "
+                             "the mean over the three ladder launches of a residual"},
     }}
 
 

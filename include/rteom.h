@@ -178,13 +178,20 @@ int rteom_debug_residual(rteom_ctx* ctx, const double* t_in, double* R_out, doub
 /*
  * rteom_set_timing / rteom_get_timing -- per-kernel-class device timing with
  * CUDA events on the context's stream (0 = off, the default).  Classes:
- * 0 ladder contraction, 1 other contractions, 2 tensor permutes,
- * 3 elementwise/update/energy.  get_timing fills ms[4] (total milliseconds),
- * launches[4] and flops[4] (algorithmic FLOPs of the timed launches); any
- * pointer may be NULL.  reset != 0 zeroes the counters after reading.
+ * 0 ladder contraction, 1 other contractions, 2 tensor permutes (and
+ * tensor-core operand packing), 3 elementwise/update/energy.  get_timing
+ * fills ms[4] (total milliseconds), launches[4] and flops[4] (FLOPs of the
+ * launches: algorithmic for FP64 GEMMs, executed split products for
+ * tensor-core GEMMs), bytes[4] (algorithmic DRAM bytes: operands read once,
+ * outputs or split-K slabs written); any pointer may be NULL.  reset != 0
+ * zeroes the counters after reading.  Inside the captured residual graphs only the
+ * ladder launches carry event nodes, so ms[] of the other classes counts
+ * only eagerly launched work (set-up, rteom_debug_residual); launches[] and
+ * flops[] count every launch.
  */
 int rteom_set_timing(rteom_ctx* ctx, int on);
-int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* flops, int reset);
+int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* flops,
+                     double* bytes, int reset);
 
 /* rteom_kernel_launches -- number of kernels this context has launched. */
 long long rteom_kernel_launches(const rteom_ctx* ctx);

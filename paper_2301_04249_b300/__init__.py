@@ -152,9 +152,11 @@ class Propagator:
         ms = (ctypes.c_double * 4)()
         la = (ctypes.c_longlong * 4)()
         fl = (ctypes.c_double * 4)()
-        self._check(self._lib.rteom_get_timing(self._ctx, ms, la, fl, int(reset)))
+        by = (ctypes.c_double * 4)()
+        self._check(self._lib.rteom_get_timing(self._ctx, ms, la, fl, by, int(reset)))
         names = ["ladder", "contract", "permute", "elementwise"]
-        return {n: dict(ms=ms[k], launches=la[k], flops=fl[k]) for k, n in enumerate(names)}
+        return {n: dict(ms=ms[k], launches=la[k], flops=fl[k], bytes=by[k])
+                for k, n in enumerate(names)}
 
     def kernel_launches(self) -> int:
         return int(self._lib.rteom_kernel_launches(self._ctx))

@@ -99,6 +99,23 @@ void Engine::collect_timing() {
   pending_.clear();
 }
 
+bool Engine::collect_graph_timing(const std::vector<GraphPair>& pairs) {
+  for (const auto& p : pairs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&t, p.a, p.b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      graph_timing_ok = false;
+      return false;
+    }
+    ms[p.cls] += t;
+    tlaunch[p.cls] += 1;
+    tflops[p.cls] += p.flops;
+    tbytes[p.cls] += p.bytes;
+  }
+  return true;
+}
+
 void Engine::axpy(const char* spec, double alpha, const Tensor& X, double beta, const Tensor& Y) {
   Parsed p = parse(spec);
   if ((int)p.a.size() != X.nd || (int)p.c.size() != Y.nd || p.a.size() != p.c.size())
@@ -283,8 +300,14 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                  : std::string();
   if (cls == kLadder && !dry) nvtxRangePushA("rteom_ladder");
   if (!use_tc) {
-    if (int64_t w = gemm_f64_workspace(g)) g.work = arena.alloc(w);
-    launch(cls, flops, [&] { gemm_f64(g, stream); }, label);
+    const int64_t w = gemm_f64_workspace(g);
+    if (w) g.work = arena.alloc(w);
+    // operands read once, output written (or slabs written and read back)
+    const double bytes = 8.0 * ((A.cplx ? 2 : 1) * (double)Mt * Kt * Bt +
+                                (B.cplx ? 2 : 1) * (double)Kt * Nt * Bt +
+                                (C.cplx ? 2 : 1) * (double)Mt * Nt * Bt * (beta != 0.0 ? 2 : 1)) +
+                         16.0 * (double)w;
+    launch(cls, flops, [&] { gemm_f64(g, stream); }, label, bytes);
   } else {
     const TcLayout L = gemm_tc_layout(g);
     auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t elems,
@@ -313,8 +336,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     const Packed pa = operand("A", A, cA, L.a_elems, true);
     const Packed pb = operand("B", B, cB, L.b_elems, false);
     float* D = reinterpret_cast<float*>(arena.alloc((L.d_elems + 1) / 2));
+    // packed hi/lo operands read once, FP32 slabs written
+    const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 4.0 * (double)L.d_elems;
     launch(cls, 3.0 * flops,
-           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, D, tc_err, stream); }, label);
+           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, D, tc_err, stream); }, label, bytes);
     launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, D, stream); }, "tc finalize");
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);

@@ -33,11 +33,30 @@ class Engine {
   bool tc_cache_fill = false;
   std::function<float*(int64_t)> persistent_alloc;  // floats, owned by the context
 
-  // timing (eager execution only)
+  // Timing.  Eager launches are each bracketed by events.  While a residual
+  // graph is being captured (capturing == true) only launches of the class
+  // graph_timed_class get event-record nodes; their event pairs are kept in
+  // graph_pairs and read back after each replay with collect_graph_timing().
   bool timing = false;
+  bool capturing = false;
+  KernelClass graph_timed_class = kLadder;
+  struct GraphPair {
+    cudaEvent_t a, b;
+    KernelClass cls;
+    double flops, bytes;
+  };
+  std::vector<GraphPair>* graph_pairs = nullptr;  // list of the graph being captured
+  // per-class launches and FLOPs of the untimed launches of that graph
+  struct GraphTally {
+    long long launches[kNumClasses] = {0, 0, 0, 0};
+    double flops[kNumClasses] = {0, 0, 0, 0};
+    double bytes[kNumClasses] = {0, 0, 0, 0};
+  };
+  GraphTally* graph_tally = nullptr;
   double ms[kNumClasses] = {0, 0, 0, 0};
   long long tlaunch[kNumClasses] = {0, 0, 0, 0};
   double tflops[kNumClasses] = {0, 0, 0, 0};
+  double tbytes[kNumClasses] = {0, 0, 0, 0};  // algorithmic DRAM bytes of the launches
 
   ~Engine();
 
@@ -51,11 +70,32 @@ class Engine {
   // Wrap a launch: counts it and, when timing, brackets it with events.
   // `what` labels the launch in the optional trace file.
   template <class F>
-  void launch(KernelClass cls, double flops, F&& f, const std::string& what = std::string()) {
+  void launch(KernelClass cls, double flops, F&& f, const std::string& what = std::string(),
+              double bytes = 0.0) {
     if (dry) return;
     ++launches;
     if (!timing) {
       f();
+      return;
+    }
+    if (capturing) {  // event-record nodes only around the timed class
+      if (cls != graph_timed_class || !graph_pairs) {
+        if (graph_tally) {
+          graph_tally->launches[cls] += 1;
+          graph_tally->flops[cls] += flops;
+          graph_tally->bytes[cls] += bytes;
+        }
+        f();
+        return;
+      }
+      cudaEvent_t a, b;
+      RT_CUDA(cudaEventCreate(&a));
+      RT_CUDA(cudaEventCreate(&b));
+      // external records become event-record nodes of the captured graph
+      RT_CUDA(cudaEventRecordWithFlags(a, stream, cudaEventRecordExternal));
+      f();
+      RT_CUDA(cudaEventRecordWithFlags(b, stream, cudaEventRecordExternal));
+      graph_pairs->push_back({a, b, cls, flops, bytes});
       return;
     }
     cudaEvent_t a = get_event(), b = get_event();
@@ -65,11 +105,17 @@ class Engine {
     pending_.push_back({a, b, cls, flops, trace_on() ? what : std::string()});
     tlaunch[cls] += 1;
     tflops[cls] += flops;
+    tbytes[cls] += bytes;
   }
   // Synchronises and folds pending event pairs into ms[]; when the
   // environment variable RTEOM_TRACE names a file, appends one JSON line per
   // timed launch (class, label, flops, ms) to it.
   void collect_timing();
+  // After a replay of a graph captured with timing: fold its pairs in.
+  // Returns false (and clears the error) when the driver cannot time
+  // event-record nodes; the caller then times residuals eagerly instead.
+  bool collect_graph_timing(const std::vector<GraphPair>& pairs);
+  bool graph_timing_ok = true;
 
  private:
   struct Pending {

@@ -50,6 +50,10 @@ struct rteom_ctx {
   long long steps = 0, micro_total = 0;
   long long graph_kernels = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
+  bool graph_timed[2] = {false, false};            // captured with event-record nodes
+  std::vector<Engine::GraphPair> graph_pairs[2];
+  Engine::GraphTally graph_tally[2];
+  int graph_pending[2] = {0, 0};                   // replays whose timing is not yet read
   std::string err;
 
   // Non-blocking stepping (the blocking rteom_propagate and the server both
@@ -91,6 +95,11 @@ struct rteom_ctx {
     if (run.ev) cudaEventDestroy(run.ev);
     for (auto& gx : graph)
       if (gx) cudaGraphExecDestroy(gx);
+    for (auto& v : graph_pairs)
+      for (auto& pr : v) {
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
+      }
     for (void* p : allocs)
       if (p) cudaFree(p);
     if (h_maxdiff) cudaFreeHost(h_maxdiff);
@@ -133,33 +142,87 @@ double bits_to_double(unsigned long long b) {
   return d;
 }
 
+void drop_graph(rteom_ctx* c, int which) {
+  if (c->graph[which]) cudaGraphExecDestroy(c->graph[which]);
+  c->graph[which] = nullptr;
+  for (auto& pr : c->graph_pairs[which]) {
+    cudaEventDestroy(pr.a);
+    cudaEventDestroy(pr.b);
+  }
+  c->graph_pairs[which].clear();
+  c->graph_tally[which] = Engine::GraphTally();
+  c->graph_pending[which] = 0;
+}
+
+// Fold the timing of finished graph replays into the engine's counters
+// (the caller has observed that the stream passed them).
+void collect_graph_timing(rteom_ctx* c) {
+  for (int w = 0; w < 2; ++w) {
+    if (c->graph_pending[w] && c->graph_timed[w]) {
+      const auto& ty = c->graph_tally[w];
+      for (int k = 0; k < kNumClasses; ++k) {
+        c->E.tlaunch[k] += ty.launches[k];
+        c->E.tflops[k] += ty.flops[k];
+        c->E.tbytes[k] += ty.bytes[k];
+      }
+      if (!c->E.collect_graph_timing(c->graph_pairs[w])) {
+        // the driver cannot time graph event nodes: drop the timed graphs,
+        // later timed residuals run eagerly with an event pair per launch
+        c->graph_pending[w] = 0;
+        drop_graph(c, 0);
+        drop_graph(c, 1);
+        return;
+      }
+    }
+    c->graph_pending[w] = 0;
+  }
+}
+
 void run_residual(rteom_ctx* c, int which) {
   const double* t = which == 0 ? c->T_N : c->T_K;
   double* R = which == 0 ? c->R_N : c->R_K;
-  if (c->E.timing) {  // eager, so every kernel is bracketed by events
+  if (c->E.timing && !c->E.graph_timing_ok) {  // eager, every kernel bracketed by events
     compute_residual(c->E, c->op, t, R);
     return;
   }
+  if (c->graph[which] && c->graph_timed[which] != c->E.timing) drop_graph(c, which);
   if (!c->graph[which]) {
     long long before = c->E.launches;
     cudaGraph_t gr;
     RT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->E.capturing = true;
+    c->E.graph_pairs = &c->graph_pairs[which];
+    c->graph_tally[which] = Engine::GraphTally();
+    c->E.graph_tally = &c->graph_tally[which];
     try {
       compute_residual(c->E, c->op, t, R);
     } catch (...) {
+      c->E.capturing = false;
+      c->E.graph_pairs = nullptr;
+      c->E.graph_tally = nullptr;
       cudaStreamEndCapture(c->stream, &gr);
       if (gr) cudaGraphDestroy(gr);
       throw;
     }
+    c->E.capturing = false;
+    c->E.graph_pairs = nullptr;
+    c->E.graph_tally = nullptr;
     RT_CUDA(cudaStreamEndCapture(c->stream, &gr));
     cudaError_t e = cudaGraphInstantiate(&c->graph[which], gr, 0);
     cudaGraphDestroy(gr);
     RT_CUDA(e);
+    c->graph_timed[which] = c->E.timing;
     c->graph_kernels = c->E.launches - before;
     c->E.launches = before;
   }
+  // a replay overwrites the graph's events: read the previous replay first
+  if (c->graph_pending[which] && c->graph_timed[which]) {
+    RT_CUDA(cudaStreamSynchronize(c->stream));
+    collect_graph_timing(c);
+  }
   RT_CUDA(cudaGraphLaunch(c->graph[which], c->stream));
   c->E.launches += c->graph_kernels;
+  c->graph_pending[which] = 1;
 }
 
 void ensure_hist(rteom_ctx* c, long long need) {
@@ -426,6 +489,7 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
       return RTEOM_OK;
     }
     RT_CUDA(q);
+    if (c->E.timing) collect_graph_timing(c);  // the stream passed every pending replay
     if (c->h_maxdiff[1] != 0) {
       r.phase = 2;
       return fail(c, RTEOM_ERR_CUDA,
@@ -700,7 +764,8 @@ int rteom_set_timing(rteom_ctx* c, int on) {
   return RTEOM_OK;
 }
 
-int rteom_get_timing(rteom_ctx* c, double* ms, long long* launches, double* flops, int reset) {
+int rteom_get_timing(rteom_ctx* c, double* ms, long long* launches, double* flops, double* bytes,
+                     int reset) {
   if (!c) return RTEOM_ERR_ARG;
   return guarded(c, [&] {
     c->E.collect_timing();
@@ -708,10 +773,12 @@ int rteom_get_timing(rteom_ctx* c, double* ms, long long* launches, double* flop
       if (ms) ms[k] = c->E.ms[k];
       if (launches) launches[k] = c->E.tlaunch[k];
       if (flops) flops[k] = c->E.tflops[k];
+      if (bytes) bytes[k] = c->E.tbytes[k];
       if (reset) {
         c->E.ms[k] = 0;
         c->E.tlaunch[k] = 0;
         c->E.tflops[k] = 0;
+        c->E.tbytes[k] = 0;
       }
     }
     return RTEOM_OK;

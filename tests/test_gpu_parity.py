@@ -197,7 +197,9 @@ def test_bad_calls_return_errors():
         assert e.value.code == P.RTEOM_ERR_NONFINITE
 
 
-def test_graph_and_eager_paths_agree_bitwise():
+def test_timed_and_untimed_graphs_agree_bitwise():
+    """Timing adds event-record nodes around the ladder GEMMs of the captured
+    residual graphs; results must not change."""
     p = gen_problem(4, 15, 20, 61)
     with _ctx(p) as g:
         C1 = g.propagate(5, 0.05, tol=1e-12)

@@ -335,12 +335,14 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     };
     const Packed pa = operand("A", A, cA, L.a_elems, true);
     const Packed pb = operand("B", B, cB, L.b_elems, false);
-    float* D = reinterpret_cast<float*>(arena.alloc((L.d_elems + 1) / 2));
+    float* D = L.d_elems ? reinterpret_cast<float*>(arena.alloc((L.d_elems + 1) / 2)) : nullptr;
     // packed hi/lo operands read once, FP32 slabs written
-    const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 4.0 * (double)L.d_elems;
+    const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 4.0 * (double)L.d_elems +
+                         (L.splits == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
     launch(cls, 3.0 * flops,
            [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, D, tc_err, stream); }, label, bytes);
-    launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, D, stream); }, "tc finalize");
+    if (L.splits > 1)
+      launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, D, stream); }, "tc finalize");
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();

@@ -277,16 +277,33 @@ struct GemvArgs {
   double alpha, beta;
 };
 
+// Contiguous outputs: a block covers 32 outputs x 8 K-groups; group g sums
+// k = g, g+8, ... and the 8 partials are added in group order.
 template <bool XC, bool MC>
-__global__ void gemv_thread_kernel(GemvArgs a) {
+__global__ void __launch_bounds__(256) gemv_thread_kernel(GemvArgs a) {
   constexpr bool YC = XC || MC;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n) return;
+  __shared__ double sre[8][32], sim[8][32];
+  const int lane = threadIdx.x % 32, grp = threadIdx.x / 32;
+  const int j = blockIdx.x * 32 + lane;
   double re = 0.0, im = 0.0;
-  for (int k = 0; k < a.K; ++k) cmad<XC, MC>(re, im, a.x, k * a.sx, a.m, k * a.sk + j * a.sj);
-  double* y = a.y + (YC ? 2 : 1) * (int64_t)j * a.sy;
-  y[0] = a.beta == 0.0 ? a.alpha * re : fma(a.beta, y[0], a.alpha * re);
-  if (YC) y[1] = a.beta == 0.0 ? a.alpha * im : fma(a.beta, y[1], a.alpha * im);
+  if (j < a.n)
+    for (int k = grp; k < a.K; k += 8)
+      cmad<XC, MC>(re, im, a.x, k * a.sx, a.m, k * a.sk + j * a.sj);
+  sre[grp][lane] = re;
+  sim[grp][lane] = im;
+  __syncthreads();
+  if (grp == 0 && j < a.n) {
+    re = 0.0;
+    im = 0.0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      re += sre[g][lane];
+      im += sim[g][lane];
+    }
+    double* y = a.y + (YC ? 2 : 1) * (int64_t)j * a.sy;
+    y[0] = a.beta == 0.0 ? a.alpha * re : fma(a.beta, y[0], a.alpha * re);
+    if (YC) y[1] = a.beta == 0.0 ? a.alpha * im : fma(a.beta, y[1], a.alpha * im);
+  }
 }
 
 template <bool XC, bool MC>
@@ -313,7 +330,7 @@ __global__ void gemv_warp_kernel(GemvArgs a) {
 template <bool XC, bool MC>
 void launch_gemv(const GemvArgs& a, cudaStream_t st) {
   if (a.sj == 1) {
-    gemv_thread_kernel<XC, MC><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+    gemv_thread_kernel<XC, MC><<<(a.n + 31) / 32, 256, 0, st>>>(a);
   } else {
     gemv_warp_kernel<XC, MC><<<(a.n + 7) / 8, 256, 0, st>>>(a);
   }

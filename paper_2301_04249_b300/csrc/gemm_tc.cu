@@ -165,6 +165,14 @@ struct KArgs {
   int Mp, Np;        // padded extents of the slab
   uint32_t lbo, sbo;
   int* err;          // set to a non-zero code when a wait runs out
+  // direct epilogue (single K slice): write alpha*acc + beta*C into the FP64
+  // output instead of FP32 slabs
+  int direct;
+  double* C;
+  bool cplx;
+  int M, N, mode;    // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
+  int64_t ldc, sC;
+  double alpha, beta;
 };
 
 template <int BN, int STAGES>
@@ -263,6 +271,34 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
     tc_fence_after();
     if (!ok) {
       if (nk > 0) atomicExch(g.err, 3);
+    } else if (g.direct) {
+      // map (row', col') of D = A'B'^T onto one real or imaginary part of C
+      const int mr = m_tile * BM + row;
+      int m = mr, part = 0;
+      if (g.mode == 1 && mr >= g.M) {
+        m = mr - g.M;
+        part = 1;
+      }
+      const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32), r);
+        if (!row_ok) continue;
+#pragma unroll 4
+        for (int v = 0; v < 32; ++v) {
+          const int nr = n_tile * BN + c * 32 + v;
+          int n = nr, pt = part;
+          if (g.mode == 2 && nr >= g.N) {
+            n = nr - g.N;
+            pt = 1;
+          }
+          if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
+          double* cp = g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldc + n) + pt;
+          const double val = g.alpha * (double)__uint_as_float(r[v]);
+          *cp = g.beta == 0.0 ? val : fma(g.beta, *cp, val);
+        }
+      }
     } else {
       float* Drow = g.D + ((int64_t)z * g.Mp + (int64_t)m_tile * BM + row) * g.Np +
                     (int64_t)n_tile * BN;
@@ -455,7 +491,8 @@ TcLayout gemm_tc_layout(const GemmDesc& d) {
   TcLayout l;
   l.a_elems = p.a_elems;
   l.b_elems = p.b_elems;
-  l.d_elems = p.d_elems;
+  l.d_elems = p.splits == 1 ? 0 : p.d_elems;  // single slice: direct epilogue, no slabs
+  l.splits = p.splits;
   l.padded_flops = 3LL * 2 * (int64_t)p.Mp * p.Np * p.Kp * d.batch;
   return l;
 }
@@ -539,6 +576,16 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.lbo = 128;   // core matrices adjacent along K
   g.sbo = 1024;  // 8-row groups
   g.err = err;
+  g.direct = p.splits == 1;
+  g.C = d.C;
+  g.cplx = d.Acplx || d.Bcplx;
+  g.M = d.M;
+  g.N = d.N;
+  g.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
+  g.ldc = d.ldc;
+  g.sC = d.strideC;
+  g.alpha = d.alpha;
+  g.beta = d.beta;
   dim3 grid(p.Np / kBN, p.Mp / BM, d.batch * p.splits);
   tc_gemm_kernel<kBN, kStages><<<grid, THREADS, kSmemBytes, st>>>(g);
   RT_CHECK_LAUNCH();
@@ -548,6 +595,7 @@ void gemm_tc_finalize(const GemmDesc& d, const float* D, cudaStream_t st) {
   using namespace tc;
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const Plan p = plan(d);
+  if (p.splits == 1) return;  // the MMA kernel wrote C directly
   FinArgs fa{};
   fa.D = D;
   fa.Mp = p.Mp;

@@ -35,6 +35,7 @@ void gemm_f64(const GemmDesc& d, cudaStream_t st);
 // in FP64 into C with alpha/beta.  gemm_tc_init() once per process first.
 struct TcLayout {
   int64_t a_elems, b_elems, d_elems, padded_flops;
+  int splits;  // K slices; 1 = the MMA kernel writes C directly (finalize is a no-op)
 };
 TcLayout gemm_tc_layout(const GemmDesc& d);
 void gemm_tc_init();
@@ -60,6 +61,11 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
 // (t2 may be null when c1 == 0); all complex.
 void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, const double* y,
                   double c2, double c3, int nO, int nV, cudaStream_t st);
+
+// R[i,j,a,b] += c0*X[i,j,a,b] + c1*X[j,i,a,b] + c2*X[i,j,b,a] + c3*X[j,i,b,a]
+// (complex [nO][nO][nV][nV]; the permutation operators P(ij), P(ab)).
+void antisym_add(double* R, const double* X, double c0, double c1, double c2, double c3, int nO,
+                 int nV, cudaStream_t st);
 
 // Antisymmetric pair packing of same-spin blocks.  Pairs are listed as
 // (p < q) in row-major order: pair index k <-> (p, q), npair = n(n-1)/2.

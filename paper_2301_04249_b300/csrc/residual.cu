@@ -42,6 +42,11 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   auto axpy = [&](const char* s, double a, const Tensor& X, double b, const Tensor& Y) {
     E.axpy(s, a, X, b, Y);
   };
+  // R += c0 X + c1 P_ij X + c2 P_ab X + c3 P_ij P_ab X (one pass)
+  auto asym = [&](const Tensor& R, const Tensor& X, double c0, double c1, double c2, double c3) {
+    E.launch(kPermute, 0.0,
+             [&] { antisym_add(R.p, X.p, c0, c1, c2, c3, nO, nV, E.stream); }, "antisym");
+  };
   auto t2t1 = [&](const Tensor& out, const Tensor* t2, double c1, const Tensor& x,
                   const Tensor& y, double c2, double c3) {
     E.launch(kElementwise, 0.0, [&] {
@@ -218,11 +223,9 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     axpy("ibja->ijab", -1.0, ovov, 1.0, R);
     Tensor x = new2();
     ein("ijae,be->ijab", 1.0, t2ss[s], Fvv[s], 0.0, x);
-    axpy("ijab->ijab", 1.0, x, 1.0, R);
-    axpy("ijba->ijab", -1.0, x, 1.0, R);
+    asym(R, x, 1.0, 0.0, -1.0, 0.0);
     ein("imab,mj->ijab", 1.0, t2ss[s], Foo[s], 0.0, x);
-    axpy("ijab->ijab", -1.0, x, 1.0, R);
-    axpy("jiab->ijab", 1.0, x, 1.0, R);
+    asym(R, x, -1.0, 1.0, 0.0, 0.0);
     ein("mnab,mnij->ijab", 0.5, tau_ss[s], Wss[s], 1.0, R);
     // ladder over antisymmetric pairs: sum_{e<f} tau_ij^ef [(ae|bf) - (af|be)]
     // for i<j, a<b, scattered to the four (i,j,a,b) sign patterns
@@ -240,8 +243,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     Tensor Z = newc({nO, nO, nV, nO});
     ein("ijef,mfae->ijam", 1.0, tau_ss[s], ovvv, 0.0, Z);
     ein("mb,ijam->ijab", 1.0, t1[s], Z, 0.0, x);
-    axpy("ijab->ijab", -1.0, x, 1.0, R);
-    axpy("ijba->ijab", 1.0, x, 1.0, R);
+    asym(R, x, -1.0, 0.0, 1.0, 0.0);
     // ring: P(ij)P(ab) [t_im^ae W_mbej - t_i^e t_m^a <mb||ej>]
     ein("imae,mbej->ijab", 1.0, t2ss[s], Wsame[s], 0.0, x);
     ein("imae,mbej->ijab", 1.0, t2su[s], Wx[s], 1.0, x);
@@ -249,20 +251,15 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     ein("ie,mejb->imbj", 1.0, t1[s], ovov, 0.0, Q);
     ein("ie,mjbe->imbj", -1.0, t1[s], oovv, 1.0, Q);
     ein("ma,imbj->ijab", -1.0, t1[s], Q, 1.0, x);
-    axpy("ijab->ijab", 1.0, x, 1.0, R);
-    axpy("jiab->ijab", -1.0, x, 1.0, R);
-    axpy("ijba->ijab", -1.0, x, 1.0, R);
-    axpy("jiba->ijab", 1.0, x, 1.0, R);
+    asym(R, x, 1.0, -1.0, -1.0, 1.0);
     // P(ij) t_i^e <ab||ej>
     ein("ie,jbae->ijab", 1.0, t1[s], ovvv, 0.0, x);
     ein("ie,jabe->ijab", -1.0, t1[s], ovvv, 1.0, x);
-    axpy("ijab->ijab", 1.0, x, 1.0, R);
-    axpy("jiab->ijab", -1.0, x, 1.0, R);
+    asym(R, x, 1.0, -1.0, 0.0, 0.0);
     // -P(ab) t_m^a <mb||ij>
     ein("ma,mijb->ijab", 1.0, t1[s], ooov, 0.0, x);
     ein("ma,mjib->ijab", -1.0, t1[s], ooov, 1.0, x);
-    axpy("ijab->ijab", -1.0, x, 1.0, R);
-    axpy("ijba->ijab", 1.0, x, 1.0, R);
+    asym(R, x, -1.0, 0.0, 1.0, 0.0);
   }
 
   // ---- T2 projection, alpha-beta (Eq. 8)

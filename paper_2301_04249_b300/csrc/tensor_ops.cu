@@ -93,6 +93,44 @@ __global__ void t2_t1t1_kernel(double2* __restrict__ out, const double2* __restr
   }
 }
 
+// ---------------------------------------------------------------- P(ij), P(ab)
+__global__ void antisym_add_kernel(double2* __restrict__ R, const double2* __restrict__ X,
+                                   double c0, double c1, double c2, double c3, int nO, int nV) {
+  const int64_t n = (int64_t)nO * nO * nV * nV;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = e % nV;
+    const int a = (e / nV) % nV;
+    const int j = (e / ((int64_t)nV * nV)) % nO;
+    const int i = e / ((int64_t)nV * nV * nO);
+    auto at = [&](int p, int q, int r, int s) {
+      return X[(((int64_t)p * nO + q) * nV + r) * nV + s];
+    };
+    double2 acc = R[e];
+    if (c0 != 0.0) {
+      const double2 v = at(i, j, a, b);
+      acc.x = fma(c0, v.x, acc.x);
+      acc.y = fma(c0, v.y, acc.y);
+    }
+    if (c1 != 0.0) {
+      const double2 v = at(j, i, a, b);
+      acc.x = fma(c1, v.x, acc.x);
+      acc.y = fma(c1, v.y, acc.y);
+    }
+    if (c2 != 0.0) {
+      const double2 v = at(i, j, b, a);
+      acc.x = fma(c2, v.x, acc.x);
+      acc.y = fma(c2, v.y, acc.y);
+    }
+    if (c3 != 0.0) {
+      const double2 v = at(j, i, b, a);
+      acc.x = fma(c3, v.x, acc.x);
+      acc.y = fma(c3, v.y, acc.y);
+    }
+    R[e] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- antisymmetric pairs
 // Pair k of n items in the order (0,1),(0,2),...,(0,n-1),(1,2),...: row p
 // starts at p*(2n-p-1)/2.  Decoded with a short scan (n is small).
@@ -573,6 +611,16 @@ void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, con
   t2_t1t1_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
       reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(t2), c1,
       reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(y), c2, c3, nO, nV);
+  RT_CHECK_LAUNCH();
+}
+
+void antisym_add(double* R, const double* X, double c0, double c1, double c2, double c3, int nO,
+                 int nV, cudaStream_t st) {
+  int64_t n = (int64_t)nO * nO * nV * nV;
+  if (n == 0) return;
+  antisym_add_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(reinterpret_cast<double2*>(R),
+                                                            reinterpret_cast<const double2*>(X),
+                                                            c0, c1, c2, c3, nO, nV);
   RT_CHECK_LAUNCH();
 }
 

@@ -31,6 +31,56 @@ struct Error : std::runtime_error {
 
 constexpr int kMaxDims = 6;
 
+// IEEE-754 binary32 <-> binary64 conversions on the integer ALUs.  The FP64
+// pipe of this part issues about two operations per clock per SM, so the
+// elementwise kernels keep FP64 arithmetic to what the result needs and
+// convert with bit operations instead.  Both are exact for normal numbers
+// and zeros (f64_to_f32 rounds to nearest, ties to even); magnitudes below
+// the normal binary32 range become signed zeros, larger ones infinities,
+// NaN stays NaN.
+#ifdef __CUDACC__
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t man = (uint64_t)(u & 0x7FFFFFu) << 29;
+  const uint64_t ex = e == 0xFFu ? 0x7FFull : (uint64_t)(e + 896u);
+  return __longlong_as_double(e == 0u ? (long long)sign : (long long)(sign | (ex << 52) | man));
+}
+
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const uint64_t m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  int E = e - 896;
+  if (E <= 0) return __uint_as_float(sign);
+  uint32_t m23 = (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ++m23;
+  if (m23 == 0x800000u) {
+    m23 = 0;
+    ++E;
+  }
+  if (E >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((uint32_t)E << 23) | m23);
+}
+
+__device__ __forceinline__ double neg_f64(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// Compensated FP32 accumulation (Knuth's TwoSum): s + c carries the running
+// sum to about twice the FP32 precision.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+#endif
+
 // Row-major device tensor, FP64 real or complex128 (interleaved re, im).
 struct Tensor {
   double* p = nullptr;

@@ -335,14 +335,15 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     };
     const Packed pa = operand("A", A, cA, L.a_elems, true);
     const Packed pb = operand("B", B, cB, L.b_elems, false);
-    float* D = L.d_elems ? reinterpret_cast<float*>(arena.alloc((L.d_elems + 1) / 2)) : nullptr;
-    // packed hi/lo operands read once, FP32 slabs written
-    const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 4.0 * (double)L.d_elems +
-                         (L.splits == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
+    float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
+    // packed hi/lo operands read once; partial pairs written (and read back
+    // by the finalize) or the output written directly
+    const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 8.0 * (double)L.p_elems +
+                         (L.ranges == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
     launch(cls, 3.0 * flops,
-           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, D, tc_err, stream); }, label, bytes);
-    if (L.splits > 1)
-      launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, D, stream); }, "tc finalize");
+           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, P, tc_err, stream); }, label, bytes);
+    if (L.ranges > 1)
+      launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, P, stream); }, "tc finalize");
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();

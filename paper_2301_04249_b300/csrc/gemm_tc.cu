@@ -10,16 +10,22 @@
 // (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)), laid out as 128-row x 32-col
 // tiles of 8x4 core matrices (K-major, no swizzle), each tile contiguous so a
 // stage is four 16 KB bulk copies.  The product hi*hi + hi*lo + lo*hi is
-// accumulated in FP32 in tensor memory; K may be split across CTAs.  The
-// epilogue writes FP32 slabs; `tc_finalize` sums the slabs of each output in
-// slice order (deterministic) and maps them to the FP64 (complex) output with
-// alpha and beta.
+// accumulated in FP32 in tensor memory over slices of at most 512 of K; the
+// epilogue warps add every slice into compensated FP32 pairs (TwoSum, about
+// 48 bits) while the next slice accumulates in the other half of the tensor
+// memory.  A CTA owns one output tile and a contiguous range of K; with one
+// range it writes alpha*acc + beta*C straight into the FP64 (complex)
+// output, otherwise it writes its (sum, compensation) pair and `tc_finalize`
+// combines the ranges in order (deterministic).  The FP64 pipe of this part
+// is slow, so conversions use integer bit operations and FP64 arithmetic is
+// spent only on a general alpha and a non-zero beta.
 //
-// Warp roles (192 threads): warp 0 lane 0 issues the bulk copies, warp 1 owns
-// the tensor-memory allocation and lane 0 issues the MMAs, warps 2-5 drain
-// the accumulator (warp w reads lanes 32*(w%4)..+31).  Every mbarrier wait is
-// bounded by a clock budget; on expiry the CTA records an error code, lets its
-// copies land, frees its tensor memory and returns.
+// Warp roles (320 threads): warp 0 lane 0 issues the bulk copies, warp 1 owns
+// the tensor-memory allocation and lane 0 issues the MMAs, warps 2-9 drain
+// the accumulator (warp w reads lanes 32*(w%4)..+31, half (w-2)/4 of the
+// columns).  Every mbarrier wait is bounded by a clock budget; on expiry the
+// CTA records an error code, lets its copies land, frees its tensor memory
+// and returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -34,7 +40,9 @@ constexpr int BM = 128;   // rows of A' per tile (TMEM lanes)
 constexpr int BK = 32;    // K per stage (tf32 elements, 128 bytes)
 constexpr int TILE_ELEMS = BM * BK;            // 4096 floats
 constexpr uint32_t TILE_BYTES = TILE_ELEMS * 4;  // 16 KB
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int kSliceKt = 16;  // k-tiles per FP32 accumulation slice (512 of K)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -71,6 +79,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
@@ -159,15 +171,13 @@ struct KArgs {
   const float *Ahi, *Alo, *Bhi, *Blo;  // packed tiles: [batch][rowtile][ktile][4096]
   int64_t sA, sB;                      // per-batch element strides of the packed operands
   int KT;                              // k-tiles per row tile
-  int ktiles_per_split;
-  int splits;
-  float* D;          // slabs [batch*splits][Mp][Np]
-  int Mp, Np;        // padded extents of the slab
+  int kpr;                             // k-tiles per K range
+  int ranges;                          // K ranges (CTAs along K per tile)
+  float2* P;         // (sum, compensation) partials [batch*ranges][Mp][Np] when ranges > 1
+  int Mp, Np;        // padded extents of the partials
   uint32_t lbo, sbo;
   int* err;          // set to a non-zero code when a wait runs out
-  // direct epilogue (single K slice): write alpha*acc + beta*C into the FP64
-  // output instead of FP32 slabs
-  int direct;
+  // output (single range): alpha*acc + beta*C into the FP64 output
   double* C;
   bool cplx;
   int M, N, mode;    // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
@@ -181,32 +191,38 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
   constexpr uint32_t A_BYTES = TILE_BYTES;
   constexpr uint32_t B_BYTES = (uint32_t)BN * BK * 4;
   constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int HALF = BN / 2;  // columns drained by one epilogue warp
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* acc_full = empty + STAGES;  // [2]: slice accumulated in buffer i
+  uint64_t* acc_empty = acc_full + 2;   // [2]: buffer i drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* issued = abort_flag + 1;  // bulk-load stages issued by the producer
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y;
   const int z = blockIdx.z;
-  const int b = z / g.splits, sp = z % g.splits;
-  const int kt0 = sp * g.ktiles_per_split;
-  const int kt1 = min(g.KT, kt0 + g.ktiles_per_split);
-  const int nk = kt1 - kt0;
+  const int b = z / g.ranges, rg = z % g.ranges;
+  const int kt0 = rg * g.kpr;
+  const int kt1 = min(g.KT, kt0 + g.kpr);
+  const int nk = max(kt1 - kt0, 0);
+  const int nslices = (nk + kSliceKt - 1) / kSliceKt;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], EPI_WARPS);
+    }
     *abort_flag = 0;
     *issued = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(tmem_slot, BN);
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -236,9 +252,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
       *issued = k + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: 4 K-steps of 8 per stage, three hi/lo products each
+    // MMA issuer: 4 K-steps of 8 per stage, three hi/lo products each; slice
+    // j accumulates in tensor-memory buffer j % 2
     const uint32_t idesc = idesc_tf32(BN);
     for (int k = 0; k < nk; ++k) {
+      const int j = k / kSliceKt, kin = k % kSliceKt, buf = j & 1;
+      if (kin == 0 && j >= 2) {
+        if (!mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1)) {
+          *abort_flag = 1;
+          atomicExch(g.err, 4);
+          break;
+        }
+      }
       const int s = k % STAGES;
       if (!mbar_wait(&full[s], (k / STAGES) & 1)) {
         *abort_flag = 1;
@@ -246,32 +271,56 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
         break;
       }
       tc_fence_after();
+      const uint32_t dt = tmem + (uint32_t)(buf * BN);
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
       const uint32_t a_hi = base, a_lo = base + A_BYTES;
       const uint32_t b_hi = base + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
-      for (int j = 0; j < BK / 8; ++j) {
-        const uint32_t off = j * 256;  // two 16-byte core matrices along K
+      for (int q = 0; q < BK / 8; ++q) {
+        const uint32_t off = q * 256;  // two 16-byte core matrices along K
         const uint64_t ah = smem_desc(a_hi + off, g.lbo, g.sbo);
         const uint64_t al = smem_desc(a_lo + off, g.lbo, g.sbo);
         const uint64_t bh = smem_desc(b_hi + off, g.lbo, g.sbo);
         const uint64_t bl = smem_desc(b_lo + off, g.lbo, g.sbo);
-        mma_tf32(tmem, ah, bh, idesc, (k > 0 || j > 0) ? 1u : 0u);
-        mma_tf32(tmem, ah, bl, idesc, 1u);
-        mma_tf32(tmem, al, bh, idesc, 1u);
+        mma_tf32(dt, ah, bh, idesc, (kin > 0 || q > 0) ? 1u : 0u);
+        mma_tf32(dt, ah, bl, idesc, 1u);
+        mma_tf32(dt, al, bh, idesc, 1u);
       }
       mma_commit(&empty[s]);
+      if (kin == kSliceKt - 1 || k == nk - 1) mma_commit(&acc_full[buf]);
     }
-    mma_commit(accum);
   } else if (warp >= 2) {
-    // epilogue: row r of the tile lives in TMEM lane r
+    // epilogue: row r of the tile lives in TMEM lane r; this warp adds the
+    // columns [h*HALF, (h+1)*HALF) of every slice into compensated pairs
     const int q = warp % 4;
+    const int h = (warp - 2) / 4;
     const int row = 32 * q + lane;
-    const bool ok = nk > 0 && mbar_wait(accum, 0);
-    tc_fence_after();
-    if (!ok) {
-      if (nk > 0) atomicExch(g.err, 3);
-    } else if (g.direct) {
+    float sum[HALF], cmp[HALF];
+#pragma unroll
+    for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
+    bool ok = nk > 0;
+#pragma unroll 1
+    for (int j = 0; j < nslices; ++j) {
+      const int buf = j & 1;
+      if (!mbar_wait(&acc_full[buf], (j >> 1) & 1)) {
+        ok = false;
+        atomicExch(g.err, 3);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + h * HALF);
+#pragma unroll
+      for (int c = 0; c < HALF / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(taddr + (uint32_t)(c * 32), r);
+#pragma unroll
+        for (int v = 0; v < 32; ++v) two_sum_acc(sum[c * 32 + v], cmp[c * 32 + v], __uint_as_float(r[v]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    if (ok && g.ranges == 1) {
       // map (row', col') of D = A'B'^T onto one real or imaginary part of C
       const int mr = m_tile * BM + row;
       int m = mr, part = 0;
@@ -280,14 +329,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
         part = 1;
       }
       const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32), r);
-        if (!row_ok) continue;
-#pragma unroll 4
-        for (int v = 0; v < 32; ++v) {
-          const int nr = n_tile * BN + c * 32 + v;
+      const bool unit = g.alpha == 1.0 || g.alpha == -1.0;
+      const float sgn = g.alpha == -1.0 ? -1.0f : 1.0f;
+      if (row_ok) {
+#pragma unroll
+        for (int v = 0; v < HALF; ++v) {
+          const int nr = n_tile * BN + h * HALF + v;
           int n = nr, pt = part;
           if (g.mode == 2 && nr >= g.N) {
             n = nr - g.N;
@@ -295,23 +342,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
           }
           if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
           double* cp = g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldc + n) + pt;
-          const double val = g.alpha * (double)__uint_as_float(r[v]);
-          *cp = g.beta == 0.0 ? val : fma(g.beta, *cp, val);
+          const float f = sum[v] + cmp[v];
+          const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
+          *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
         }
       }
-    } else {
-      float* Drow = g.D + ((int64_t)z * g.Mp + (int64_t)m_tile * BM + row) * g.Np +
-                    (int64_t)n_tile * BN;
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32), r);
-        float4* dst = reinterpret_cast<float4*>(Drow + c * 32);
+    } else if (ok) {
+      float4* dst = reinterpret_cast<float4*>(
+          g.P + ((int64_t)z * g.Mp + (int64_t)m_tile * BM + row) * g.Np +
+          (int64_t)n_tile * BN + h * HALF);
 #pragma unroll
-        for (int v = 0; v < 8; ++v)
-          dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                               __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
-      }
+      for (int v = 0; v < HALF / 2; ++v)
+        dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
     }
   }
   // teardown: if a stage was abandoned, let its copies land before exiting
@@ -325,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -360,7 +402,7 @@ __global__ void tc_pack_kernel(PackArgs p, int batch) {
     const int64_t q = e - (int64_t)b * per;
     const int rp = (int)(q / p.Kp), kp = (int)(q % p.Kp);
     int r = rp, c = kp, part = 0;
-    double sign = 1.0;
+    bool neg = false;
     bool valid = true;
     switch (p.mode) {
       case kPlain:
@@ -383,29 +425,21 @@ __global__ void tc_pack_kernel(PackArgs p, int batch) {
         valid = rp < 2 * p.R && kp < 2 * p.C;
         // [[Re, Im], [-Im, Re]] indexed by (k-half, n-half): part = Im when halves differ
         part = ro != ko;
-        sign = (ko && !ro) ? -1.0 : 1.0;
+        neg = ko && !ro;
       }
     }
-    double x = 0.0;
+    float xf = 0.0f;
     if (valid) {
       const int64_t off = b * p.s_b + r * p.s_r + c * p.s_c;
-      x = p.cplx ? p.src[2 * off + part] : p.src[off];
-      x *= sign;
+      xf = f64_to_f32(p.cplx ? p.src[2 * off + part] : p.src[off]);
+      if (neg) xf = -xf;
     }
-    float hi = __uint_as_float(__float_as_uint(0.0f));
-    {
-      float xf = (float)x;
-      uint32_t h;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(xf));
-      hi = __uint_as_float(h);
-    }
-    float lo;
-    {
-      float rf = (float)(x - (double)hi);
-      uint32_t l;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rf));
-      lo = __uint_as_float(l);
-    }
+    // x ~ hi + lo: hi = tf32(x), lo = tf32(x - hi) (the difference is exact in FP32)
+    uint32_t hb, lb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xf));
+    const float hi = __uint_as_float(hb);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(xf - hi));
+    const float lo = __uint_as_float(lb);
     // tiled core-matrix layout
     const int rt = rp / p.rowtile, rr = rp % p.rowtile;
     const int kt = kp / BK, kk = kp % BK;
@@ -418,8 +452,8 @@ __global__ void tc_pack_kernel(PackArgs p, int batch) {
 
 // ---------------------------------------------------------------- finalize
 struct FinArgs {
-  const float* D;  // [batch*splits][Mp][Np]
-  int Mp, Np, splits;
+  const float2* P;  // (sum, compensation) [batch*ranges][Mp][Np]
+  int Mp, Np, ranges;
   int M, N;        // logical output extents
   int mode;        // 0 real, 1 stacked rows (C re/im = row halves), 2 stacked columns
   double* C;
@@ -430,6 +464,8 @@ struct FinArgs {
 
 __global__ void tc_finalize_kernel(FinArgs f, int batch) {
   const int64_t per = (int64_t)f.M * f.N;
+  const bool unit = f.alpha == 1.0 || f.alpha == -1.0;
+  const float sgn = f.alpha == -1.0 ? -1.0f : 1.0f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / per);
@@ -441,26 +477,30 @@ __global__ void tc_finalize_kernel(FinArgs f, int batch) {
       int mr = m, nr = n;
       if (f.mode == 1) mr = m + part * f.M;
       if (f.mode == 2) nr = n + part * f.N;
-      double s = 0.0;
-      for (int z = 0; z < f.splits; ++z)
-        s += (double)f.D[(((int64_t)b * f.splits + z) * f.Mp + mr) * f.Np + nr];
-      const double v = f.alpha * s;
-      c[part] = f.beta == 0.0 ? v : fma(f.beta, c[part], v);
+      float s = 0.0f, cm = 0.0f;
+      for (int z = 0; z < f.ranges; ++z) {
+        const float2 pz = f.P[(((int64_t)b * f.ranges + z) * f.Mp + mr) * f.Np + nr];
+        two_sum_acc(s, cm, pz.x);
+        cm += pz.y;
+      }
+      const float sf = s + cm;
+      const double v = unit ? f32_to_f64(sgn * sf) : f.alpha * f32_to_f64(sf);
+      c[part] = f.beta == 0.0 ? v : (f.beta == 1.0 ? c[part] + v : fma(f.beta, c[part], v));
     }
   }
 }
 
 constexpr int kBN = 128;
 constexpr int kStages = 3;
-constexpr int kMaxKtPerSplit = 16;  // FP32 partial sums over at most 512 of K
 constexpr size_t kSmemBytes = kStages * (2 * TILE_BYTES + 2 * (size_t)kBN * BK * 4) + 128;
 
 inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Plan {
   int mode;  // 0 RR, 1 CR, 2 RC, 3 CC
-  int Mp, Np, Kp, KT, splits, kps;
-  int64_t a_elems, b_elems, d_elems;  // per operand part (hi or lo), and slabs
+  int Mp, Np, Kp, KT, ranges, kpr;
+  int64_t a_elems, b_elems;  // per operand part (hi or lo)
+  int64_t p_elems;           // (sum, compensation) partials (0 with one range)
 };
 
 Plan plan(const GemmDesc& d) {
@@ -473,14 +513,27 @@ Plan plan(const GemmDesc& d) {
   p.Np = roundup(std::max(Br, 1), kBN);
   p.Kp = roundup(std::max(Ak, 1), BK);
   p.KT = p.Kp / BK;
+  // K ranges: fewest waves x k-tiles per CTA, a range costing about four
+  // k-tiles for writing and re-reading its partial tile
   const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / kBN) * d.batch;
-  int splits = (p.KT + kMaxKtPerSplit - 1) / kMaxKtPerSplit;
-  while (tiles * splits < 148 && splits < p.KT) ++splits;
-  p.kps = (p.KT + splits - 1) / splits;
-  p.splits = (p.KT + p.kps - 1) / p.kps;  // every split owns at least one k-tile
+  double best = 0.0;
+  p.ranges = 1;
+  p.kpr = p.KT;
+  for (int r = 1; r <= p.KT; ++r) {
+    const int kpr = (p.KT + r - 1) / r;
+    if ((p.KT + kpr - 1) / kpr != r) continue;  // same split as a smaller r
+    if ((int64_t)d.batch * r > 65535) break;
+    const double waves = (double)((tiles * r + 147) / 148);
+    const double cost = waves * (kpr + (r > 1 ? 4 : 0));
+    if (r == 1 || cost < best) {
+      best = cost;
+      p.ranges = r;
+      p.kpr = kpr;
+    }
+  }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
-  p.d_elems = (int64_t)p.splits * p.Mp * p.Np * d.batch;
+  p.p_elems = p.ranges == 1 ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
   return p;
 }
 
@@ -491,8 +544,8 @@ TcLayout gemm_tc_layout(const GemmDesc& d) {
   TcLayout l;
   l.a_elems = p.a_elems;
   l.b_elems = p.b_elems;
-  l.d_elems = p.splits == 1 ? 0 : p.d_elems;  // single slice: direct epilogue, no slabs
-  l.splits = p.splits;
+  l.p_elems = p.p_elems;
+  l.ranges = p.ranges;
   l.padded_flops = 3LL * 2 * (int64_t)p.Mp * p.Np * p.Kp * d.batch;
   return l;
 }
@@ -554,11 +607,11 @@ void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
 }
 
 void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,
-                 const float* Blo, float* D, int* err, cudaStream_t st) {
+                 const float* Blo, float2* P, int* err, cudaStream_t st) {
   using namespace tc;
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const Plan p = plan(d);
-  if (p.Mp / BM > 65535 || (int64_t)d.batch * p.splits > 65535)
+  if (p.Mp / BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
     throw Error(-1, "gemm_tc: grid too large");
   KArgs g{};
   g.Ahi = Ahi;
@@ -568,15 +621,14 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.sA = (int64_t)p.Mp * p.Kp;
   g.sB = (int64_t)p.Np * p.Kp;
   g.KT = p.KT;
-  g.ktiles_per_split = p.kps;
-  g.splits = p.splits;
-  g.D = D;
+  g.kpr = p.kpr;
+  g.ranges = p.ranges;
+  g.P = P;
   g.Mp = p.Mp;
   g.Np = p.Np;
   g.lbo = 128;   // core matrices adjacent along K
   g.sbo = 1024;  // 8-row groups
   g.err = err;
-  g.direct = p.splits == 1;
   g.C = d.C;
   g.cplx = d.Acplx || d.Bcplx;
   g.M = d.M;
@@ -586,21 +638,21 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid(p.Np / kBN, p.Mp / BM, d.batch * p.splits);
+  dim3 grid(p.Np / kBN, p.Mp / BM, d.batch * p.ranges);
   tc_gemm_kernel<kBN, kStages><<<grid, THREADS, kSmemBytes, st>>>(g);
   RT_CHECK_LAUNCH();
 }
 
-void gemm_tc_finalize(const GemmDesc& d, const float* D, cudaStream_t st) {
+void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st) {
   using namespace tc;
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const Plan p = plan(d);
-  if (p.splits == 1) return;  // the MMA kernel wrote C directly
+  if (p.ranges == 1) return;  // the MMA kernel wrote C directly
   FinArgs fa{};
-  fa.D = D;
+  fa.P = P;
   fa.Mp = p.Mp;
   fa.Np = p.Np;
-  fa.splits = p.splits;
+  fa.ranges = p.ranges;
   fa.M = d.M;
   fa.N = d.N;
   fa.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);

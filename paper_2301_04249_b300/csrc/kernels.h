@@ -27,23 +27,27 @@ int gemm_f64_splits(const GemmDesc& d);
 int64_t gemm_f64_workspace(const GemmDesc& d);
 void gemm_f64(const GemmDesc& d, cudaStream_t st);
 
-// Split-TF32 tensor-core GEMM (tcgen05) with the same contract as gemm_f64,
-// in four launches: pack A and pack B into TF32 hi/lo tiles (a_elems /
-// b_elems floats each part), the tcgen05 MMA kernel into FP32 slabs
-// (d_elems floats; FP32 accumulation over slices of at most 512 of K; err set
-// non-zero if a pipeline wait ran out), and the finalize that sums the slices
-// in FP64 into C with alpha/beta.  gemm_tc_init() once per process first.
+// Split-TF32 tensor-core GEMM (tcgen05) with the same contract as gemm_f64:
+// pack A and pack B into TF32 hi/lo tiles (a_elems / b_elems floats each
+// part), then the tcgen05 MMA kernel (FP32 accumulation over slices of at
+// most 512 of K, slices summed as compensated FP32 pairs; err set non-zero
+// if a pipeline wait ran out).  With one K range per tile it writes C with
+// alpha/beta itself; otherwise it writes p_elems (sum, compensation) pairs
+// and the finalize combines them in range order into C.  gemm_tc_init()
+// once per process first.
 struct TcLayout {
-  int64_t a_elems, b_elems, d_elems, padded_flops;
-  int splits;  // K slices; 1 = the MMA kernel writes C directly (finalize is a no-op)
+  int64_t a_elems, b_elems;  // floats per packed hi (or lo) operand
+  int64_t p_elems;           // float2 partials; 0 = the MMA kernel writes C directly
+  int64_t padded_flops;
+  int ranges;                // K ranges per output tile (1 = finalize is a no-op)
 };
 TcLayout gemm_tc_layout(const GemmDesc& d);
 void gemm_tc_init();
 void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st);
 void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st);
 void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,
-                 const float* Blo, float* D, int* err, cudaStream_t st);
-void gemm_tc_finalize(const GemmDesc& d, const float* D, cudaStream_t st);
+                 const float* Blo, float2* P, int* err, cudaStream_t st);
+void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st);
 
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
 // contiguous with dims out_dim[0..nd-1]; strides count elements.  A real

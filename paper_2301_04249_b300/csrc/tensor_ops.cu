@@ -27,37 +27,65 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 // ---------------------------------------------------------------- permute
+// out = alpha * v + beta * out in the forms that need no FP64 multiply (the
+// FP64 pipe is the scarce unit for these HBM-bound kernels).
+enum AxOp { kCopy = 0, kNeg = 1, kAdd = 2, kSub = 3, kGeneral = 4 };
+
+__device__ __forceinline__ double axop(int op, double v, double c, double alpha, double beta) {
+  switch (op) {
+    case kCopy:
+      return v;
+    case kNeg:
+      return neg_f64(v);
+    case kAdd:
+      return c + v;
+    case kSub:
+      return c - v;
+    default:
+      return beta == 0.0 ? alpha * v : fma(beta, c, alpha * v);
+  }
+}
+
+inline int axop_of(double alpha, double beta) {
+  if (beta == 0.0 && alpha == 1.0) return kCopy;
+  if (beta == 0.0 && alpha == -1.0) return kNeg;
+  if (beta == 1.0 && alpha == 1.0) return kAdd;
+  if (beta == 1.0 && alpha == -1.0) return kSub;
+  return kGeneral;
+}
+
 // CPI / CPO: input / output complex.  A real input into a complex output
-// scales the real part and leaves beta * imaginary part.
-template <bool CPI, bool CPO>
+// scales the real part and leaves beta * imaginary part.  IDX: the integer
+// type of the output-index decomposition (32-bit whenever it fits).
+template <bool CPI, bool CPO, typename IDX>
 __global__ void permute_kernel(const double* __restrict__ in, double* __restrict__ out,
-                               PermDesc d, double alpha, double beta, int64_t total) {
+                               PermDesc d, double alpha, double beta, int op, int64_t total) {
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
        o += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = o, off = 0;
+    IDX rem = (IDX)o;
+    int64_t off = 0;
 #pragma unroll
     for (int k = 5; k >= 0; --k) {
       if (k < d.nd) {
-        int64_t idx = rem % d.out_dim[k];
-        rem /= d.out_dim[k];
-        off += idx * d.in_stride[k];
+        const IDX dim = (IDX)d.out_dim[k];
+        const IDX q = rem / dim;
+        off += (int64_t)(rem - q * dim) * d.in_stride[k];
+        rem = q;
       }
     }
+    const bool rd = op == kAdd || op == kSub || (op == kGeneral && beta != 0.0);  // reads out
     if constexpr (CPO) {
       double2 v = CPI ? reinterpret_cast<const double2*>(in)[off] : make_double2(in[off], 0.0);
       double2* po = reinterpret_cast<double2*>(out) + o;
+      const double2 c = rd ? *po : make_double2(0.0, 0.0);
       double2 r;
-      if (beta == 0.0) {
-        r = make_double2(alpha * v.x, alpha * v.y);
-      } else {
-        double2 c = *po;
-        r = make_double2(fma(beta, c.x, alpha * v.x), fma(beta, c.y, alpha * v.y));
-      }
+      r.x = axop(op, v.x, c.x, alpha, beta);
+      r.y = CPI ? axop(op, v.y, c.y, alpha, beta)
+                : (rd ? (op == kGeneral ? beta * c.y : c.y) : 0.0);
       *po = r;
     } else {
-      double v = alpha * in[off];
-      if (beta != 0.0) v = fma(beta, out[o], v);
-      out[o] = v;
+      const double c = rd ? out[o] : 0.0;
+      out[o] = axop(op, in[off], c, alpha, beta);
     }
   }
 }
@@ -595,12 +623,21 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
   if (total == 0) return;
   if (in_cplx && !out_cplx) throw Error(-1, "permute_add: complex input into real output");
   int grid = grid_for(total, 16);
-  if (in_cplx)
-    permute_kernel<true, true><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
-  else if (out_cplx)
-    permute_kernel<false, true><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
+  const int op = axop_of(alpha, beta);
+  auto go = [&](auto idx_tag) {
+    using I = decltype(idx_tag);
+    if (in_cplx)
+      permute_kernel<true, true, I><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, op, total);
+    else if (out_cplx)
+      permute_kernel<false, true, I><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, op, total);
+    else
+      permute_kernel<false, false, I><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, op,
+                                                                  total);
+  };
+  if (total <= 0xFFFFFFFFll)
+    go(0u);
   else
-    permute_kernel<false, false><<<grid, kThreads, 0, st>>>(in, out, d, alpha, beta, total);
+    go((uint64_t)0);
   RT_CHECK_LAUNCH();
 }
 

@@ -88,6 +88,7 @@ struct Tensor {
   int64_t dim[kMaxDims] = {0, 0, 0, 0, 0, 0};
   bool cplx = false;
   bool constant = false;  // contents fixed for the context's lifetime (integrals)
+  bool released = false;  // device copy freed: usable only through cached tensor-core packs
 
   int64_t numel() const {
     int64_t n = 1;

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
+#include <mutex>
 
 #include "engine.h"
 
@@ -114,6 +116,155 @@ bool Engine::collect_graph_timing(const std::vector<GraphPair>& pairs) {
     tbytes[p.cls] += p.bytes;
   }
   return true;
+}
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, GemmChoice> g_tune;  // process-wide autotuner choices
+
+std::string tune_key(const GemmDesc& g, bool tc_ok) {
+  char buf[320];
+  std::snprintf(buf, sizeof buf, "%d,%d,%d,%d|%d%d%d%d|%lld,%lld,%lld,%lld,%lld,%lld|%d|%d", g.M,
+                g.N, g.K, g.batch, (int)g.Acplx, (int)g.Bcplx, (int)g.transA, (int)g.transB,
+                (long long)g.lda, (long long)g.ldb, (long long)g.ldc, (long long)g.strideA,
+                (long long)g.strideB, (long long)g.strideC, (int)(g.beta != 0.0), (int)tc_ok);
+  return buf;
+}
+
+bool tune_lookup(const std::string& k, GemmChoice* c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+// First choice stored for a key wins; returns the stored one.
+GemmChoice tune_store(const std::string& k, const GemmChoice& c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune.emplace(k, c).first->second;
+}
+
+// FP64 candidates: every tile shape with 1, 2, 4, ... K slices while a slice
+// keeps at least 16 of K, the grid stays within 8 waves and the partial
+// sums within 16 outputs' worth (and 256 MB).
+std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
+  std::vector<GemmChoice> out;
+  const int64_t outd = (int64_t)g.M * g.N * g.batch * ((g.Acplx || g.Bcplx) ? 2 : 1);
+  for (int t = 0; t < gemm_f64_tiles(); ++t) {
+    int tbm = 0, tbn = 0;
+    gemm_f64_tile_shape(t, &tbm, &tbn);
+    if ((g.M + tbm - 1) / tbm > 65535) continue;  // grid y limit
+    for (int s = 1; s <= 64; s *= 2) {
+      if (s > 1 && g.K / s < 16) break;
+      GemmDesc d = g;
+      d.tile = t;
+      d.splits = s;
+      if (gemm_f64_splits(d) != s) break;
+      const int64_t ws = gemm_f64_workspace(d);
+      if (ws > 16 * outd || ws * 8 > (int64_t(256) << 20)) break;
+      int bm = 0, bn = 0;
+      gemm_f64_tile_shape(t, &bm, &bn);
+      const int64_t blocks = (int64_t)((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.batch * s;
+      if (s > 1 && blocks > 8 * 148) break;
+      out.push_back({false, t, s});
+    }
+  }
+  return out;
+}
+
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  RT_CUDA(cudaStreamIsCapturing(st, &cs));
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+// Scratch of one tuning session: an output of C's size (the trials write it
+// with beta = 0), the largest split-K workspace among the FP64 candidates
+// and, for the tensor-core candidate, packed operands and partials.  With
+// out == nullptr (planning) the scratch is only reserved in the arena;
+// otherwise every candidate runs once (screened out when over twice the
+// best so far) and then twice more timed, and the fastest is returned.  Operands the tensor-core cache would hold are packed
+// outside the timing.
+void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool a_const, bool b_const,
+                            GemmChoice* out) {
+  std::vector<GemmChoice> cands = f64_candidates(g);
+  if (tc_ok) cands.push_back({true, -1, 0});
+  const int64_t mark = arena.mark();
+  GemmDesc base = g;
+  base.beta = 0.0;
+  base.tile = -1;
+  base.splits = 0;
+  base.C = arena.alloc((int64_t)g.M * g.N * g.batch * ((g.Acplx || g.Bcplx) ? 2 : 1));
+  int64_t wsmax = 0;
+  for (const auto& c : cands) {
+    if (c.tc) continue;
+    GemmDesc d = base;
+    d.tile = c.tile;
+    d.splits = c.splits;
+    wsmax = std::max(wsmax, gemm_f64_workspace(d));
+  }
+  double* ws = wsmax ? arena.alloc(wsmax) : nullptr;
+  float *ahi = nullptr, *alo = nullptr, *bhi = nullptr, *blo = nullptr;
+  float2* P = nullptr;
+  if (tc_ok) {
+    const TcLayout L = gemm_tc_layout(base);
+    ahi = reinterpret_cast<float*>(arena.alloc((L.a_elems + 1) / 2));
+    alo = reinterpret_cast<float*>(arena.alloc((L.a_elems + 1) / 2));
+    bhi = reinterpret_cast<float*>(arena.alloc((L.b_elems + 1) / 2));
+    blo = reinterpret_cast<float*>(arena.alloc((L.b_elems + 1) / 2));
+    if (L.p_elems) P = reinterpret_cast<float2*>(arena.alloc(L.p_elems));
+  }
+  if (out == nullptr || dry) {
+    arena.release(mark);
+    return;
+  }
+  if (tc_ok) {
+    if (a_const) gemm_tc_pack_a(base, ahi, alo, stream);
+    if (b_const) gemm_tc_pack_b(base, bhi, blo, stream);
+  }
+  cudaEvent_t e0 = get_event(), e1 = get_event();
+  float best_ms = std::numeric_limits<float>::infinity();
+  GemmChoice best;
+  for (const auto& c : cands) {
+    auto run = [&] {
+      if (c.tc) {
+        if (!a_const) gemm_tc_pack_a(base, ahi, alo, stream);
+        if (!b_const) gemm_tc_pack_b(base, bhi, blo, stream);
+        gemm_tc_mma(base, ahi, alo, bhi, blo, P, tc_err, stream);
+        gemm_tc_finalize(base, P, stream);
+      } else {
+        GemmDesc d = base;
+        d.tile = c.tile;
+        d.splits = c.splits;
+        d.work = ws;
+        gemm_f64(d, stream);
+      }
+    };
+    auto timed = [&](int reps) {
+      RT_CUDA(cudaEventRecord(e0, stream));
+      for (int r = 0; r < reps; ++r) run();
+      RT_CUDA(cudaEventRecord(e1, stream));
+      RT_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      RT_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      return t / reps;
+    };
+    // first run (cold) screens out clearly slower candidates
+    if (timed(1) > 2.0f * best_ms) continue;
+    const float ms = timed(2);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  free_events_.push_back(e0);
+  free_events_.push_back(e1);
+  arena.release(mark);
+  *out = best;
 }
 
 void Engine::axpy(const char* spec, double alpha, const Tensor& X, double beta, const Tensor& Y) {
@@ -239,9 +390,36 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     return out;
   };
 
-  double mult0 = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
-  const bool use_tc =
+  const double mult0 = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
+  bool use_tc =
       tensor_cores && mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt >= tc_min_flops;
+
+  GemmDesc g;
+  g.M = (int)Mt;
+  g.N = (int)Nt;
+  g.K = (int)Kt;
+  g.batch = (int)Bt;
+  g.Acplx = A.cplx;
+  g.transA = bTA;
+  g.lda = bTA ? Mt : Kt;
+  g.strideA = Mt * Kt;
+  g.Bcplx = B.cplx;
+  g.transB = bTB;
+  g.ldb = bTB ? Kt : Nt;
+  g.strideB = Kt * Nt;
+  g.ldc = Nt;
+  g.strideC = Mt * Nt;
+  g.alpha = alpha;
+  g.beta = bPC ? 0.0 : beta;
+
+  // launch configuration from the autotuner, when it has one for this shape
+  const double flops0 = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+  const bool tunable = autotune && !use_tc && !gemm_f64_is_gemv(g) && flops0 <= tune_max_flops;
+  const bool tc_ok = tensor_cores && flops0 >= tc_tune_min_flops;
+  const std::string tkey = tunable ? tune_key(g, tc_ok) : std::string();
+  GemmChoice choice;
+  bool chosen = tunable && tune_lookup(tkey, &choice);
+  if (chosen && choice.tc) use_tc = true;
 
   // tensor-core operands of constant tensors may already be packed
   auto key = [&](const char* role, const Tensor& T) {
@@ -260,6 +438,8 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     if (it != tc_cache_.end()) cB = &it->second;
   }
 
+  if (!dry && ((A.released && !cA) || (B.released && !cB)))
+    throw Error(-3, std::string("contract: freed operand without a cached pack in ") + spec);
   const Tensor Ause = (bPA && !cA) ? permuted(A, p.a, batch + bM + bK) : A;
   const Tensor Buse = (bPB && !cB) ? permuted(B, p.b, batch + bK + bN) : B;
   Tensor Cuse = C;
@@ -269,28 +449,24 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     for (int k = 0; k < Cuse.nd; ++k) Cuse.dim[k] = dimof[(unsigned char)lab[k]];
     Cuse.p = arena.alloc(Cuse.doubles());
   }
-
-  GemmDesc g;
-  g.M = (int)Mt;
-  g.N = (int)Nt;
-  g.K = (int)Kt;
-  g.batch = (int)Bt;
   g.A = Ause.p;
-  g.Acplx = A.cplx;
-  g.transA = bTA;
-  g.lda = bTA ? Mt : Kt;
-  g.strideA = Mt * Kt;
   g.B = Buse.p;
-  g.Bcplx = B.cplx;
-  g.transB = bTB;
-  g.ldb = bTB ? Kt : Nt;
-  g.strideB = Kt * Nt;
   g.C = Cuse.p;
-  g.ldc = Nt;
-  g.strideC = Mt * Nt;
-  g.alpha = alpha;
-  g.beta = bPC ? 0.0 : beta;
-  double flops = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+
+  if (tunable && dry) tuning_scratch(g, tc_ok, A.constant, B.constant, nullptr);
+  if (tunable && !chosen && tuning && !dry && !stream_capturing(stream)) {
+    GemmChoice c;
+    tuning_scratch(g, tc_ok, A.constant, B.constant, &c);
+    choice = tune_store(tkey, c);
+    chosen = true;
+    ++tuned;
+    if (choice.tc) use_tc = true;
+  }
+  if (chosen && !choice.tc) {
+    g.tile = choice.tile;
+    g.splits = choice.splits;
+  }
+  const double flops = flops0;
   const std::string label =
       trace_on() ? std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
                        " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
@@ -330,7 +506,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                  gemm_tc_pack_b(g, pk.hi, pk.lo, stream);
              },
              "tc pack");
-      if (store) tc_cache_[key(role, T)] = pk;
+      if (store) {
+        tc_cache_[key(role, T)] = pk;
+        tc_cached_.insert(T.p);
+      }
       return pk;
     };
     const Packed pa = operand("A", A, cA, L.a_elems, true);

@@ -6,6 +6,7 @@
 
 #include <functional>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -15,6 +16,12 @@
 namespace rteom {
 
 enum KernelClass { kLadder = 0, kContract = 1, kPermute = 2, kElementwise = 3, kNumClasses = 4 };
+
+// Launch configuration of one GEMM shape picked by the autotuner.
+struct GemmChoice {
+  bool tc = false;         // tensor-core (split-TF32) path
+  int tile = -1, splits = 0;  // FP64 kernel tile index and K slices
+};
 
 class Engine {
  public:
@@ -32,6 +39,19 @@ class Engine {
   // pass at set-up); later evaluations, captured graphs included, read them.
   bool tc_cache_fill = false;
   std::function<float*(int64_t)> persistent_alloc;  // floats, owned by the context
+
+  // Autotuner.  A GEMM of at most tune_max_flops that is not a matrix-vector
+  // product takes its launch configuration (FP64 tile shape and K slices, or
+  // the tensor-core path when tensor_cores is set and it has at least
+  // tc_tune_min_flops) from timed trials run during eager evaluations with
+  // `tuning` set.  Choices are kept process-wide, keyed by the GEMM's shape
+  // and form, so every context of the process launches the same kernels and
+  // gets the same bits; without a choice the shape heuristics apply.
+  bool autotune = true;
+  bool tuning = false;
+  double tune_max_flops = 2e9;
+  double tc_tune_min_flops = 1e6;
+  long long tuned = 0;  // GEMM shapes this engine has tuned
 
   // Timing.  Eager launches are each bracketed by events.  While a residual
   // graph is being captured (capturing == true) only launches of the class
@@ -115,6 +135,8 @@ class Engine {
   // Returns false (and clears the error) when the driver cannot time
   // event-record nodes; the caller then times residuals eagerly instead.
   bool collect_graph_timing(const std::vector<GraphPair>& pairs);
+  // Whether some tensor-core pack of the tensor at p is cached.
+  bool tc_cached(const double* p) const { return tc_cached_.count(p) != 0; }
   bool graph_timing_ok = true;
 
  private:
@@ -125,10 +147,13 @@ class Engine {
     std::string what;
   };
   bool trace_on() const;
+  void tuning_scratch(const GemmDesc& g, bool tc_ok, bool a_const, bool b_const,
+                      GemmChoice* out);
   struct Packed {
     float *hi, *lo;
   };
   std::map<std::string, Packed> tc_cache_;
+  std::set<const double*> tc_cached_;  // tensors with at least one cached pack
   std::vector<Pending> pending_;
   std::vector<cudaEvent_t> free_events_;
   cudaEvent_t get_event();

@@ -218,10 +218,14 @@ __global__ void splitk_reduce(const double* __restrict__ P, double* C, int M, in
   }
 }
 
-// Output tile shapes, chosen from the output's extents.
+// Output tile shapes: the table the autotuner walks, and the heuristic pick.
 struct Tile {
   int bm, bn;
 };
+
+constexpr Tile kTiles[] = {{64, 64}, {32, 64}, {16, 64}, {8, 128},
+                           {64, 16}, {16, 16}, {8, 32},  {32, 32}};
+constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
 
 Tile pick_tile(int M, int N) {
   if (M <= 8 && N > 16) return {8, 128};
@@ -232,20 +236,27 @@ Tile pick_tile(int M, int N) {
   return {64, 64};
 }
 
+Tile tile_of(const GemmDesc& d) {
+  return d.tile >= 0 && d.tile < kNumTiles ? kTiles[d.tile] : pick_tile(d.M, d.N);
+}
+
 template <bool AC, bool BC>
-void launch_typed(const GemmArgs& g, int batch, int splits, cudaStream_t st) {
-  const Tile t = pick_tile(g.M, g.N);
+void launch_typed(const GemmArgs& g, Tile t, int batch, int splits, cudaStream_t st) {
   dim3 grid((g.N + t.bn - 1) / t.bn, (g.M + t.bm - 1) / t.bm, batch * splits);
   if (t.bm == 64 && t.bn == 64)
     gemm_kernel<AC, BC, 64, 64, 4, 4><<<grid, 256, 0, st>>>(g);
-  else if (t.bm == 32)
+  else if (t.bm == 32 && t.bn == 64)
     gemm_kernel<AC, BC, 32, 64, 2, 4><<<grid, 256, 0, st>>>(g);
   else if (t.bm == 16 && t.bn == 64)
     gemm_kernel<AC, BC, 16, 64, 1, 4><<<grid, 256, 0, st>>>(g);
-  else if (t.bm == 8)
+  else if (t.bm == 8 && t.bn == 128)
     gemm_kernel<AC, BC, 8, 128, 1, 4><<<grid, 256, 0, st>>>(g);
-  else if (t.bn == 16 && t.bm == 64)
+  else if (t.bm == 64 && t.bn == 16)
     gemm_kernel<AC, BC, 64, 16, 4, 1><<<grid, 256, 0, st>>>(g);
+  else if (t.bm == 8 && t.bn == 32)
+    gemm_kernel<AC, BC, 8, 32, 1, 1><<<grid, 256, 0, st>>>(g);
+  else if (t.bm == 32 && t.bn == 32)
+    gemm_kernel<AC, BC, 32, 32, 2, 2><<<grid, 256, 0, st>>>(g);
   else
     gemm_kernel<AC, BC, 16, 16, 1, 1><<<grid, 256, 0, st>>>(g);
 }
@@ -377,13 +388,28 @@ void gemv_f64(const GemmDesc& d, cudaStream_t st) {
 
 }  // namespace
 
+int gemm_f64_tiles() { return kNumTiles; }
+
+void gemm_f64_tile_shape(int t, int* bm, int* bn) {
+  *bm = kTiles[t].bm;
+  *bn = kTiles[t].bn;
+}
+
+bool gemm_f64_is_gemv(const GemmDesc& d) { return d.batch == 1 && (d.M == 1 || d.N == 1); }
+
 int gemm_f64_splits(const GemmDesc& d) {
-  if (d.batch == 1 && (d.M == 1 || d.N == 1)) return 1;  // matrix-vector path
+  if (gemm_f64_is_gemv(d)) return 1;  // matrix-vector path
+  if (d.M <= 0 || d.N <= 0) return 1;
+  if (d.splits > 0) {  // autotuner's choice, kept within K and the grid limit
+    int64_t s = std::min<int64_t>(d.splits, std::max(d.K, 1));
+    if ((int64_t)d.batch * s > 65535) s = 65535 / d.batch;
+    return (int)std::max<int64_t>(s, 1);
+  }
   // Split K when the output alone gives too few blocks to balance 148 SMs
   // (the FP64 pipe is the bottleneck, so only the block count matters); each
   // slice keeps at least 128 of K.
-  if (d.M <= 0 || d.N <= 0 || d.K < 256) return 1;
-  const Tile t = pick_tile(d.M, d.N);
+  if (d.K < 256) return 1;
+  const Tile t = tile_of(d);
   int64_t tiles = (int64_t)((d.N + t.bn - 1) / t.bn) * ((d.M + t.bm - 1) / t.bm) * d.batch;
   const int64_t target = 8 * 148;
   if (tiles >= target) return 1;
@@ -402,15 +428,16 @@ int64_t gemm_f64_workspace(const GemmDesc& d) {
 
 void gemm_f64(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  if ((d.M + 7) / 8 > 65535 || d.batch > 65535)
-    throw Error(-1, "gemm_f64: grid too large");
-  if (d.batch == 1 && (d.M == 1 || d.N == 1)) {
+  if (d.batch > 65535) throw Error(-1, "gemm_f64: batch too large");
+  if (gemm_f64_is_gemv(d)) {
     gemv_f64(d, st);
     RT_CHECK_LAUNCH();
     return;
   }
   const int splits = gemm_f64_splits(d);
   if (splits > 1 && d.work == nullptr) throw Error(-1, "gemm_f64: split-K needs a workspace");
+  if ((d.M + tile_of(d).bm - 1) / tile_of(d).bm > 65535)
+    throw Error(-1, "gemm_f64: too many row tiles for the grid");
   GemmArgs g;
   g.M = d.M;
   g.N = d.N;
@@ -438,13 +465,13 @@ void gemm_f64(const GemmDesc& d, cudaStream_t st) {
     g.beta = d.beta;
   }
   if (d.Acplx && d.Bcplx)
-    launch_typed<true, true>(g, d.batch, splits, st);
+    launch_typed<true, true>(g, tile_of(d), d.batch, splits, st);
   else if (d.Acplx)
-    launch_typed<true, false>(g, d.batch, splits, st);
+    launch_typed<true, false>(g, tile_of(d), d.batch, splits, st);
   else if (d.Bcplx)
-    launch_typed<false, true>(g, d.batch, splits, st);
+    launch_typed<false, true>(g, tile_of(d), d.batch, splits, st);
   else
-    launch_typed<false, false>(g, d.batch, splits, st);
+    launch_typed<false, false>(g, tile_of(d), d.batch, splits, st);
   RT_CHECK_LAUNCH();
   if (splits > 1) {
     const bool cc = d.Acplx || d.Bcplx;

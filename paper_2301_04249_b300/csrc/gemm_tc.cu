@@ -383,6 +383,7 @@ struct PackArgs {
   int rowtile;            // 128 for A', BN for B'
   float *hi, *lo;
   int64_t s_out;          // elements per batch entry of the packed output
+  bool rows_fast;         // consecutive threads walk packed rows (source rows contiguous)
 };
 
 // Packed row r' / column k' -> (source row, source column, part, sign).
@@ -393,14 +394,23 @@ enum PackMode {
   kBcc = 3,         // complex B of a complex x complex product
 };
 
+template <typename IDX>
 __global__ void tc_pack_kernel(PackArgs p, int batch) {
-  const int64_t per = (int64_t)p.Rp * p.Kp;
+  const IDX per = (IDX)p.Rp * (IDX)p.Kp;
   const int KT = p.Kp / BK;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const IDX n = per * (IDX)batch;
+  for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < n;
+       e += (IDX)gridDim.x * blockDim.x) {
     const int b = (int)(e / per);
-    const int64_t q = e - (int64_t)b * per;
-    const int rp = (int)(q / p.Kp), kp = (int)(q % p.Kp);
+    const IDX q = e - (IDX)b * per;
+    int rp, kp;
+    if (p.rows_fast) {
+      rp = (int)(q % (IDX)p.Rp);
+      kp = (int)(q / (IDX)p.Rp);
+    } else {
+      rp = (int)(q / (IDX)p.Kp);
+      kp = (int)(q % (IDX)p.Kp);
+    }
     int r = rp, c = kp, part = 0;
     bool neg = false;
     bool valid = true;
@@ -558,6 +568,14 @@ void gemm_tc_init() {
 
 namespace {
 int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
+
+void launch_pack(const tc::PackArgs& pa, int64_t elems, int batch, cudaStream_t st) {
+  if (elems < (int64_t(1) << 32) - (int64_t)256 * 148 * 16)
+    tc::tc_pack_kernel<uint32_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  else
+    tc::tc_pack_kernel<uint64_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  RT_CHECK_LAUNCH();
+}
 }  // namespace
 
 void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
@@ -579,8 +597,8 @@ void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pa.hi = hi;
   pa.lo = lo;
   pa.s_out = (int64_t)p.Mp * p.Kp;
-  tc_pack_kernel<<<grid_of(p.a_elems), 256, 0, st>>>(pa, d.batch);
-  RT_CHECK_LAUNCH();
+  pa.rows_fast = pa.s_r == 1 && pa.s_c != 1;
+  launch_pack(pa, p.a_elems, d.batch, st);
 }
 
 void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
@@ -602,8 +620,8 @@ void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pb.hi = hi;
   pb.lo = lo;
   pb.s_out = (int64_t)p.Np * p.Kp;
-  tc_pack_kernel<<<grid_of(p.b_elems), 256, 0, st>>>(pb, d.batch);
-  RT_CHECK_LAUNCH();
+  pb.rows_fast = pb.s_r == 1 && pb.s_c != 1;
+  launch_pack(pb, p.b_elems, d.batch, st);
 }
 
 void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,

@@ -20,9 +20,17 @@ struct GemmDesc {
   int64_t ldc = 0, strideC = 0;
   double alpha = 1.0, beta = 0.0;
   double* work = nullptr;  // split-K partial sums, gemm_f64_workspace() doubles
+  // launch configuration chosen by the autotuner: tile index < gemm_f64_tiles()
+  // and K slices; -1 / 0 = the shape heuristic
+  int tile = -1, splits = 0;
 };
 // Number of K slices the kernel will use for this shape (1 = no split).
 int gemm_f64_splits(const GemmDesc& d);
+// Number of output tile shapes of the FP64 kernel (autotuner candidates).
+int gemm_f64_tiles();
+void gemm_f64_tile_shape(int t, int* bm, int* bn);
+// True when the shape takes the matrix-vector path (no tile or split choice).
+bool gemm_f64_is_gemv(const GemmDesc& d);
 // Scratch (doubles) a split-K launch needs; 0 when no split is used.
 int64_t gemm_f64_workspace(const GemmDesc& d);
 void gemm_f64(const GemmDesc& d, cudaStream_t st);

@@ -61,7 +61,8 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   const Tensor ovov = R_(op.ovov, {nO, nV, nO, nV});
   const Tensor ovov_as = R_(op.ovov_as, {nO, nV, nO, nV});
   const Tensor ovvv = R_(op.ovvv, {nO, nV, nV, nV});
-  const Tensor vvvv = R_(op.vvvv, {nV, nV, nV, nV});
+  Tensor vvvv = R_(op.vvvv, {nV, nV, nV, nV});
+  vvvv.released = op.vvvv_released;
   Tensor fov[2], foo_c[2], fov_c[2], fvv_c[2];
   for (int s = 0; s < 2; ++s) {
     fov[s] = R_(op.fov[s], {nO, nV});
@@ -235,7 +236,9 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
         Tensor tp = newc({npo, npv});
         Tensor Rp = newc({npo, npv});
         E.launch(kElementwise, 0.0, [&] { pack_pairs(tau_ss[s].p, tp.p, nO, nV, E.stream); });
-        E.contract("pq,qr->pr", 1.0, tp, R_(op.vvvv_as, {npv, npv}), 0.0, Rp, kLadder);
+        Tensor Wm = R_(op.vvvv_as, {npv, npv});
+        Wm.released = op.vvvv_as_released;
+        E.contract("pq,qr->pr", 1.0, tp, Wm, 0.0, Rp, kLadder);
         E.launch(kElementwise, 0.0,
                  [&] { unpack_pairs_antisym(Rp.p, R.p, nO, nV, 1.0, E.stream); });
       }

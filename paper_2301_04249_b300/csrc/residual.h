@@ -19,6 +19,9 @@ struct ResidualOperands {
   const double* vvvv = nullptr;  // ladder layout [e][f][a][b] = (ae|bf)
   // same-spin ladder block [(e<f)][(a<b)] = (ae|bf) - (af|be)
   const double* vvvv_as = nullptr;
+  // the FP64 ladder blocks were freed after their tensor-core packs were
+  // cached (split precision); the pointers remain the cache keys
+  bool vvvv_released = false, vvvv_as_released = false;
   // (N-1) Fock slot blocks per spin (0 = alpha, 1 = beta), real and complex
   const double *foo[2] = {nullptr, nullptr}, *fov[2] = {nullptr, nullptr},
                *fvv[2] = {nullptr, nullptr};

@@ -5,6 +5,7 @@
 // micro-iteration (Eq. 9) and the cumulant history (Eqs. 5-6).  Each residual
 // evaluation is one CUDA graph (captured on first use); the host reads one
 // 8-byte convergence word per micro-iteration.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -50,6 +51,7 @@ struct rteom_ctx {
   long long steps = 0, micro_total = 0;
   long long graph_kernels = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
+  bool tune_first = false;  // run the next residual eagerly for the autotuner
   bool graph_timed[2] = {false, false};            // captured with event-record nodes
   std::vector<Engine::GraphPair> graph_pairs[2];
   Engine::GraphTally graph_tally[2];
@@ -183,6 +185,18 @@ void run_residual(rteom_ctx* c, int which) {
   double* R = which == 0 ? c->R_N : c->R_K;
   if (c->E.timing && !c->E.graph_timing_ok) {  // eager, every kernel bracketed by events
     compute_residual(c->E, c->op, t, R);
+    return;
+  }
+  if (c->tune_first) {  // eager, the autotuner timing shapes it has not seen
+    c->tune_first = false;
+    c->E.tuning = true;
+    try {
+      compute_residual(c->E, c->op, t, R);
+    } catch (...) {
+      c->E.tuning = false;
+      throw;
+    }
+    c->E.tuning = false;
     return;
   }
   if (c->graph[which] && c->graph_timed[which] != c->E.timing) drop_graph(c, which);
@@ -322,13 +336,18 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   double* vvvv = c->dmalloc(8ull * nV * nV * nV * nV);
   // scratch arena for set-up contractions and, later, the residual
   E.dry = true;
+  if (const char* v = std::getenv("RTEOM_AUTOTUNE")) E.autotune = std::atoi(v) != 0;
   E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;  // plan the residual's scratch as it will run
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
   E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
   compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
                    reinterpret_cast<double*>(uintptr_t(4096)));
   int64_t need = E.arena.peak_bytes() / 8;
-  int64_t setup_need = (int64_t)nV * nV * nV * nV + 64;  // (ae|bf) before its permute
+  // the ladder block is built in chunks of ce values of e, each through a
+  // GEMM output of ce*nV^3 doubles that is then permuted into place
+  const int64_t nv3 = (int64_t)nV * nV * nV;
+  const int ce = (int)std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) / nv3));
+  int64_t setup_need = ce * nv3 + 64;
   if (setup_need > need) need = setup_need;
   E.dry = false;
   E.tensor_cores = false;  // set-up contractions in FP64
@@ -346,9 +365,20 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
              make_tensor(ovov, false, {nO, nV, nO, nV}));
   E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lvv, nV, nV), 0.0,
              make_tensor(ovvv, false, {nO, nV, nV, nV}));
-  // ladder layout [e][f][a][b] = (ae|bf) = sum_Q L_ea L_fb
-  E.contract("Qea,Qfb->efab", 1.0, Lt(Lvv, nV, nV), Lt(Lvv, nV, nV), 0.0,
-             make_tensor(vvvv, false, {nV, nV, nV, nV}));
+  // ladder layout [e][f][a][b] = (ae|bf) = sum_Q L_ea L_fb, built for ce
+  // values of e at a time from LvvT[e][a][Q] = L_ea
+  {
+    double* LvvT = c->dmalloc(8ull * nchol * nV * nV);
+    E.axpy("Qea->eaQ", 1.0, Lt(Lvv, nV, nV), 0.0, make_tensor(LvvT, false, {nV, nV, nchol}));
+    for (int e0 = 0; e0 < nV; e0 += ce) {
+      const int n = std::min(ce, nV - e0);
+      E.contract("eaQ,Qfb->efab", 1.0,
+                 make_tensor(LvvT + (int64_t)e0 * nV * nchol, false, {n, nV, nchol}),
+                 Lt(Lvv, nV, nV), 0.0, make_tensor(vvvv + e0 * nv3, false, {n, nV, nV, nV}));
+    }
+    RT_CUDA(cudaStreamSynchronize(st));
+    c->dfree(LvvT);
+  }
   // antisymmetrised (me|nf) - (mf|ne), shared by the W_mbej builds
   double* ovov_as = c->dmalloc(8ull * nO * nV * nO * nV);
   {
@@ -410,7 +440,6 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   RT_CUDA(cudaStreamSynchronize(st));
   // split precision: tensor-core contractions inside the residual only (the
   // set-up integrals above stay FP64); pipeline timeouts land in maxdiff[1].
-  // One eager residual on T(0) packs every constant tensor-core operand once.
   if (c->precision == RTEOM_SPLIT_TF32) {
     gemm_tc_init();
     E.tensor_cores = true;
@@ -419,10 +448,30 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
     E.persistent_alloc = [c](int64_t floats) {
       return reinterpret_cast<float*>(c->dmalloc(4ull * (floats > 0 ? floats : 1)));
     };
+  }
+  // In split precision one eager residual on T(0) (into the scratch
+  // amplitude set) packs every constant tensor-core operand once, and the
+  // autotuner times the GEMM shapes the process has not seen.  In FP64 the
+  // first residual of the propagation runs eagerly for the autotuner instead.
+  if (c->precision == RTEOM_SPLIT_TF32) {
+    E.tuning = E.autotune;
     E.tc_cache_fill = true;
-    compute_residual(E, c->op, c->T_N, c->R_N);
+    compute_residual(E, c->op, c->T_N, c->R_K);
     E.tc_cache_fill = false;
+    E.tuning = false;
     RT_CUDA(cudaStreamSynchronize(st));
+    // the ladder contractions now read only their packed operands: free the
+    // FP64 ladder blocks (the largest arrays of the context)
+    if (E.tc_cached(vvvv)) {
+      c->dfree(vvvv);
+      op.vvvv_released = true;
+    }
+    if (E.tc_cached(vvvv_as)) {
+      c->dfree(vvvv_as);
+      op.vvvv_as_released = true;
+    }
+  } else {
+    c->tune_first = E.autotune;
   }
 }
 
@@ -556,8 +605,8 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
     return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64 or RTEOM_SPLIT_TF32");
   if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
-  if ((double)(nvir + 1) * (nvir + 1) * (nvir + 1) * (nvir + 1) > 6.0e9)
-    return bad(RTEOM_ERR_ARG, "nvir too large for the cached (ae|bf) ladder block of this build");
+  if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)
+    return bad(RTEOM_ERR_ARG, "nvir too large: (nvir+1)^2 pair indices must fit 32 bits");
   if (!all_finite(eps, nb) || (nchol && !all_finite(L, size_t(nchol) * nb * nb)) ||
       (t1_gs && !all_finite(t1_gs, size_t(nocc) * nvir)) ||
       (t2_gs && !all_finite(t2_gs, size_t(nocc) * nocc * nvir * nvir)))

@@ -209,3 +209,19 @@ def test_timed_and_untimed_graphs_agree_bitwise():
         tm = g.timing()
     assert np.array_equal(C1, C2)
     assert tm["ladder"]["launches"] > 0 and tm["ladder"]["ms"] > 0
+
+
+def test_autotuned_and_heuristic_launches_agree(monkeypatch):
+    """The autotuner changes tile shapes and K splits (summation order only):
+    the propagation must agree with the heuristic launches to rounding."""
+    p = gen_problem(5, 30, 40, 71)
+    monkeypatch.setenv("RTEOM_AUTOTUNE", "0")
+    with _ctx(p) as g:
+        C0 = g.propagate(6, 0.05, tol=1e-12)
+    monkeypatch.setenv("RTEOM_AUTOTUNE", "1")
+    with _ctx(p) as g:
+        C1 = g.propagate(6, 0.05, tol=1e-12)
+    with _ctx(p) as g:                      # a second context reuses the choices: same bits
+        C2 = g.propagate(6, 0.05, tol=1e-12)
+    assert _relC(C1, C0) < 1e-12
+    assert np.array_equal(C1, C2)

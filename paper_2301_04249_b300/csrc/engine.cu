@@ -490,7 +490,16 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                        bool is_a) -> Packed {
       if (cached) return *cached;
       Packed pk;
-      const bool store = T.constant && tc_cache_fill && !dry && persistent_alloc;
+      const std::string ck = T.constant ? key(role, T) : std::string();
+      const bool keep = T.constant && (!tc_cache_select || tc_cache_allowed.count(ck) ||
+                                        (!tc_cache_cands.count(ck) && elems <= (int64_t(1) << 25)));
+      if (dry && T.constant) {
+        CacheCand& cc = tc_cache_cands[ck];
+        cc.bytes = 8 * elems;
+        cc.tensor = T.p;
+        if (plan_cached && keep) return Packed{nullptr, nullptr};  // held by the cache
+      }
+      const bool store = keep && tc_cache_fill && !dry && persistent_alloc;
       if (store) {
         pk.hi = persistent_alloc(elems);
         pk.lo = persistent_alloc(elems);
@@ -507,7 +516,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
              },
              "tc pack");
       if (store) {
-        tc_cache_[key(role, T)] = pk;
+        tc_cache_[ck] = pk;
         tc_cached_.insert(T.p);
       }
       return pk;
@@ -526,6 +535,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();
+  if (dry && std::getenv("RTEOM_PLAN_TRACE"))  // scratch planning: arena top inside this call
+    std::fprintf(stderr, "plan %-22s M=%lld N=%lld K=%lld %s arena %.3f GB (peak %.3f GB)\n", spec,
+                 (long long)Mt, (long long)Nt, (long long)Kt, use_tc ? "tc" : "f64",
+                 arena.mark() * 8e-9, arena.peak_bytes() * 1e-9);
   arena.release(mark);
 }
 

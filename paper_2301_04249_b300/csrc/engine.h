@@ -39,6 +39,19 @@ class Engine {
   // pass at set-up); later evaluations, captured graphs included, read them.
   bool tc_cache_fill = false;
   std::function<float*(int64_t)> persistent_alloc;  // floats, owned by the context
+  // Cache planning.  Dry runs with tensor_cores record every constant
+  // operand a pack would be cached for (key, bytes, tensor).  With
+  // tc_cache_select the cache holds only the keys in tc_cache_allowed (and
+  // small packs the plan did not see); with plan_cached, dry runs reserve no
+  // arena scratch for the packs the cache will hold.
+  struct CacheCand {
+    int64_t bytes = 0;
+    const double* tensor = nullptr;
+  };
+  std::map<std::string, CacheCand> tc_cache_cands;
+  std::set<std::string> tc_cache_allowed;
+  bool tc_cache_select = false;
+  bool plan_cached = false;
 
   // Autotuner.  A GEMM of at most tune_max_flops that is not a matrix-vector
   // product takes its launch configuration (FP64 tile shape and K slices, or

@@ -52,6 +52,7 @@ struct rteom_ctx {
   long long graph_kernels = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
   bool tune_first = false;  // run the next residual eagerly for the autotuner
+  long long cache_plan_bytes = 0;  // tensor-core pack cache planned at set-up
   bool graph_timed[2] = {false, false};            // captured with event-record nodes
   std::vector<Engine::GraphPair> graph_pairs[2];
   Engine::GraphTally graph_tally[2];
@@ -334,22 +335,74 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   double* ovov = c->dmalloc(8ull * nO * nV * nO * nV);
   double* ovvv = c->dmalloc(8ull * nO * nV * nV * nV);
   double* vvvv = c->dmalloc(8ull * nV * nV * nV * nV);
-  // scratch arena for set-up contractions and, later, the residual
-  E.dry = true;
+  // antisymmetrised (me|nf) - (mf|ne) and the packed same-spin ladder block
+  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  double* ovov_as = c->dmalloc(8ull * nO * nV * nO * nV);
+  double* vvvv_as = c->dmalloc(8ull * (npv > 0 ? npv * npv : 1));
+  op.oooo = oooo;
+  op.ooov = ooov;
+  op.oovv = oovv;
+  op.ovov = ovov;
+  op.ovvv = ovvv;
+  op.vvvv = vvvv;
+  op.ovov_as = ovov_as;
+  op.vvvv_as = vvvv_as;
+  c->ovov = ovov;
+
+  // scratch arena for set-up contractions and, later, the residual, sized
+  // by dry runs of the residual as it will run
+  const bool split = c->precision == RTEOM_SPLIT_TF32;
   if (const char* v = std::getenv("RTEOM_AUTOTUNE")) E.autotune = std::atoi(v) != 0;
-  E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;  // plan the residual's scratch as it will run
+  E.tensor_cores = split;
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
-  E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
-  compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
-                   reinterpret_cast<double*>(uintptr_t(4096)));
-  int64_t need = E.arena.peak_bytes() / 8;
+  auto dry_peak = [&]() {
+    E.dry = true;
+    E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
+    compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
+                     reinterpret_cast<double*>(uintptr_t(4096)));
+    E.dry = false;
+    return E.arena.peak_bytes() / 8;
+  };
+  E.plan_cached = split;
+  int64_t need = dry_peak();
   // the ladder block is built in chunks of ce values of e, each through a
   // GEMM output of ce*nV^3 doubles that is then permuted into place
   const int64_t nv3 = (int64_t)nV * nV * nV;
   const int ce = (int)std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) / nv3));
-  int64_t setup_need = ce * nv3 + 64;
+  const int64_t setup_need = ce * nv3 + 64;
+  if (split) {
+    // Memory plan of the tensor-core pack cache: it holds the packs of the
+    // FP64 ladder blocks (freed once packed) first, then the other constant
+    // operands from small to large, as many as fit beside the arena and the
+    // allocations still to come (amplitude sets, set-up temporaries, 1 GB
+    // margin).  A constant left out is packed into the arena at every use.
+    const int64_t later = 4 * 16 * (int64_t)c->g.total() + 8ll * nchol * nV * nV +
+                          8ll * O * O * V * V + (int64_t(1) << 30);
+    size_t fr = 0, tot = 0;
+    RT_CUDA(cudaMemGetInfo(&fr, &tot));
+    std::vector<std::pair<std::string, Engine::CacheCand>> order(E.tc_cache_cands.begin(),
+                                                                 E.tc_cache_cands.end());
+    auto ladder = [&](const Engine::CacheCand& x) {
+      return x.tensor == vvvv || x.tensor == vvvv_as;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](const auto& a, const auto& b) {
+      if (ladder(a.second) != ladder(b.second)) return ladder(a.second);
+      return a.second.bytes < b.second.bytes;
+    });
+    E.tc_cache_select = true;
+    for (size_t keep = order.size();; --keep) {
+      E.tc_cache_allowed.clear();
+      int64_t cache_bytes = 0;
+      for (size_t k = 0; k < keep; ++k) {
+        E.tc_cache_allowed.insert(order[k].first);
+        cache_bytes += order[k].second.bytes;
+      }
+      need = dry_peak();
+      c->cache_plan_bytes = cache_bytes;
+      if (8 * std::max(need, setup_need) + cache_bytes + later <= (int64_t)fr || keep == 0) break;
+    }
+  }
   if (setup_need > need) need = setup_need;
-  E.dry = false;
   E.tensor_cores = false;  // set-up contractions in FP64
   c->arena_doubles = need + 1024;
   c->arena_base = c->dmalloc(8ull * c->arena_doubles);
@@ -380,26 +433,14 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
     c->dfree(LvvT);
   }
   // antisymmetrised (me|nf) - (mf|ne), shared by the W_mbej builds
-  double* ovov_as = c->dmalloc(8ull * nO * nV * nO * nV);
   {
     const Tensor src = make_tensor(ovov, false, {nO, nV, nO, nV});
     const Tensor dst = make_tensor(ovov_as, false, {nO, nV, nO, nV});
     E.axpy("menf->menf", 1.0, src, 0.0, dst);
     E.axpy("mfne->menf", -1.0, src, 1.0, dst);
   }
-  op.ovov_as = ovov_as;
   // packed antisymmetric ladder block for the same-spin T2 blocks
-  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
-  double* vvvv_as = c->dmalloc(8ull * (npv > 0 ? npv * npv : 1));
   E.launch(kElementwise, 0.0, [&] { pack_ladder_antisym(vvvv, vvvv_as, nV, st); });
-  op.vvvv_as = vvvv_as;
-  op.oooo = oooo;
-  op.ooov = ooov;
-  op.oovv = oovv;
-  op.ovov = ovov;
-  op.ovvv = ovvv;
-  op.vvvv = vvvv;
-  c->ovov = ovov;
 
   // E_N^corr (Eq. 3) from the closed-shell ground-state amplitudes
   c->partial = c->dmalloc(16ull * 2048);

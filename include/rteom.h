@@ -53,12 +53,24 @@ extern "C" {
 /* precision forms */
 #define RTEOM_FP64        0   /* every contraction and update in FP64           */
 #define RTEOM_SPLIT_BF16  1   /* reserved (not built): split-BF16 contractions  */
-#define RTEOM_SPLIT_TF32  2   /* contractions of at least 5e7 FLOP on the tensor
-                                 cores as split-TF32 products (x = hi + lo,
-                                 hi*hi + hi*lo + lo*hi) with FP32 accumulation
-                                 over slices of at most 512 of K, slices summed
-                                 in FP64; every other step (small contractions,
-                                 Adams-Moulton update, cumulant, phases) FP64 */
+#define RTEOM_SPLIT_TF32  2   /* contractions of at least 5e7 FLOP (and smaller
+                                 ones the autotuner finds faster there) on the
+                                 tensor cores as split-TF32 products (x = hi +
+                                 lo, hi*hi + hi*lo + lo*hi) with FP32
+                                 accumulation over slices of at most 512 of K,
+                                 slices summed as compensated FP32 pairs; every
+                                 other step (small contractions, Adams-Moulton
+                                 update, cumulant, phases) FP64 */
+#define RTEOM_FP64_OZAKI  3   /* FP64-accurate contractions on the BF16 tensor
+                                 cores (no counterpart in the paper): operands
+                                 sliced into seven 8-bit digit planes with
+                                 per-row power-of-two scales (Ozaki et al.,
+                                 Numer. Algorithms 59, 2012), the 28 leading
+                                 digit-pair products summed exactly in FP32 over
+                                 chunks of 128 of K and accumulated as
+                                 compensated pairs (about 2^-48 relative to the
+                                 row scales); contractions below 5e7 FLOP and
+                                 every other step as in RTEOM_FP64 */
 
 /* flags for rteom_create */
 #define RTEOM_FLAG_CUMULANT_NO_FOV 1  /* cumulant integrand without sum f_ia t_i^a,
@@ -83,7 +95,8 @@ typedef struct rteom_ctx rteom_ctx;
  *             NULL; t1_gs/t2_gs only enter E_N^corr of Eq. 3:
  *             E = sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
  *  core_index spatial index c of the ionised orbital, 0 <= c < O
- *  precision  RTEOM_FP64 or RTEOM_SPLIT_TF32 (RTEOM_SPLIT_BF16: RTEOM_ERR_ARG)
+ *  precision  RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI
+ *             (RTEOM_SPLIT_BF16: RTEOM_ERR_ARG)
  *  flags      RTEOM_FLAG_* bits
  *  cuda_stream cudaStream_t to run on, or NULL for a non-blocking stream
  *             created and owned by the context
@@ -222,7 +235,8 @@ typedef struct rteom_server rteom_server;
  *  mem_budget_bytes  device memory the running requests may hold (0: 80 % of
  *                    the free memory at creation)
  *  max_active        slots: requests running at once (>= 1)
- *  precision         RTEOM_FP64 or RTEOM_SPLIT_TF32 for every request
+ *  precision         RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI for
+ *                    every request
  */
 int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_active,
                         int precision);

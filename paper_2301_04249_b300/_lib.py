@@ -17,6 +17,7 @@ RTEOM_ERR_STATE = -6
 RTEOM_FP64 = 0
 RTEOM_SPLIT_BF16 = 1
 RTEOM_SPLIT_TF32 = 2
+RTEOM_FP64_OZAKI = 3
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
 RTEOM_REQ_QUEUED = 0
 RTEOM_REQ_RUNNING = 1

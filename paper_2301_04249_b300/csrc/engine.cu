@@ -123,12 +123,12 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::string, GemmChoice> g_tune;  // process-wide autotuner choices
 
-std::string tune_key(const GemmDesc& g, bool tc_ok) {
+std::string tune_key(const GemmDesc& g, int form) {
   char buf[320];
   std::snprintf(buf, sizeof buf, "%d,%d,%d,%d|%d%d%d%d|%lld,%lld,%lld,%lld,%lld,%lld|%d|%d", g.M,
                 g.N, g.K, g.batch, (int)g.Acplx, (int)g.Bcplx, (int)g.transA, (int)g.transB,
                 (long long)g.lda, (long long)g.ldb, (long long)g.ldc, (long long)g.strideA,
-                (long long)g.strideB, (long long)g.strideC, (int)(g.beta != 0.0), (int)tc_ok);
+                (long long)g.strideB, (long long)g.strideC, (int)(g.beta != 0.0), form);
   return buf;
 }
 
@@ -168,7 +168,7 @@ std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
       gemm_f64_tile_shape(t, &bm, &bn);
       const int64_t blocks = (int64_t)((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.batch * s;
       if (s > 1 && blocks > 8 * 148) break;
-      out.push_back({false, t, s});
+      out.push_back({false, false, t, s});
     }
   }
   return out;
@@ -189,10 +189,11 @@ bool stream_capturing(cudaStream_t st) {
 // otherwise every candidate runs once (screened out when over twice the
 // best so far) and then twice more timed, and the fastest is returned.  Operands the tensor-core cache would hold are packed
 // outside the timing.
-void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool a_const, bool b_const,
-                            GemmChoice* out) {
+void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_const,
+                            bool b_const, GemmChoice* out) {
   std::vector<GemmChoice> cands = f64_candidates(g);
-  if (tc_ok) cands.push_back({true, -1, 0});
+  if (tc_ok) cands.push_back({true, false, -1, 0});
+  if (oz_ok) cands.push_back({false, true, -1, 0});
   const int64_t mark = arena.mark();
   GemmDesc base = g;
   base.beta = 0.0;
@@ -201,41 +202,70 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool a_const, bool b_
   base.C = arena.alloc((int64_t)g.M * g.N * g.batch * ((g.Acplx || g.Bcplx) ? 2 : 1));
   int64_t wsmax = 0;
   for (const auto& c : cands) {
-    if (c.tc) continue;
+    if (c.tc || c.oz) continue;
     GemmDesc d = base;
     d.tile = c.tile;
     d.splits = c.splits;
     wsmax = std::max(wsmax, gemm_f64_workspace(d));
   }
   double* ws = wsmax ? arena.alloc(wsmax) : nullptr;
-  float *ahi = nullptr, *alo = nullptr, *bhi = nullptr, *blo = nullptr;
-  float2* P = nullptr;
+  auto bytes_alloc = [&](int64_t bytes) { return static_cast<void*>(arena.alloc((bytes + 7) / 8)); };
+  void *a0 = nullptr, *a1 = nullptr, *b0 = nullptr, *b1 = nullptr, *P = nullptr;
   if (tc_ok) {
     const TcLayout L = gemm_tc_layout(base);
-    ahi = reinterpret_cast<float*>(arena.alloc((L.a_elems + 1) / 2));
-    alo = reinterpret_cast<float*>(arena.alloc((L.a_elems + 1) / 2));
-    bhi = reinterpret_cast<float*>(arena.alloc((L.b_elems + 1) / 2));
-    blo = reinterpret_cast<float*>(arena.alloc((L.b_elems + 1) / 2));
-    if (L.p_elems) P = reinterpret_cast<float2*>(arena.alloc(L.p_elems));
+    a0 = bytes_alloc(4 * L.a_elems);
+    a1 = bytes_alloc(4 * L.a_elems);
+    b0 = bytes_alloc(4 * L.b_elems);
+    b1 = bytes_alloc(4 * L.b_elems);
+    if (L.p_elems) P = bytes_alloc(8 * L.p_elems);
+  }
+  if (oz_ok) {
+    const OzLayout L = gemm_oz_layout(base);
+    a0 = bytes_alloc(2 * L.planes * L.a_elems);
+    a1 = bytes_alloc(4 * L.a_rows);
+    b0 = bytes_alloc(2 * L.planes * L.b_elems);
+    b1 = bytes_alloc(4 * L.b_rows);
+    if (L.p_elems) P = bytes_alloc(8 * L.p_elems);
   }
   if (out == nullptr || dry) {
     arena.release(mark);
     return;
   }
-  if (tc_ok) {
-    if (a_const) gemm_tc_pack_a(base, ahi, alo, stream);
-    if (b_const) gemm_tc_pack_b(base, bhi, blo, stream);
+  auto pack_a = [&] {
+    if (tc_ok)
+      gemm_tc_pack_a(base, static_cast<float*>(a0), static_cast<float*>(a1), stream);
+    else
+      gemm_oz_pack_a(base, static_cast<uint16_t*>(a0), static_cast<int*>(a1), stream);
+  };
+  auto pack_b = [&] {
+    if (tc_ok)
+      gemm_tc_pack_b(base, static_cast<float*>(b0), static_cast<float*>(b1), stream);
+    else
+      gemm_oz_pack_b(base, static_cast<uint16_t*>(b0), static_cast<int*>(b1), stream);
+  };
+  if (tc_ok || oz_ok) {
+    if (a_const) pack_a();
+    if (b_const) pack_b();
   }
   cudaEvent_t e0 = get_event(), e1 = get_event();
   float best_ms = std::numeric_limits<float>::infinity();
   GemmChoice best;
   for (const auto& c : cands) {
     auto run = [&] {
-      if (c.tc) {
-        if (!a_const) gemm_tc_pack_a(base, ahi, alo, stream);
-        if (!b_const) gemm_tc_pack_b(base, bhi, blo, stream);
-        gemm_tc_mma(base, ahi, alo, bhi, blo, P, tc_err, stream);
-        gemm_tc_finalize(base, P, stream);
+      if (c.tc || c.oz) {
+        if (!a_const) pack_a();
+        if (!b_const) pack_b();
+        if (c.tc) {
+          gemm_tc_mma(base, static_cast<float*>(a0), static_cast<float*>(a1),
+                      static_cast<float*>(b0), static_cast<float*>(b1), static_cast<float2*>(P),
+                      tc_err, stream);
+          gemm_tc_finalize(base, static_cast<float2*>(P), stream);
+        } else {
+          gemm_oz_mma(base, static_cast<uint16_t*>(a0), static_cast<int*>(a1),
+                      static_cast<uint16_t*>(b0), static_cast<int*>(b1), static_cast<double*>(P),
+                      tc_err, stream);
+          gemm_oz_finalize(base, static_cast<double*>(P), stream);
+        }
       } else {
         GemmDesc d = base;
         d.tile = c.tile;
@@ -391,8 +421,9 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   };
 
   const double mult0 = (A.cplx && B.cplx) ? 8.0 : (A.cplx || B.cplx) ? 4.0 : 2.0;
-  bool use_tc =
-      tensor_cores && mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt >= tc_min_flops;
+  const double flops0 = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
+  bool use_tc = tensor_cores && flops0 >= tc_min_flops;
+  bool use_oz = fp64_emulation && flops0 >= oz_min_flops;
 
   GemmDesc g;
   g.M = (int)Mt;
@@ -413,13 +444,16 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   g.beta = bPC ? 0.0 : beta;
 
   // launch configuration from the autotuner, when it has one for this shape
-  const double flops0 = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
-  const bool tunable = autotune && !use_tc && !gemm_f64_is_gemv(g) && flops0 <= tune_max_flops;
+  const bool tunable =
+      autotune && !use_tc && !use_oz && !gemm_f64_is_gemv(g) && flops0 <= tune_max_flops;
   const bool tc_ok = tensor_cores && flops0 >= tc_tune_min_flops;
-  const std::string tkey = tunable ? tune_key(g, tc_ok) : std::string();
+  const bool oz_ok = fp64_emulation && flops0 >= tc_tune_min_flops;
+  const std::string tkey = tunable ? tune_key(g, tc_ok ? 1 : (oz_ok ? 2 : 0)) : std::string();
   GemmChoice choice;
   bool chosen = tunable && tune_lookup(tkey, &choice);
   if (chosen && choice.tc) use_tc = true;
+  if (chosen && choice.oz) use_oz = true;
+  const bool packed_path = use_tc || use_oz;
 
   // tensor-core operands of constant tensors may already be packed
   auto key = [&](const char* role, const Tensor& T) {
@@ -429,11 +463,11 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   };
   const Packed* cA = nullptr;
   const Packed* cB = nullptr;
-  if (use_tc && A.constant) {
+  if (packed_path && A.constant) {
     auto it = tc_cache_.find(key("A", A));
     if (it != tc_cache_.end()) cA = &it->second;
   }
-  if (use_tc && B.constant) {
+  if (packed_path && B.constant) {
     auto it = tc_cache_.find(key("B", B));
     if (it != tc_cache_.end()) cB = &it->second;
   }
@@ -453,16 +487,17 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   g.B = Buse.p;
   g.C = Cuse.p;
 
-  if (tunable && dry) tuning_scratch(g, tc_ok, A.constant, B.constant, nullptr);
+  if (tunable && dry) tuning_scratch(g, tc_ok, oz_ok, A.constant, B.constant, nullptr);
   if (tunable && !chosen && tuning && !dry && !stream_capturing(stream)) {
     GemmChoice c;
-    tuning_scratch(g, tc_ok, A.constant, B.constant, &c);
+    tuning_scratch(g, tc_ok, oz_ok, A.constant, B.constant, &c);
     choice = tune_store(tkey, c);
     chosen = true;
     ++tuned;
     if (choice.tc) use_tc = true;
+    if (choice.oz) use_oz = true;
   }
-  if (chosen && !choice.tc) {
+  if (chosen && !choice.tc && !choice.oz) {
     g.tile = choice.tile;
     g.splits = choice.splits;
   }
@@ -470,12 +505,63 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   const std::string label =
       trace_on() ? std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
                        " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
-                       (use_tc ? std::string(" tc") + (cA ? " cA" : "") + (cB ? " cB" : "")
-                               : " s=" + std::to_string(gemm_f64_splits(g))) +
+                       (use_tc || use_oz
+                            ? std::string(use_tc ? " tc" : " oz") + (cA ? " cA" : "") +
+                                  (cB ? " cB" : "")
+                            : " s=" + std::to_string(gemm_f64_splits(g))) +
                        (bPA ? " pA" : "") + (bPB ? " pB" : "") + (bPC ? " pC" : "")
                  : std::string();
   if (cls == kLadder && !dry) nvtxRangePushA("rteom_ladder");
-  if (!use_tc) {
+  // packed operand of the tensor-core paths: from the cache, stored in it
+  // (constant tensors during the cache fill), or packed into the arena
+  auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t bytes0,
+                     int64_t bytes1, bool is_a) -> Packed {
+    if (cached) return *cached;
+    Packed pk;
+    const std::string ck = T.constant ? key(role, T) : std::string();
+    const int64_t bytes = bytes0 + bytes1;
+    const bool keep = T.constant && (!tc_cache_select || tc_cache_allowed.count(ck) ||
+                                      (!tc_cache_cands.count(ck) && bytes <= (int64_t(1) << 28)));
+    if (dry && T.constant) {
+      CacheCand& cc = tc_cache_cands[ck];
+      cc.bytes = bytes;
+      cc.tensor = T.p;
+      if (plan_cached && keep) return Packed{};  // held by the cache
+    }
+    const bool store = keep && tc_cache_fill && !dry && persistent_alloc;
+    if (store) {
+      pk.p0 = persistent_alloc(bytes0);
+      pk.p1 = persistent_alloc(bytes1);
+    } else {
+      pk.p0 = arena.alloc((bytes0 + 7) / 8);
+      pk.p1 = arena.alloc((bytes1 + 7) / 8);
+    }
+    launch(kPermute, 0.0,
+           [&] {
+             if (use_tc) {
+               float* hi = static_cast<float*>(pk.p0);
+               float* lo = static_cast<float*>(pk.p1);
+               if (is_a)
+                 gemm_tc_pack_a(g, hi, lo, stream);
+               else
+                 gemm_tc_pack_b(g, hi, lo, stream);
+             } else {
+               uint16_t* planes = static_cast<uint16_t*>(pk.p0);
+               int* expo = static_cast<int*>(pk.p1);
+               if (is_a)
+                 gemm_oz_pack_a(g, planes, expo, stream);
+               else
+                 gemm_oz_pack_b(g, planes, expo, stream);
+             }
+           },
+           use_tc ? "tc pack" : "oz pack");
+    if (store) {
+      tc_cache_[ck] = pk;
+      tc_cached_.insert(T.p);
+    }
+    return pk;
+  };
+  if (!packed_path) {
     const int64_t w = gemm_f64_workspace(g);
     if (w) g.work = arena.alloc(w);
     // operands read once, output written (or slabs written and read back)
@@ -484,54 +570,43 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                                 (C.cplx ? 2 : 1) * (double)Mt * Nt * Bt * (beta != 0.0 ? 2 : 1)) +
                          16.0 * (double)w;
     launch(cls, flops, [&] { gemm_f64(g, stream); }, label, bytes);
-  } else {
+  } else if (use_tc) {
     const TcLayout L = gemm_tc_layout(g);
-    auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t elems,
-                       bool is_a) -> Packed {
-      if (cached) return *cached;
-      Packed pk;
-      const std::string ck = T.constant ? key(role, T) : std::string();
-      const bool keep = T.constant && (!tc_cache_select || tc_cache_allowed.count(ck) ||
-                                        (!tc_cache_cands.count(ck) && elems <= (int64_t(1) << 25)));
-      if (dry && T.constant) {
-        CacheCand& cc = tc_cache_cands[ck];
-        cc.bytes = 8 * elems;
-        cc.tensor = T.p;
-        if (plan_cached && keep) return Packed{nullptr, nullptr};  // held by the cache
-      }
-      const bool store = keep && tc_cache_fill && !dry && persistent_alloc;
-      if (store) {
-        pk.hi = persistent_alloc(elems);
-        pk.lo = persistent_alloc(elems);
-      } else {
-        pk.hi = reinterpret_cast<float*>(arena.alloc((elems + 1) / 2));
-        pk.lo = reinterpret_cast<float*>(arena.alloc((elems + 1) / 2));
-      }
-      launch(kPermute, 0.0,
-             [&] {
-               if (is_a)
-                 gemm_tc_pack_a(g, pk.hi, pk.lo, stream);
-               else
-                 gemm_tc_pack_b(g, pk.hi, pk.lo, stream);
-             },
-             "tc pack");
-      if (store) {
-        tc_cache_[ck] = pk;
-        tc_cached_.insert(T.p);
-      }
-      return pk;
-    };
-    const Packed pa = operand("A", A, cA, L.a_elems, true);
-    const Packed pb = operand("B", B, cB, L.b_elems, false);
+    const Packed pa = operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true);
+    const Packed pb = operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false);
     float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
     // packed hi/lo operands read once; partial pairs written (and read back
     // by the finalize) or the output written directly
     const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 8.0 * (double)L.p_elems +
                          (L.ranges == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
     launch(cls, 3.0 * flops,
-           [&] { gemm_tc_mma(g, pa.hi, pa.lo, pb.hi, pb.lo, P, tc_err, stream); }, label, bytes);
+           [&] {
+             gemm_tc_mma(g, static_cast<float*>(pa.p0), static_cast<float*>(pa.p1),
+                         static_cast<float*>(pb.p0), static_cast<float*>(pb.p1), P, tc_err, stream);
+           },
+           label, bytes);
     if (L.ranges > 1)
       launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, P, stream); }, "tc finalize");
+  } else {
+    const OzLayout L = gemm_oz_layout(g);
+    const Packed pa = operand("A", A, cA, 2 * L.planes * L.a_elems, 4 * L.a_rows, true);
+    const Packed pb = operand("B", B, cB, 2 * L.planes * L.b_elems, 4 * L.b_rows, false);
+    double* P = L.p_elems ? arena.alloc(L.p_elems) : nullptr;
+    // digit planes read once; FP64 partials written or the output written
+    const double bytes = 2.0 * L.planes * (double)(L.a_elems + L.b_elems) +
+                         8.0 * (double)L.p_elems +
+                         (L.ranges == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
+    // counted as the FP64 GEMM it replaces (the tensor cores execute 28 times
+    // as many BF16 FLOPs, one product per digit pair)
+    launch(cls, flops,
+           [&] {
+             gemm_oz_mma(g, static_cast<uint16_t*>(pa.p0), static_cast<int*>(pa.p1),
+                         static_cast<uint16_t*>(pb.p0), static_cast<int*>(pb.p1), P, tc_err,
+                         stream);
+           },
+           label, bytes);
+    if (L.ranges > 1)
+      launch(kElementwise, 0.0, [&] { gemm_oz_finalize(g, P, stream); }, "oz finalize");
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();

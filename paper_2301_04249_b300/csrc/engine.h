@@ -19,7 +19,8 @@ enum KernelClass { kLadder = 0, kContract = 1, kPermute = 2, kElementwise = 3, k
 
 // Launch configuration of one GEMM shape picked by the autotuner.
 struct GemmChoice {
-  bool tc = false;         // tensor-core (split-TF32) path
+  bool tc = false;            // tensor-core (split-TF32) path
+  bool oz = false;            // tensor-core FP64 emulation (digit slicing)
   int tile = -1, splits = 0;  // FP64 kernel tile index and K slices
 };
 
@@ -33,12 +34,16 @@ class Engine {
   // cores (split TF32, FP32 accumulation); tc_err collects pipeline timeouts
   bool tensor_cores = false;
   double tc_min_flops = 5e7;
-  int* tc_err = nullptr;
+  int* tc_err = nullptr;  // also collects timeouts of the emulated-FP64 kernel
+  // FP64 emulation: contractions of at least oz_min_flops run as sliced BF16
+  // products on the tensor cores with FP64-level accuracy
+  bool fp64_emulation = false;
+  double oz_min_flops = 5e7;
   // Packed tensor-core operands of constant tensors, keyed by tensor, spec
   // and role.  Entries are created only while tc_cache_fill is set (an eager
   // pass at set-up); later evaluations, captured graphs included, read them.
   bool tc_cache_fill = false;
-  std::function<float*(int64_t)> persistent_alloc;  // floats, owned by the context
+  std::function<void*(int64_t)> persistent_alloc;  // bytes, owned by the context
   // Cache planning.  Dry runs with tensor_cores record every constant
   // operand a pack would be cached for (key, bytes, tensor).  With
   // tc_cache_select the cache holds only the keys in tc_cache_allowed (and
@@ -63,7 +68,7 @@ class Engine {
   bool autotune = true;
   bool tuning = false;
   double tune_max_flops = 2e9;
-  double tc_tune_min_flops = 1e6;
+  double tc_tune_min_flops = 1e6;  // also the floor of the emulated-FP64 candidate
   long long tuned = 0;  // GEMM shapes this engine has tuned
 
   // Timing.  Eager launches are each bracketed by events.  While a residual
@@ -160,10 +165,12 @@ class Engine {
     std::string what;
   };
   bool trace_on() const;
-  void tuning_scratch(const GemmDesc& g, bool tc_ok, bool a_const, bool b_const,
+  void tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_const, bool b_const,
                       GemmChoice* out);
+  // A packed tensor-core operand: TF32 hi / lo parts, or the digit planes
+  // and row exponents of the FP64 emulation.
   struct Packed {
-    float *hi, *lo;
+    void *p0 = nullptr, *p1 = nullptr;
   };
   std::map<std::string, Packed> tc_cache_;
   std::set<const double*> tc_cached_;  // tensors with at least one cached pack

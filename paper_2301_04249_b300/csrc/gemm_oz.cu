@@ -1,0 +1,629 @@
+// FP64-accurate GEMM on the BF16 tensor cores (tcgen05 kind::f16) by operand
+// slicing, after Ozaki's error-free splitting of floating-point matrix
+// products (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012).
+//
+// Every engine GEMM is first embedded as one real GEMM D = A' B'^T exactly as
+// in the split-TF32 kernel (complex operands stacked along rows, columns or
+// K).  Each row r of A' (and of B') gets a power-of-two scale 2^E_r with
+// |x| < 2^E_r over the row, and each element becomes the 56-bit integer
+// X = round(x 2^(55 - E_r)) written in S = 7 balanced base-256 digits
+//   x = 2^E_r sum_{s=1..7} d_s 2^(1 - 8 s),   d_s in [-128, 128],
+// each digit exact in BF16.  The product keeps the digit pairs (s, t) with
+// s + t <= 8 (28 of 49; the rest lie below 2^-53 of the row scales):
+//   (A'B'^T)_ij = 2^(E_i + E_j) sum_{d=2..8} 2^(2 - 8 d) sum_{s+t=d} sum_k d_s d_t.
+// Products of digits are exact in FP32 (|d_s d_t| <= 2^14), and a diagonal
+// accumulates at most 7 pairs over a chunk of 128 of K, at most 7 * 2^21 <
+// 2^24 in magnitude: every chunk sum in tensor memory is an exact integer.
+// The epilogue scales each chunk sum by 2^(2 - 8 d) (exact) and adds it to a
+// compensated FP32 pair (TwoSum, about 48 bits); the pair becomes one FP64
+// value at the end, times 2^(E_i + E_j).  The result carries about 2^-48 of
+// the row-scale product per term, against 2^-53 for FP64 FMA accumulation,
+// and runs on the tensor pipe instead of the FP64 pipe (about two operations
+// per clock per SM on this part).
+//
+// Operand layout: digit planes [S][batch][row tile][k tile][rows x 32] of
+// BF16 in 8 x 8 core matrices (K-major, no swizzle; 128 B between core
+// matrices along K, 512 B between 8-row groups).  A stage holds all seven
+// planes of one k tile of A (128 rows) and B (64 rows), 84 KB; two stages.
+// Tensor memory holds the seven diagonal accumulators, 7 x 64 columns.
+//
+// Warp roles (320 threads): warp 0 lane 0 issues the bulk copies, warp 1
+// owns the tensor memory and lane 0 issues the MMAs, warps 2-9 drain the
+// accumulators (warp w reads lanes 32*(w%4)..+31, column half (w-2)/4).
+// Every wait is bounded; on expiry the CTA records an error code, lets its
+// copies land, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace rteom {
+
+namespace oz {
+
+using namespace tc5;
+
+constexpr int S = 7;                       // digit planes per operand
+constexpr int BM = 128;                    // rows of A' per tile (TMEM lanes)
+constexpr int BN = 64;                     // rows of B' per tile (output columns)
+constexpr int BK = 32;                     // K per k tile (BF16, 64 bytes per row)
+constexpr int CHUNK_KT = 4;                // k tiles per exact chunk (128 of K)
+constexpr int STAGES = 2;
+constexpr uint32_t A_TILE = BM * BK * 2;   // 8 KB
+constexpr uint32_t B_TILE = BN * BK * 2;   // 4 KB
+constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint32_t TMEM_COLS = 512;        // 7 diagonals x 64 columns, rounded up
+constexpr int kZeroExp = INT_MIN / 4;      // scale exponent of an all-zero row
+constexpr size_t kSmemBytes = STAGES * (size_t)STAGE_BYTES + 256;
+static_assert(S * BN <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
+static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
+
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
+// K-major, N = bn, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// v * 2^k on the exponent bits (v finite); results below the normal range
+// become signed zeros, above it infinities.
+__device__ __forceinline__ double scale2(double v, int k) {
+  const long long u = __double_as_longlong(v);
+  const long long sign = u & (long long)0x8000000000000000ull;
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0) return __longlong_as_double(sign);
+  const int ne = e + k;
+  if (ne <= 0) return __longlong_as_double(sign);
+  if (ne >= 2047) return __longlong_as_double(sign | (0x7FFll << 52));
+  return __longlong_as_double((u & ~(0x7FFll << 52)) | ((long long)ne << 52));
+}
+
+// ---------------------------------------------------------------- packing
+struct PackArgs {
+  const double* src;
+  bool cplx;
+  int64_t s_r, s_c, s_b;  // element strides of logical rows, columns, batch
+  int R, C;               // logical extents of the source operand (rows x K)
+  int mode;               // 0 plain, 1 complex rows [Re; Im], 2 complex K [Re | Im], 3 complex B
+  int Rp, Kp, rowtile;    // packed extents (rows multiple of rowtile, K of 32)
+  __nv_bfloat16* planes;  // S planes of plane_elems
+  int64_t plane_elems;
+  int64_t s_out;          // elements per batch entry within a plane
+  int* expo;              // [batch][Rp] row scale exponents
+  bool rows_fast;         // consecutive threads walk packed rows (source rows contiguous)
+};
+
+// Value of the embedded real operand at packed (row rp, column kp).
+__device__ __forceinline__ double embedded(const PackArgs& p, int b, int rp, int kp) {
+  int r = rp, c = kp, part = 0;
+  bool neg = false, valid;
+  switch (p.mode) {
+    case 0:
+      valid = rp < p.R && kp < p.C;
+      break;
+    case 1:
+      part = rp >= p.R;
+      r = rp - part * p.R;
+      valid = rp < 2 * p.R && kp < p.C;
+      break;
+    case 2:
+      part = kp >= p.C;
+      c = kp - part * p.C;
+      valid = rp < p.R && kp < 2 * p.C;
+      break;
+    default: {  // rows n' = [n; n], K' = [k | k]: [[Re, Im], [-Im, Re]]
+      const int ro = rp >= p.R, ko = kp >= p.C;
+      r = rp - ro * p.R;
+      c = kp - ko * p.C;
+      valid = rp < 2 * p.R && kp < 2 * p.C;
+      part = ro != ko;
+      neg = ko && !ro;
+    }
+  }
+  if (!valid) return 0.0;
+  const int64_t off = b * p.s_b + r * p.s_r + c * p.s_c;
+  const double x = p.cplx ? p.src[2 * off + part] : p.src[off];
+  return neg ? neg_f64(x) : x;
+}
+
+// Row scale exponents: E = max biased exponent - 1022, so |x| < 2^E.
+__global__ void oz_expo_kernel(PackArgs p, int batch) {
+  const int64_t rows = (int64_t)batch * p.Rp;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < rows; w += nwarps) {
+    const int b = (int)(w / p.Rp), rp = (int)(w % p.Rp);
+    unsigned emax = 0;
+    for (int kp = lane; kp < p.Kp; kp += 32) {
+      const double x = embedded(p, b, rp, kp);
+      emax = max(emax, (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF));
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) p.expo[w] = emax == 0 ? kZeroExp : (int)emax - 1022;
+  }
+}
+
+// Digit planes: X = round(x 2^(55 - E)) on the integer ALUs, then balanced
+// base-256 digits from the least significant one.
+template <typename IDX>
+__global__ void oz_digits_kernel(PackArgs p, int batch) {
+  const IDX per = (IDX)p.Rp * (IDX)p.Kp;
+  const IDX n = per * (IDX)batch;
+  const int KT = p.Kp / BK;
+  for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < n;
+       e += (IDX)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const IDX q = e - (IDX)b * per;
+    int rp, kp;
+    if (p.rows_fast) {
+      rp = (int)(q % (IDX)p.Rp);
+      kp = (int)(q / (IDX)p.Rp);
+    } else {
+      rp = (int)(q / (IDX)p.Kp);
+      kp = (int)(q % (IDX)p.Kp);
+    }
+    const double x = embedded(p, b, rp, kp);
+    const int E = p.expo[(int64_t)b * p.Rp + rp];
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7FF);
+    long long X = 0;
+    if (ex != 0 && E != kZeroExp) {
+      const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = ex - 1020 - E;  // <= 2 because |x| < 2^E
+      unsigned long long a = 0;
+      if (sh >= 0)
+        a = m << sh;
+      else if (sh > -64)
+        a = (m + (1ull << (-sh - 1))) >> (-sh);
+      X = (u >> 63) ? -(long long)a : (long long)a;
+    }
+    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+    const int kt = kp / BK, kk = kp % BK;
+    const int64_t off = (int64_t)b * p.s_out +
+                        ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
+                        ((rr / 8) * (BK / 8) + kk / 8) * 64 + (rr % 8) * 8 + (kk % 8);
+#pragma unroll
+    for (int s = S - 1; s >= 1; --s) {
+      const int r = (int)(X & 255);
+      const int d = r >= 128 ? r - 256 : r;
+      p.planes[s * p.plane_elems + off] = __int2bfloat16_rn(d);
+      X = (X - d) >> 8;
+    }
+    p.planes[off] = __int2bfloat16_rn((int)X);
+  }
+}
+
+// ---------------------------------------------------------------- MMA kernel
+struct KArgs {
+  const __nv_bfloat16 *A, *B;  // digit planes
+  int64_t a_plane, b_plane;    // elements per plane
+  int64_t sA, sB;              // per-batch element strides within a plane
+  const int *ea, *eb;          // row scale exponents of A' [batch][Mp] and B' [batch][Np]
+  int KT, kpr, ranges;
+  double* P;                   // FP64 partials [batch*ranges][Mp][Np] when ranges > 1
+  int Mp, Np;
+  int* err;
+  double* C;
+  bool cplx;
+  int M, N, mode;              // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
+  int64_t ldc, sC;
+  double alpha, beta;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;  // chunk accumulated
+  uint64_t* acc_empty = acc_full + 1;   // chunk drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* issued = abort_flag + 1;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y, z = blockIdx.z;
+  const int b = z / g.ranges, rg = z % g.ranges;
+  const int kt0 = rg * g.kpr;
+  const int kt1 = min(g.KT, kt0 + g.kpr);
+  const int nk = max(kt1 - kt0, 0);
+  const int nchunks = (nk + CHUNK_KT - 1) / CHUNK_KT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, EPI_WARPS);
+    *abort_flag = 0;
+    *issued = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const __nv_bfloat16* A = g.A + b * g.sA + (int64_t)m_tile * g.KT * (BM * BK);
+    const __nv_bfloat16* B = g.B + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % STAGES;
+      if (k >= STAGES && !mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicExch(g.err, 11);
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const int64_t kt = kt0 + k;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll
+      for (int pl = 0; pl < S; ++pl)
+        bulk_load(st + pl * A_TILE, A + pl * g.a_plane + kt * (BM * BK), A_TILE, &full[s]);
+#pragma unroll
+      for (int pl = 0; pl < S; ++pl)
+        bulk_load(st + S * A_TILE + pl * B_TILE, B + pl * g.b_plane + kt * (BN * BK), B_TILE,
+                  &full[s]);
+      *issued = k + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // diagonal d = s + t (planes s, t counted from 0) accumulates in columns
+    // [d*BN, (d+1)*BN); a chunk's first MMA into d (s = 0) starts it afresh
+    const uint32_t idesc = idesc_bf16(BN);
+    for (int k = 0; k < nk; ++k) {
+      const int j = k / CHUNK_KT, kin = k % CHUNK_KT;
+      if (kin == 0 && j >= 1) {
+        if (!mbar_wait(acc_empty, (j - 1) & 1)) {
+          *abort_flag = 1;
+          atomicExch(g.err, 14);
+          break;
+        }
+      }
+      const int s = k % STAGES;
+      if (!mbar_wait(&full[s], (k / STAGES) & 1)) {
+        *abort_flag = 1;
+        atomicExch(g.err, 12);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+      for (int sa = 0; sa < S; ++sa) {
+#pragma unroll
+        for (int sb = 0; sb < S - sa; ++sb) {
+          const uint32_t dt = tmem + (uint32_t)((sa + sb) * BN);
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ++ks) {
+            const uint64_t ad = smem_desc(base + sa * A_TILE + ks * 256, 128, 512);
+            const uint64_t bd = smem_desc(base + S * A_TILE + sb * B_TILE + ks * 256, 128, 512);
+            mma_bf16(dt, ad, bd, idesc, (kin > 0 || ks > 0 || sa > 0) ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(&empty[s]);
+      if (kin == CHUNK_KT - 1 || k == nk - 1) mma_commit(acc_full);
+    }
+  } else if (warp >= 2) {
+    const int q = warp % 4;
+    const int h = (warp - 2) / 4;
+    const int row = 32 * q + lane;
+    float sum[32], cmp[32];
+#pragma unroll
+    for (int v = 0; v < 32; ++v) sum[v] = cmp[v] = 0.0f;
+    bool ok = nk > 0;
+#pragma unroll 1
+    for (int j = 0; j < nchunks; ++j) {
+      if (!mbar_wait(acc_full, j & 1)) {
+        ok = false;
+        atomicExch(g.err, 13);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll 1
+      for (int d = 0; d < S; ++d) {
+        const float w = __int_as_float((127 - 14 - 8 * d) << 23);  // 2^(2 - 8 (d + 2))
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + h * 32), r);
+#pragma unroll
+        for (int v = 0; v < 32; ++v) two_sum_acc(sum[v], cmp[v], __uint_as_float(r[v]) * w);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+    if (ok) {
+      const int mr = m_tile * BM + row;
+      const int er = g.ea[(int64_t)b * g.Mp + mr];
+      if (g.ranges == 1) {
+        int m = mr, part = 0;
+        if (g.mode == 1 && mr >= g.M) {
+          m = mr - g.M;
+          part = 1;
+        }
+        const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
+        if (row_ok) {
+#pragma unroll
+          for (int v = 0; v < 32; ++v) {
+            const int nr = n_tile * BN + h * 32 + v;
+            int n = nr, pt = part;
+            if (g.mode == 2 && nr >= g.N) {
+              n = nr - g.N;
+              pt = 1;
+            }
+            if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
+            const int ec = g.eb[(int64_t)b * g.Np + nr];
+            double val = 0.0;
+            if (er != kZeroExp && ec != kZeroExp)
+              val = scale2(f32_to_f64(sum[v]) + f32_to_f64(cmp[v]), er + ec);
+            if (g.alpha == -1.0)
+              val = neg_f64(val);
+            else if (g.alpha != 1.0)
+              val *= g.alpha;
+            double* cp =
+                g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldc + n) + pt;
+            *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
+          }
+        }
+      } else {
+        double* dst = g.P + ((int64_t)z * g.Mp + mr) * g.Np + (int64_t)n_tile * BN + h * 32;
+#pragma unroll
+        for (int v = 0; v < 32; ++v) {
+          const int ec = g.eb[(int64_t)b * g.Np + n_tile * BN + h * 32 + v];
+          dst[v] = (er != kZeroExp && ec != kZeroExp)
+                       ? scale2(f32_to_f64(sum[v]) + f32_to_f64(cmp[v]), er + ec)
+                       : 0.0;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    const int n = *issued;
+    for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
+      mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- finalize
+struct FinArgs {
+  const double* P;  // [batch*ranges][Mp][Np]
+  int Mp, Np, ranges;
+  int M, N, mode;
+  double* C;
+  bool cplx;
+  int64_t ldc, sC;
+  double alpha, beta;
+};
+
+__global__ void oz_finalize_kernel(FinArgs f, int batch) {
+  const int64_t per = (int64_t)f.M * f.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const int64_t q = e - (int64_t)b * per;
+    const int m = (int)(q / f.N), n = (int)(q % f.N);
+    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldc + n);
+    const int parts = f.cplx ? 2 : 1;
+    for (int part = 0; part < parts; ++part) {
+      const int mr = f.mode == 1 ? m + part * f.M : m;
+      const int nr = f.mode == 2 ? n + part * f.N : n;
+      double s = 0.0;
+      for (int z = 0; z < f.ranges; ++z)
+        s += f.P[(((int64_t)b * f.ranges + z) * f.Mp + mr) * f.Np + nr];
+      if (f.alpha == -1.0)
+        s = neg_f64(s);
+      else if (f.alpha != 1.0)
+        s *= f.alpha;
+      c[part] = f.beta == 0.0 ? s : (f.beta == 1.0 ? c[part] + s : fma(f.beta, c[part], s));
+    }
+  }
+}
+
+inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Plan {
+  int mode;  // 0 RR, 1 CR, 2 RC, 3 CC
+  int Mp, Np, Kp, KT, ranges, kpr;
+  int64_t a_elems, b_elems;  // BF16 per digit plane
+  int64_t p_elems;           // FP64 partials (0 with one range)
+};
+
+Plan plan(const GemmDesc& d) {
+  Plan p;
+  p.mode = (d.Acplx ? 1 : 0) + (d.Bcplx ? 2 : 0);
+  const int Ar = p.mode == 1 ? 2 * d.M : d.M;
+  const int Ak = p.mode == 3 ? 2 * d.K : d.K;
+  const int Br = (p.mode & 2) ? 2 * d.N : d.N;
+  p.Mp = roundup(std::max(Ar, 1), BM);
+  p.Np = roundup(std::max(Br, 1), BN);
+  p.Kp = roundup(std::max(Ak, 1), BK);
+  p.KT = p.Kp / BK;
+  // K ranges: fewest waves x k tiles per CTA, a range costing about four k
+  // tiles for writing and re-reading its partial tile
+  const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / BN) * d.batch;
+  double best = 0.0;
+  p.ranges = 1;
+  p.kpr = p.KT;
+  for (int r = 1; r <= p.KT; ++r) {
+    const int kpr = (p.KT + r - 1) / r;
+    if ((p.KT + kpr - 1) / kpr != r) continue;
+    if ((int64_t)d.batch * r > 65535) break;
+    const double waves = (double)((tiles * r + 147) / 148);
+    const double cost = waves * (kpr + (r > 1 ? 4 : 0));
+    if (r == 1 || cost < best) {
+      best = cost;
+      p.ranges = r;
+      p.kpr = kpr;
+    }
+  }
+  p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
+  p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
+  p.p_elems = p.ranges == 1 ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
+  return p;
+}
+
+int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
+
+void pack(PackArgs pa, int64_t elems, int batch, cudaStream_t st) {
+  const int64_t rows = (int64_t)batch * pa.Rp;
+  oz_expo_kernel<<<(int)std::min<int64_t>((rows * 32 + 255) / 256, 148 * 16), 256, 0, st>>>(
+      pa, batch);
+  RT_CHECK_LAUNCH();
+  if (elems < (int64_t(1) << 32) - (int64_t)256 * 148 * 16)
+    oz_digits_kernel<uint32_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  else
+    oz_digits_kernel<uint64_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  RT_CHECK_LAUNCH();
+}
+
+}  // namespace oz
+
+OzLayout gemm_oz_layout(const GemmDesc& d) {
+  const oz::Plan p = oz::plan(d);
+  OzLayout l;
+  l.planes = oz::S;
+  l.a_elems = p.a_elems;
+  l.b_elems = p.b_elems;
+  l.a_rows = (int64_t)p.Mp * d.batch;
+  l.b_rows = (int64_t)p.Np * d.batch;
+  l.p_elems = p.p_elems;
+  l.ranges = p.ranges;
+  l.padded_flops = 2.0 * oz::S * (oz::S + 1) / 2 * (double)p.Mp * p.Np * p.Kp * d.batch;
+  return l;
+}
+
+void gemm_oz_init() {
+  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)oz::kSmemBytes));
+}
+
+void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const oz::Plan p = oz::plan(d);
+  oz::PackArgs pa{};
+  pa.src = d.A;
+  pa.cplx = d.Acplx;
+  pa.s_r = d.transA ? 1 : d.lda;
+  pa.s_c = d.transA ? d.lda : 1;
+  pa.s_b = d.strideA;
+  pa.R = d.M;
+  pa.C = d.K;
+  pa.mode = p.mode == 1 ? 1 : (p.mode == 3 ? 2 : 0);
+  pa.Rp = p.Mp;
+  pa.Kp = p.Kp;
+  pa.rowtile = oz::BM;
+  pa.planes = reinterpret_cast<__nv_bfloat16*>(planes);
+  pa.plane_elems = p.a_elems;
+  pa.s_out = (int64_t)p.Mp * p.Kp;
+  pa.expo = expo;
+  pa.rows_fast = pa.s_r == 1 && pa.s_c != 1;
+  oz::pack(pa, p.a_elems, d.batch, st);
+}
+
+void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const oz::Plan p = oz::plan(d);
+  oz::PackArgs pb{};
+  pb.src = d.B;
+  pb.cplx = d.Bcplx;
+  pb.s_r = d.transB ? d.ldb : 1;  // rows of B' are the output columns n
+  pb.s_c = d.transB ? 1 : d.ldb;
+  pb.s_b = d.strideB;
+  pb.R = d.N;
+  pb.C = d.K;
+  pb.mode = p.mode == 2 ? 1 : (p.mode == 3 ? 3 : 0);
+  pb.Rp = p.Np;
+  pb.Kp = p.Kp;
+  pb.rowtile = oz::BN;
+  pb.planes = reinterpret_cast<__nv_bfloat16*>(planes);
+  pb.plane_elems = p.b_elems;
+  pb.s_out = (int64_t)p.Np * p.Kp;
+  pb.expo = expo;
+  pb.rows_fast = pb.s_r == 1 && pb.s_c != 1;
+  oz::pack(pb, p.b_elems, d.batch, st);
+}
+
+void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
+                 const int* eb, double* P, int* err, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const oz::Plan p = oz::plan(d);
+  if (p.Mp / oz::BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
+    throw Error(-1, "gemm_oz: grid too large");
+  oz::KArgs g{};
+  g.A = reinterpret_cast<const __nv_bfloat16*>(A);
+  g.B = reinterpret_cast<const __nv_bfloat16*>(B);
+  g.a_plane = p.a_elems;
+  g.b_plane = p.b_elems;
+  g.sA = (int64_t)p.Mp * p.Kp;
+  g.sB = (int64_t)p.Np * p.Kp;
+  g.ea = ea;
+  g.eb = eb;
+  g.KT = p.KT;
+  g.kpr = p.kpr;
+  g.ranges = p.ranges;
+  g.P = P;
+  g.Mp = p.Mp;
+  g.Np = p.Np;
+  g.err = err;
+  g.C = d.C;
+  g.cplx = d.Acplx || d.Bcplx;
+  g.M = d.M;
+  g.N = d.N;
+  g.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
+  g.ldc = d.ldc;
+  g.sC = d.strideC;
+  g.alpha = d.alpha;
+  g.beta = d.beta;
+  dim3 grid(p.Np / oz::BN, p.Mp / oz::BM, d.batch * p.ranges);
+  oz::oz_gemm_kernel<<<grid, oz::THREADS, oz::kSmemBytes, st>>>(g);
+  RT_CHECK_LAUNCH();
+}
+
+void gemm_oz_finalize(const GemmDesc& d, const double* P, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const oz::Plan p = oz::plan(d);
+  if (p.ranges == 1) return;
+  oz::FinArgs fa{};
+  fa.P = P;
+  fa.Mp = p.Mp;
+  fa.Np = p.Np;
+  fa.ranges = p.ranges;
+  fa.M = d.M;
+  fa.N = d.N;
+  fa.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
+  fa.C = d.C;
+  fa.cplx = d.Acplx || d.Bcplx;
+  fa.ldc = d.ldc;
+  fa.sC = d.strideC;
+  fa.alpha = d.alpha;
+  fa.beta = d.beta;
+  oz::oz_finalize_kernel<<<oz::grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+}  // namespace rteom

@@ -57,6 +57,30 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
                  const float* Blo, float2* P, int* err, cudaStream_t st);
 void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st);
 
+// FP64-accurate GEMM on the BF16 tensor cores (operand slicing into seven
+// 8-bit digit planes with per-row power-of-two scales; exact chunk sums,
+// compensated accumulation, about 2^-48 relative to the row scales), with
+// the same contract as gemm_f64: pack A and pack B (digit planes of
+// a_elems / b_elems BF16 each, and a_rows / b_rows row exponents), then the
+// MMA kernel, which writes C itself with one K range per tile or p_elems
+// FP64 partials that the finalize sums in range order.  gemm_oz_init() once
+// per process first.
+struct OzLayout {
+  int planes;
+  int64_t a_elems, b_elems;  // BF16 per digit plane
+  int64_t a_rows, b_rows;    // int row exponents
+  int64_t p_elems;           // FP64 partials; 0 = the MMA kernel writes C directly
+  int ranges;
+  double padded_flops;       // executed tensor-core FLOPs (28 digit-pair products)
+};
+OzLayout gemm_oz_layout(const GemmDesc& d);
+void gemm_oz_init();
+void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
+void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
+void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
+                 const int* eb, double* P, int* err, cudaStream_t st);
+void gemm_oz_finalize(const GemmDesc& d, const double* P, cudaStream_t st);
+
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
 // contiguous with dims out_dim[0..nd-1]; strides count elements.  A real
 // input may feed a complex output (imaginary part only scaled by beta).

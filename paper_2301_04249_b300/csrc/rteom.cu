@@ -351,10 +351,13 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
 
   // scratch arena for set-up contractions and, later, the residual, sized
   // by dry runs of the residual as it will run
-  const bool split = c->precision == RTEOM_SPLIT_TF32;
+  // forms with packed tensor-core operands (and a cache of the constant ones)
+  const bool split = c->precision == RTEOM_SPLIT_TF32 || c->precision == RTEOM_FP64_OZAKI;
   if (const char* v = std::getenv("RTEOM_AUTOTUNE")) E.autotune = std::atoi(v) != 0;
-  E.tensor_cores = split;
+  E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;
+  E.fp64_emulation = c->precision == RTEOM_FP64_OZAKI;
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
+  if (const char* v = std::getenv("RTEOM_OZ_MIN_FLOPS")) E.oz_min_flops = std::atof(v);
   auto dry_peak = [&]() {
     E.dry = true;
     E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
@@ -404,6 +407,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   }
   if (setup_need > need) need = setup_need;
   E.tensor_cores = false;  // set-up contractions in FP64
+  E.fp64_emulation = false;
   c->arena_doubles = need + 1024;
   c->arena_base = c->dmalloc(8ull * c->arena_doubles);
   E.arena.init(c->arena_base, c->arena_doubles);
@@ -479,22 +483,27 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   RT_CUDA(cudaMallocHost(&hp, 64));
   c->h_maxdiff = static_cast<unsigned long long*>(hp);
   RT_CUDA(cudaStreamSynchronize(st));
-  // split precision: tensor-core contractions inside the residual only (the
-  // set-up integrals above stay FP64); pipeline timeouts land in maxdiff[1].
-  if (c->precision == RTEOM_SPLIT_TF32) {
-    gemm_tc_init();
-    E.tensor_cores = true;
-    if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
+  // split precision and FP64 emulation: tensor-core contractions inside the
+  // residual only (the set-up integrals above are FP64); pipeline timeouts
+  // land in maxdiff[1].
+  if (split) {
+    if (c->precision == RTEOM_SPLIT_TF32) {
+      gemm_tc_init();
+      E.tensor_cores = true;
+    } else {
+      gemm_oz_init();
+      E.fp64_emulation = true;
+    }
     E.tc_err = reinterpret_cast<int*>(c->maxdiff + 1);
-    E.persistent_alloc = [c](int64_t floats) {
-      return reinterpret_cast<float*>(c->dmalloc(4ull * (floats > 0 ? floats : 1)));
+    E.persistent_alloc = [c](int64_t bytes) {
+      return static_cast<void*>(c->dmalloc(bytes > 0 ? bytes : 16));
     };
   }
-  // In split precision one eager residual on T(0) (into the scratch
-  // amplitude set) packs every constant tensor-core operand once, and the
-  // autotuner times the GEMM shapes the process has not seen.  In FP64 the
-  // first residual of the propagation runs eagerly for the autotuner instead.
-  if (c->precision == RTEOM_SPLIT_TF32) {
+  // With packed operands one eager residual on T(0) (into the scratch
+  // amplitude set) packs every constant operand the cache plan keeps, and
+  // the autotuner times the GEMM shapes the process has not seen.  In FP64
+  // the first residual of the propagation runs eagerly for the autotuner.
+  if (split) {
     E.tuning = E.autotune;
     E.tc_cache_fill = true;
     compute_residual(E, c->op, c->T_N, c->R_K);
@@ -642,8 +651,8 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   if (nocc < 1 || nvir < 1 || nchol < 0) return bad(RTEOM_ERR_ARG, "need nocc >= 1, nvir >= 1, nchol >= 0");
   if (core_index < 0 || core_index >= nocc) return bad(RTEOM_ERR_ARG, "core_index outside the occupied orbitals");
   if (!eps || (nchol > 0 && !L)) return bad(RTEOM_ERR_ARG, "eps (and L when nchol > 0) must be given");
-  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32)
-    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64 or RTEOM_SPLIT_TF32");
+  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 && precision != RTEOM_FP64_OZAKI)
+    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI");
   if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)

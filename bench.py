@@ -39,6 +39,8 @@ TF32_PER_BF16_NOMINAL = 1.1 / 2.25  # dense TF32 / dense BF16, nominal B300 figu
 MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
 LADDER_TC_PROFILE = os.path.join(HERE, "profiles", "ladder_tc_tf32_c2.txt")
+LADDER_OZ_PROFILE = os.path.join(HERE, "profiles", "ladder_oz_bf16_c2.txt")
+OZ_PRODUCTS = 28  # digit-pair BF16 products per emulated FP64 product
 
 
 def parse_args():
@@ -52,6 +54,7 @@ def parse_args():
     ap.add_argument("--max-micro", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 form")
+    ap.add_argument("--no-ozaki", action="store_true", help="skip the emulated-FP64 form")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=16)
     return ap.parse_args()
@@ -240,6 +243,46 @@ def split_summary(split, args, fp64_value, world, C_fp64, peaks):
     }}
 
 
+def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks):
+    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of the
+    emulated-FP64 form measured on the same workload and step counts."""
+    if run is None:
+        return None
+    lad = run["tm"]["ladder"]
+    v = world * args.steps / run["elapsed"]
+    bf16 = peaks.get("bf16_tflops")
+    avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
+    fl = lad["flops"] / max(lad["launches"], 1)  # FP64-equivalent
+    eq = fl / avg_s / 1e12 if lad["launches"] else None
+    ach = OZ_PRODUCTS * eq if eq else None
+    n = min(len(C_fp64), len(run["C"]))
+    Cf = np.asarray(C_fp64)[:n]
+    dC = float(np.abs(np.asarray(run["C"])[:n] - Cf).max())
+    return {"fp64_ozaki": {
+        "value": v, "unit": UNIT, "ms_per_step": 1e3 * run["elapsed"] / args.steps,
+        "speedup_vs_fp64": v / fp64_value,
+        "micro_iterations_per_step": run["micro"] / args.steps,
+        "max_abs_dC_vs_fp64": dC,
+        "max_rel_dC_vs_fp64": dC / max(float(np.abs(Cf).max()), 1e-300),
+        "gpu_launches": run["launches"],
+        "fp64_equivalent_tflops_total": sum(x["flops"] for x in run["tm"].values())
+                                       / run["elapsed"] / 1e12,
+        "roofline": {"bound": "tensor",
+                     "kernel": "oz_gemm_kernel (tcgen05 kind::f16, BF16 digit planes, ladder)",
+                     "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                     "frac": ach / bf16 if (ach and bf16) else None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured, burst)",
+                     "fp64_equivalent_tflops": eq,
+                     "frac_of_fp64_nominal": eq / FP64_NOMINAL_TFLOPS if eq else None,
+                     "traffic": ladder_traffic_per_launch(LADDER_OZ_PROFILE, "gemm_oz.cu"),
+                     "flops_per_launch_executed": OZ_PRODUCTS * fl,
+                     "avg_launch_ms": avg_s * 1e3, "launches": lad["launches"],
+                     "note": "executed = 28 BF16 digit-pair products per FP64-equivalent "
+                             "multiply-add of the real-embedded GEMM; the mean is over the "
+                             "three ladder launches of a residual"}},
+    }
+
+
 def serving_mix(n_req):
     """Scaled core-hole request mix (seeds 4000 + r): O ~ U{4..8}, V ~ U{20..48},
     Nchol = 4V, steps ~ U{20..80}, dt = 0.025 au."""
@@ -373,10 +416,9 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
-    # the split-TF32 form on the same inputs, same step counts
-    split = None
-    if not args.no_split:
-        gs = P.Propagator.from_problem(p, stream=stream, precision=P.RTEOM_SPLIT_TF32)
+    # the other precision forms on the same inputs, same step counts
+    def run_form(prec):
+        gs = P.Propagator.from_problem(p, stream=stream, precision=prec)
         gs.propagate(args.warmup, dt, tol=args.tol, max_micro=args.max_micro)
         i0 = gs.info()
         gs.set_timing(True)
@@ -393,11 +435,13 @@ def run_ours(args):
         el_s = f0.elapsed_time(f1) / 1e3
         tms = gs.timing()
         i1 = gs.info()
-        Cs_split, _ = gs.cumulant()
-        launches_split = gs.kernel_launches() - l0
+        Cf, _ = gs.cumulant()
+        nl = gs.kernel_launches() - l0
         gs.close()
-        split = dict(elapsed=el_s, tm=tms, micro=i1["micro"] - i0["micro"], C=Cs_split,
-                     launches=launches_split)
+        return dict(elapsed=el_s, tm=tms, micro=i1["micro"] - i0["micro"], C=Cf, launches=nl)
+
+    split = None if args.no_split else run_form(P.RTEOM_SPLIT_TF32)
+    ozaki = None if args.no_ozaki else run_form(P.RTEOM_FP64_OZAKI)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -466,7 +510,8 @@ def run_ours(args):
                         "returning C_n + rteom_spectrum + destroy, wall clock"},
         "gpu_launches": launches,
         "clocks": clocks,
-        "forms": split_summary(split, args, value, world, fp64_hist, peaks),
+        "forms": {**(split_summary(split, args, value, world, fp64_hist, peaks) or {}),
+                  **(ozaki_summary(ozaki, args, value, world, fp64_hist, peaks) or {})},
         "serving": serving,
         "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }

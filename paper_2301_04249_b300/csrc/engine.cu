@@ -174,6 +174,37 @@ std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
   return out;
 }
 
+// The emulated-FP64 kernel tiles A' in 128 rows and B' in 32 or 64: a GEMM
+// whose A' has few rows runs as C^T = B^T A^T (output written transposed)
+// when that pads much less.
+int64_t oz_padded(int64_t ra, int64_t rb) {
+  return (ra + 127) / 128 * 128 * (rb <= 32 ? 32 : (rb + 63) / 64 * 64);
+}
+
+bool oz_swap(const GemmDesc& g) {
+  const int64_t ra = (g.Acplx && !g.Bcplx) ? 2 * g.M : g.M, rb = g.Bcplx ? 2 * g.N : g.N;
+  const int64_t sa = (g.Bcplx && !g.Acplx) ? 2 * g.N : g.N, sb = g.Acplx ? 2 * g.M : g.M;
+  return 4 * oz_padded(sa, sb) < 3 * oz_padded(ra, rb);
+}
+
+GemmDesc swapped(const GemmDesc& g) {
+  GemmDesc s = g;
+  s.M = g.N;
+  s.N = g.M;
+  s.A = g.B;
+  s.Acplx = g.Bcplx;
+  s.transA = !g.transB;
+  s.lda = g.ldb;
+  s.strideA = g.strideB;
+  s.B = g.A;
+  s.Bcplx = g.Acplx;
+  s.transB = !g.transA;
+  s.ldb = g.lda;
+  s.strideB = g.strideA;
+  s.transC = !g.transC;
+  return s;
+}
+
 bool stream_capturing(cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   RT_CUDA(cudaStreamIsCapturing(st, &cs));
@@ -219,8 +250,10 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
     b1 = bytes_alloc(4 * L.b_elems);
     if (L.p_elems) P = bytes_alloc(8 * L.p_elems);
   }
+  const bool oz_sw = oz_ok && oz_swap(base);
+  const GemmDesc ozd = oz_sw ? swapped(base) : base;
   if (oz_ok) {
-    const OzLayout L = gemm_oz_layout(base);
+    const OzLayout L = gemm_oz_layout(ozd);
     a0 = bytes_alloc(2 * L.planes * L.a_elems);
     a1 = bytes_alloc(4 * L.a_rows);
     b0 = bytes_alloc(2 * L.planes * L.b_elems);
@@ -235,17 +268,20 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
     if (tc_ok)
       gemm_tc_pack_a(base, static_cast<float*>(a0), static_cast<float*>(a1), stream);
     else
-      gemm_oz_pack_a(base, static_cast<uint16_t*>(a0), static_cast<int*>(a1), stream);
+      gemm_oz_pack_a(ozd, static_cast<uint16_t*>(a0), static_cast<int*>(a1), stream);
   };
   auto pack_b = [&] {
     if (tc_ok)
       gemm_tc_pack_b(base, static_cast<float*>(b0), static_cast<float*>(b1), stream);
     else
-      gemm_oz_pack_b(base, static_cast<uint16_t*>(b0), static_cast<int*>(b1), stream);
+      gemm_oz_pack_b(ozd, static_cast<uint16_t*>(b0), static_cast<int*>(b1), stream);
   };
+  // operands the cache would hold are packed outside the timing (with the
+  // orientation swapped, the packed A' comes from B and B' from A)
+  const bool pa_const = oz_sw ? b_const : a_const, pb_const = oz_sw ? a_const : b_const;
   if (tc_ok || oz_ok) {
-    if (a_const) pack_a();
-    if (b_const) pack_b();
+    if (pa_const) pack_a();
+    if (pb_const) pack_b();
   }
   cudaEvent_t e0 = get_event(), e1 = get_event();
   float best_ms = std::numeric_limits<float>::infinity();
@@ -253,18 +289,19 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
   for (const auto& c : cands) {
     auto run = [&] {
       if (c.tc || c.oz) {
-        if (!a_const) pack_a();
-        if (!b_const) pack_b();
+        if (!pa_const) pack_a();
+        if (!pb_const) pack_b();
         if (c.tc) {
           gemm_tc_mma(base, static_cast<float*>(a0), static_cast<float*>(a1),
                       static_cast<float*>(b0), static_cast<float*>(b1), static_cast<float2*>(P),
                       tc_err, stream);
           gemm_tc_finalize(base, static_cast<float2*>(P), stream);
         } else {
-          gemm_oz_mma(base, static_cast<uint16_t*>(a0), static_cast<int*>(a1),
-                      static_cast<uint16_t*>(b0), static_cast<int*>(b1), static_cast<double*>(P),
+          gemm_oz_mma(ozd, static_cast<uint16_t*>(a0), static_cast<int*>(a1),
+                      static_cast<uint16_t*>(b0), static_cast<int*>(b1), static_cast<float2*>(P),
                       tc_err, stream);
-          gemm_oz_finalize(base, static_cast<double*>(P), stream);
+          gemm_oz_finalize(ozd, static_cast<int*>(a1), static_cast<int*>(b1),
+                           static_cast<float2*>(P), stream);
         }
       } else {
         GemmDesc d = base;
@@ -463,12 +500,16 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   };
   const Packed* cA = nullptr;
   const Packed* cB = nullptr;
+  // emulated FP64 may run the GEMM transposed; the packs then change roles
+  const bool swap = use_oz && oz_swap(g);
+  const char* roleA = swap ? "sB" : "A";
+  const char* roleB = swap ? "sA" : "B";
   if (packed_path && A.constant) {
-    auto it = tc_cache_.find(key("A", A));
+    auto it = tc_cache_.find(key(roleA, A));
     if (it != tc_cache_.end()) cA = &it->second;
   }
   if (packed_path && B.constant) {
-    auto it = tc_cache_.find(key("B", B));
+    auto it = tc_cache_.find(key(roleB, B));
     if (it != tc_cache_.end()) cB = &it->second;
   }
 
@@ -506,7 +547,8 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       trace_on() ? std::string(spec) + " M=" + std::to_string(Mt) + " N=" + std::to_string(Nt) +
                        " K=" + std::to_string(Kt) + " b=" + std::to_string(Bt) +
                        (use_tc || use_oz
-                            ? std::string(use_tc ? " tc" : " oz") + (cA ? " cA" : "") +
+                            ? std::string(use_tc ? " tc" : (swap ? " oz^T" : " oz")) +
+                                  (cA ? " cA" : "") +
                                   (cB ? " cB" : "")
                             : " s=" + std::to_string(gemm_f64_splits(g))) +
                        (bPA ? " pA" : "") + (bPB ? " pB" : "") + (bPC ? " pC" : "")
@@ -515,7 +557,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   // packed operand of the tensor-core paths: from the cache, stored in it
   // (constant tensors during the cache fill), or packed into the arena
   auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t bytes0,
-                     int64_t bytes1, bool is_a) -> Packed {
+                     int64_t bytes1, bool is_a, const GemmDesc& gd) -> Packed {
     if (cached) return *cached;
     Packed pk;
     const std::string ck = T.constant ? key(role, T) : std::string();
@@ -542,19 +584,20 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                float* hi = static_cast<float*>(pk.p0);
                float* lo = static_cast<float*>(pk.p1);
                if (is_a)
-                 gemm_tc_pack_a(g, hi, lo, stream);
+                 gemm_tc_pack_a(gd, hi, lo, stream);
                else
-                 gemm_tc_pack_b(g, hi, lo, stream);
+                 gemm_tc_pack_b(gd, hi, lo, stream);
              } else {
                uint16_t* planes = static_cast<uint16_t*>(pk.p0);
                int* expo = static_cast<int*>(pk.p1);
                if (is_a)
-                 gemm_oz_pack_a(g, planes, expo, stream);
+                 gemm_oz_pack_a(gd, planes, expo, stream);
                else
-                 gemm_oz_pack_b(g, planes, expo, stream);
+                 gemm_oz_pack_b(gd, planes, expo, stream);
              }
            },
-           use_tc ? "tc pack" : "oz pack");
+           trace_on() ? std::string(use_tc ? "tc pack " : "oz pack ") + role + " " + spec
+                      : std::string());
     if (store) {
       tc_cache_[ck] = pk;
       tc_cached_.insert(T.p);
@@ -572,8 +615,8 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     launch(cls, flops, [&] { gemm_f64(g, stream); }, label, bytes);
   } else if (use_tc) {
     const TcLayout L = gemm_tc_layout(g);
-    const Packed pa = operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true);
-    const Packed pb = operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false);
+    const Packed pa = operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true, g);
+    const Packed pb = operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false, g);
     float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
     // packed hi/lo operands read once; partial pairs written (and read back
     // by the finalize) or the output written directly
@@ -588,11 +631,14 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     if (L.ranges > 1)
       launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, P, stream); }, "tc finalize");
   } else {
-    const OzLayout L = gemm_oz_layout(g);
-    const Packed pa = operand("A", A, cA, 2 * L.planes * L.a_elems, 4 * L.a_rows, true);
-    const Packed pb = operand("B", B, cB, 2 * L.planes * L.b_elems, 4 * L.b_rows, false);
-    double* P = L.p_elems ? arena.alloc(L.p_elems) : nullptr;
-    // digit planes read once; FP64 partials written or the output written
+    const GemmDesc go = swap ? swapped(g) : g;
+    const OzLayout L = gemm_oz_layout(go);
+    const Packed pa = swap ? operand(roleB, B, cB, 2 * L.planes * L.a_elems, 4 * L.a_rows, true, go)
+                           : operand(roleA, A, cA, 2 * L.planes * L.a_elems, 4 * L.a_rows, true, go);
+    const Packed pb = swap ? operand(roleA, A, cA, 2 * L.planes * L.b_elems, 4 * L.b_rows, false, go)
+                           : operand(roleB, B, cB, 2 * L.planes * L.b_elems, 4 * L.b_rows, false, go);
+    float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
+    // digit planes read once; partial pairs written or the output written
     const double bytes = 2.0 * L.planes * (double)(L.a_elems + L.b_elems) +
                          8.0 * (double)L.p_elems +
                          (L.ranges == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
@@ -600,13 +646,18 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     // as many BF16 FLOPs, one product per digit pair)
     launch(cls, flops,
            [&] {
-             gemm_oz_mma(g, static_cast<uint16_t*>(pa.p0), static_cast<int*>(pa.p1),
+             gemm_oz_mma(go, static_cast<uint16_t*>(pa.p0), static_cast<int*>(pa.p1),
                          static_cast<uint16_t*>(pb.p0), static_cast<int*>(pb.p1), P, tc_err,
                          stream);
            },
            label, bytes);
     if (L.ranges > 1)
-      launch(kElementwise, 0.0, [&] { gemm_oz_finalize(g, P, stream); }, "oz finalize");
+      launch(kElementwise, 0.0,
+             [&] {
+               gemm_oz_finalize(go, static_cast<int*>(pa.p1), static_cast<int*>(pb.p1), P,
+                                stream);
+             },
+             "oz finalize");
   }
   if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();

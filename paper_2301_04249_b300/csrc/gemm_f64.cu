@@ -429,6 +429,7 @@ int64_t gemm_f64_workspace(const GemmDesc& d) {
 void gemm_f64(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   if (d.batch > 65535) throw Error(-1, "gemm_f64: batch too large");
+  if (d.transC) throw Error(-1, "gemm_f64: transposed output not supported");
   if (gemm_f64_is_gemv(d)) {
     gemv_f64(d, st);
     RT_CHECK_LAUNCH();

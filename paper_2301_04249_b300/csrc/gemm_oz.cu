@@ -50,20 +50,25 @@ using namespace tc5;
 
 constexpr int S = 7;                       // digit planes per operand
 constexpr int BM = 128;                    // rows of A' per tile (TMEM lanes)
-constexpr int BN = 64;                     // rows of B' per tile (output columns)
 constexpr int BK = 32;                     // K per k tile (BF16, 64 bytes per row)
 constexpr int CHUNK_KT = 4;                // k tiles per exact chunk (128 of K)
 constexpr int STAGES = 2;
 constexpr uint32_t A_TILE = BM * BK * 2;   // 8 KB
-constexpr uint32_t B_TILE = BN * BK * 2;   // 4 KB
-constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t TMEM_COLS = 512;        // 7 diagonals x 64 columns, rounded up
 constexpr int kZeroExp = INT_MIN / 4;      // scale exponent of an all-zero row
-constexpr size_t kSmemBytes = STAGES * (size_t)STAGE_BYTES + 256;
-static_assert(S * BN <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
 static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
+
+// Per output-tile width BN (rows of B' per tile): 64, or 32 for B' of at
+// most 32 rows.
+template <int BN>
+struct Cfg {
+  static constexpr uint32_t B_TILE = BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
+  static constexpr uint32_t TMEM_COLS = S * BN <= 256 ? 256 : 512;  // 7 diagonals, rounded up
+  static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 256;
+  static_assert(S * BN <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
+};
 
 // Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
 // K-major, N = bn, M = 128.
@@ -106,7 +111,7 @@ struct PackArgs {
   __nv_bfloat16* planes;  // S planes of plane_elems
   int64_t plane_elems;
   int64_t s_out;          // elements per batch entry within a plane
-  int* expo;              // [batch][Rp] row scale exponents
+  int* expo;              // [batch][Rp] largest biased exponent of each row
   bool rows_fast;         // consecutive threads walk packed rows (source rows contiguous)
 };
 
@@ -143,70 +148,115 @@ __device__ __forceinline__ double embedded(const PackArgs& p, int b, int rp, int
   return neg ? neg_f64(x) : x;
 }
 
-// Row scale exponents: E = max biased exponent - 1022, so |x| < 2^E.
+// Row scale exponents, stored as the row's largest biased exponent emax
+// (0 for an all-zero row); the scale is 2^E with E = emax - 1022, so |x| <
+// 2^E over the row.  With contiguous source rows a thread walks one row over
+// a segment of K (loads coalesced across threads); otherwise a warp walks
+// one row over a segment of K.  Segments meet in an atomic max on the
+// zeroed array.
+constexpr int kExpoSeg = 64;
+
+__device__ __forceinline__ int row_exp(int raw) { return raw == 0 ? kZeroExp : raw - 1022; }
+
+__global__ void oz_expo_rows_kernel(PackArgs p, int batch) {
+  const int64_t rows = (int64_t)batch * p.Rp;
+  const int64_t segs = (p.Kp + kExpoSeg - 1) / kExpoSeg;
+  const int64_t units = rows * segs;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = u / rows, w = u % rows;  // consecutive threads: consecutive rows
+    const int b = (int)(w / p.Rp), rp = (int)(w % p.Rp);
+    const int k0 = (int)(sg * kExpoSeg), k1 = min(p.Kp, k0 + kExpoSeg);
+    unsigned emax = 0;
+    for (int kp = k0; kp < k1; ++kp)
+      emax = max(emax, (unsigned)((__double_as_longlong(embedded(p, b, rp, kp)) >> 52) & 0x7FF));
+    if (emax) atomicMax(p.expo + w, (int)emax);
+  }
+}
+
+constexpr int kExpoWarpSeg = 2048;
+
 __global__ void oz_expo_kernel(PackArgs p, int batch) {
   const int64_t rows = (int64_t)batch * p.Rp;
+  const int64_t segs = (p.Kp + kExpoWarpSeg - 1) / kExpoWarpSeg;
+  const int64_t units = rows * segs;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < rows; w += nwarps) {
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
+    const int64_t w = u / segs, sg = u % segs;
     const int b = (int)(w / p.Rp), rp = (int)(w % p.Rp);
+    const int k1 = min(p.Kp, (int)((sg + 1) * kExpoWarpSeg));
     unsigned emax = 0;
-    for (int kp = lane; kp < p.Kp; kp += 32) {
+    for (int kp = (int)(sg * kExpoWarpSeg) + lane; kp < k1; kp += 32) {
       const double x = embedded(p, b, rp, kp);
       emax = max(emax, (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF));
     }
     emax = __reduce_max_sync(0xffffffffu, emax);
-    if (lane == 0) p.expo[w] = emax == 0 ? kZeroExp : (int)emax - 1022;
+    if (lane == 0 && emax) atomicMax(p.expo + w, (int)emax);
   }
 }
 
 // Digit planes: X = round(x 2^(55 - E)) on the integer ALUs, then balanced
-// base-256 digits from the least significant one.
-template <typename IDX>
-__global__ void oz_digits_kernel(PackArgs p, int batch) {
-  const IDX per = (IDX)p.Rp * (IDX)p.Kp;
-  const IDX n = per * (IDX)batch;
-  const int KT = p.Kp / BK;
-  for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < n;
-       e += (IDX)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const IDX q = e - (IDX)b * per;
-    int rp, kp;
-    if (p.rows_fast) {
-      rp = (int)(q % (IDX)p.Rp);
-      kp = (int)(q / (IDX)p.Rp);
-    } else {
-      rp = (int)(q / (IDX)p.Kp);
-      kp = (int)(q % (IDX)p.Kp);
-    }
-    const double x = embedded(p, b, rp, kp);
-    const int E = p.expo[(int64_t)b * p.Rp + rp];
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((u >> 52) & 0x7FF);
-    long long X = 0;
-    if (ex != 0 && E != kZeroExp) {
-      const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const int sh = ex - 1020 - E;  // <= 2 because |x| < 2^E
-      unsigned long long a = 0;
-      if (sh >= 0)
-        a = m << sh;
-      else if (sh > -64)
-        a = (m + (1ull << (-sh - 1))) >> (-sh);
-      X = (u >> 63) ? -(long long)a : (long long)a;
-    }
-    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
-    const int kt = kp / BK, kk = kp % BK;
-    const int64_t off = (int64_t)b * p.s_out +
-                        ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
-                        ((rr / 8) * (BK / 8) + kk / 8) * 64 + (rr % 8) * 8 + (kk % 8);
+// base-256 digits from the least significant one.  A warp packs one 8-row x
+// 32-column block (four core matrices per plane, 512 contiguous bytes):
+// lane t takes row t/4 and the eight columns 8*(t%4).., and writes 16 bytes
+// to each plane.
+__device__ __forceinline__ void digits_of(double x, int E, int (&d)[S]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  long long X = 0;
+  if (ex != 0 && E != kZeroExp) {
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1020 - E;  // <= 2 because |x| < 2^E
+    unsigned long long a = 0;
+    if (sh >= 0)
+      a = m << sh;
+    else if (sh > -64)
+      a = (m + (1ull << (-sh - 1))) >> (-sh);
+    X = (u >> 63) ? -(long long)a : (long long)a;
+  }
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-      const int r = (int)(X & 255);
-      const int d = r >= 128 ? r - 256 : r;
-      p.planes[s * p.plane_elems + off] = __int2bfloat16_rn(d);
-      X = (X - d) >> 8;
+  for (int s = S - 1; s >= 1; --s) {
+    const int r = (int)(X & 255);
+    d[s] = r >= 128 ? r - 256 : r;
+    X = (X - d[s]) >> 8;
+  }
+  d[0] = (int)X;
+}
+
+__global__ void oz_digits_kernel(PackArgs p, int batch) {
+  const int KT = p.Kp / BK;
+  const int64_t groups = (int64_t)(p.Rp / 8) * KT;  // 8-row x 32-column blocks per batch entry
+  const int64_t units = groups * batch;
+  const int lane = threadIdx.x & 31;
+  const int rr8 = lane >> 2, kg = lane & 3;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < units; w += nwarps) {
+    const int b = (int)(w / groups);
+    const int64_t gq = w - (int64_t)b * groups;
+    const int rg = (int)(gq / KT), kt = (int)(gq % KT);
+    const int rp = rg * 8 + rr8;
+    const int E = row_exp(p.expo[(int64_t)b * p.Rp + rp]);
+    uint32_t packed[S][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      int d0[S], d1[S];
+      digits_of(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
+      digits_of(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const __nv_bfloat162 h = __halves2bfloat162(__int2bfloat16_rn(d0[s]), __int2bfloat16_rn(d1[s]));
+        packed[s][j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+      }
     }
-    p.planes[off] = __int2bfloat16_rn((int)X);
+    // core matrix (rg, kg) of the tile: 8 rows x 8 columns, row rr8 at 16 bytes
+    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+    const int64_t off = (int64_t)b * p.s_out + ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
+                        ((rr / 8) * (BK / 8) + kg) * 64 + (rr % 8) * 8;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      *reinterpret_cast<uint4*>(p.planes + s * p.plane_elems + off) =
+          make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
   }
 }
 
@@ -217,17 +267,23 @@ struct KArgs {
   int64_t sA, sB;              // per-batch element strides within a plane
   const int *ea, *eb;          // row scale exponents of A' [batch][Mp] and B' [batch][Np]
   int KT, kpr, ranges;
-  double* P;                   // FP64 partials [batch*ranges][Mp][Np] when ranges > 1
+  float2* P;                   // unscaled (sum, compensation) [batch*ranges][Mp][Np] when ranges > 1
   int Mp, Np;
   int* err;
   double* C;
   bool cplx;
   int M, N, mode;              // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
-  int64_t ldc, sC;
+  int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
   double alpha, beta;
 };
 
+template <int BN>
 __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
+  using CF = Cfg<BN>;
+  constexpr uint32_t B_TILE = CF::B_TILE;
+  constexpr uint32_t STAGE_BYTES = CF::STAGE_BYTES;
+  constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
+  constexpr int HALF = BN / 2;  // columns drained by one epilogue warp
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
@@ -326,9 +382,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     const int q = warp % 4;
     const int h = (warp - 2) / 4;
     const int row = 32 * q + lane;
-    float sum[32], cmp[32];
+    float sum[HALF], cmp[HALF];
 #pragma unroll
-    for (int v = 0; v < 32; ++v) sum[v] = cmp[v] = 0.0f;
+    for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
     bool ok = nk > 0;
 #pragma unroll 1
     for (int j = 0; j < nchunks; ++j) {
@@ -341,10 +397,14 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
 #pragma unroll 1
       for (int d = 0; d < S; ++d) {
         const float w = __int_as_float((127 - 14 - 8 * d) << 23);  // 2^(2 - 8 (d + 2))
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + h * 32), r);
 #pragma unroll
-        for (int v = 0; v < 32; ++v) two_sum_acc(sum[v], cmp[v], __uint_as_float(r[v]) * w);
+        for (int c = 0; c < HALF; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + h * HALF + c), r);
+#pragma unroll
+          for (int v = 0; v < 16; ++v)
+            two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * w);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -352,7 +412,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     }
     if (ok) {
       const int mr = m_tile * BM + row;
-      const int er = g.ea[(int64_t)b * g.Mp + mr];
+      const int er = row_exp(g.ea[(int64_t)b * g.Mp + mr]);
       if (g.ranges == 1) {
         int m = mr, part = 0;
         if (g.mode == 1 && mr >= g.M) {
@@ -362,15 +422,15 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
         const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
         if (row_ok) {
 #pragma unroll
-          for (int v = 0; v < 32; ++v) {
-            const int nr = n_tile * BN + h * 32 + v;
+          for (int v = 0; v < HALF; ++v) {
+            const int nr = n_tile * BN + h * HALF + v;
             int n = nr, pt = part;
             if (g.mode == 2 && nr >= g.N) {
               n = nr - g.N;
               pt = 1;
             }
             if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-            const int ec = g.eb[(int64_t)b * g.Np + nr];
+            const int ec = row_exp(g.eb[(int64_t)b * g.Np + nr]);
             double val = 0.0;
             if (er != kZeroExp && ec != kZeroExp)
               val = scale2(f32_to_f64(sum[v]) + f32_to_f64(cmp[v]), er + ec);
@@ -379,19 +439,16 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
             else if (g.alpha != 1.0)
               val *= g.alpha;
             double* cp =
-                g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldc + n) + pt;
+                g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldm + (int64_t)n * g.ldn) + pt;
             *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
           }
         }
       } else {
-        double* dst = g.P + ((int64_t)z * g.Mp + mr) * g.Np + (int64_t)n_tile * BN + h * 32;
+        float4* dst = reinterpret_cast<float4*>(g.P + ((int64_t)z * g.Mp + mr) * g.Np +
+                                                (int64_t)n_tile * BN + h * HALF);
 #pragma unroll
-        for (int v = 0; v < 32; ++v) {
-          const int ec = g.eb[(int64_t)b * g.Np + n_tile * BN + h * 32 + v];
-          dst[v] = (er != kZeroExp && ec != kZeroExp)
-                       ? scale2(f32_to_f64(sum[v]) + f32_to_f64(cmp[v]), er + ec)
-                       : 0.0;
-        }
+        for (int v = 0; v < HALF / 2; ++v)
+          dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
       }
     }
   }
@@ -411,12 +468,13 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
 
 // ---------------------------------------------------------------- finalize
 struct FinArgs {
-  const double* P;  // [batch*ranges][Mp][Np]
+  const float2* P;  // unscaled (sum, compensation) [batch*ranges][Mp][Np]
+  const int *ea, *eb;
   int Mp, Np, ranges;
   int M, N, mode;
   double* C;
   bool cplx;
-  int64_t ldc, sC;
+  int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
   double alpha, beta;
 };
 
@@ -427,14 +485,22 @@ __global__ void oz_finalize_kernel(FinArgs f, int batch) {
     const int b = (int)(e / per);
     const int64_t q = e - (int64_t)b * per;
     const int m = (int)(q / f.N), n = (int)(q % f.N);
-    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldc + n);
+    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
     const int parts = f.cplx ? 2 : 1;
     for (int part = 0; part < parts; ++part) {
       const int mr = f.mode == 1 ? m + part * f.M : m;
       const int nr = f.mode == 2 ? n + part * f.N : n;
-      double s = 0.0;
-      for (int z = 0; z < f.ranges; ++z)
-        s += f.P[(((int64_t)b * f.ranges + z) * f.Mp + mr) * f.Np + nr];
+      float su = 0.0f, cm = 0.0f;
+      for (int z = 0; z < f.ranges; ++z) {
+        const float2 pz = f.P[(((int64_t)b * f.ranges + z) * f.Mp + mr) * f.Np + nr];
+        two_sum_acc(su, cm, pz.x);
+        cm += pz.y;
+      }
+      const int er = row_exp(f.ea[(int64_t)b * f.Mp + mr]);
+      const int ec = row_exp(f.eb[(int64_t)b * f.Np + nr]);
+      double s = (er != kZeroExp && ec != kZeroExp)
+                     ? scale2(f32_to_f64(su) + f32_to_f64(cm), er + ec)
+                     : 0.0;
       if (f.alpha == -1.0)
         s = neg_f64(s);
       else if (f.alpha != 1.0)
@@ -448,9 +514,10 @@ inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Plan {
   int mode;  // 0 RR, 1 CR, 2 RC, 3 CC
+  int bn;    // output tile width (rows of B' per tile)
   int Mp, Np, Kp, KT, ranges, kpr;
   int64_t a_elems, b_elems;  // BF16 per digit plane
-  int64_t p_elems;           // FP64 partials (0 with one range)
+  int64_t p_elems;           // float2 partials (0 with one range)
 };
 
 Plan plan(const GemmDesc& d) {
@@ -459,13 +526,14 @@ Plan plan(const GemmDesc& d) {
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
+  p.bn = Br <= 32 ? 32 : 64;
   p.Mp = roundup(std::max(Ar, 1), BM);
-  p.Np = roundup(std::max(Br, 1), BN);
+  p.Np = roundup(std::max(Br, 1), p.bn);
   p.Kp = roundup(std::max(Ak, 1), BK);
   p.KT = p.Kp / BK;
   // K ranges: fewest waves x k tiles per CTA, a range costing about four k
   // tiles for writing and re-reading its partial tile
-  const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / BN) * d.batch;
+  const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / p.bn) * d.batch;
   double best = 0.0;
   p.ranges = 1;
   p.kpr = p.KT;
@@ -491,13 +559,19 @@ int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16
 
 void pack(PackArgs pa, int64_t elems, int batch, cudaStream_t st) {
   const int64_t rows = (int64_t)batch * pa.Rp;
-  oz_expo_kernel<<<(int)std::min<int64_t>((rows * 32 + 255) / 256, 148 * 16), 256, 0, st>>>(
-      pa, batch);
+  RT_CUDA(cudaMemsetAsync(pa.expo, 0, sizeof(int) * rows, st));
+  if (pa.rows_fast) {
+    oz_expo_rows_kernel<<<grid_of(rows * ((pa.Kp + kExpoSeg - 1) / kExpoSeg)), 256, 0, st>>>(
+        pa, batch);
+  } else {
+    const int64_t units = rows * ((pa.Kp + kExpoWarpSeg - 1) / kExpoWarpSeg);
+    oz_expo_kernel<<<(int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16), 256, 0, st>>>(
+        pa, batch);
+  }
   RT_CHECK_LAUNCH();
-  if (elems < (int64_t(1) << 32) - (int64_t)256 * 148 * 16)
-    oz_digits_kernel<uint32_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
-  else
-    oz_digits_kernel<uint64_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  const int64_t units = elems / 256;  // 8 x 32 blocks, one warp each
+  oz_digits_kernel<<<(int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16), 256, 0, st>>>(
+      pa, batch);
   RT_CHECK_LAUNCH();
 }
 
@@ -518,8 +592,12 @@ OzLayout gemm_oz_layout(const GemmDesc& d) {
 }
 
 void gemm_oz_init() {
-  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)oz::kSmemBytes));
+  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel<64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)oz::Cfg<64>::SMEM));
+  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel<32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)oz::Cfg<32>::SMEM));
 }
 
 void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st) {
@@ -559,7 +637,7 @@ void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
   pb.mode = p.mode == 2 ? 1 : (p.mode == 3 ? 3 : 0);
   pb.Rp = p.Np;
   pb.Kp = p.Kp;
-  pb.rowtile = oz::BN;
+  pb.rowtile = p.bn;
   pb.planes = reinterpret_cast<__nv_bfloat16*>(planes);
   pb.plane_elems = p.b_elems;
   pb.s_out = (int64_t)p.Np * p.Kp;
@@ -569,7 +647,7 @@ void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
 }
 
 void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
-                 const int* eb, double* P, int* err, cudaStream_t st) {
+                 const int* eb, float2* P, int* err, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d);
   if (p.Mp / oz::BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
@@ -595,21 +673,28 @@ void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint
   g.M = d.M;
   g.N = d.N;
   g.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
-  g.ldc = d.ldc;
+  g.ldm = d.transC ? 1 : d.ldc;
+  g.ldn = d.transC ? d.ldc : 1;
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid(p.Np / oz::BN, p.Mp / oz::BM, d.batch * p.ranges);
-  oz::oz_gemm_kernel<<<grid, oz::THREADS, oz::kSmemBytes, st>>>(g);
+  dim3 grid(p.Np / p.bn, p.Mp / oz::BM, d.batch * p.ranges);
+  if (p.bn == 32)
+    oz::oz_gemm_kernel<32><<<grid, oz::THREADS, oz::Cfg<32>::SMEM, st>>>(g);
+  else
+    oz::oz_gemm_kernel<64><<<grid, oz::THREADS, oz::Cfg<64>::SMEM, st>>>(g);
   RT_CHECK_LAUNCH();
 }
 
-void gemm_oz_finalize(const GemmDesc& d, const double* P, cudaStream_t st) {
+void gemm_oz_finalize(const GemmDesc& d, const int* ea, const int* eb, const float2* P,
+                      cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d);
   if (p.ranges == 1) return;
   oz::FinArgs fa{};
   fa.P = P;
+  fa.ea = ea;
+  fa.eb = eb;
   fa.Mp = p.Mp;
   fa.Np = p.Np;
   fa.ranges = p.ranges;
@@ -618,7 +703,8 @@ void gemm_oz_finalize(const GemmDesc& d, const double* P, cudaStream_t st) {
   fa.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
   fa.C = d.C;
   fa.cplx = d.Acplx || d.Bcplx;
-  fa.ldc = d.ldc;
+  fa.ldm = d.transC ? 1 : d.ldc;
+  fa.ldn = d.transC ? d.ldc : 1;
   fa.sC = d.strideC;
   fa.alpha = d.alpha;
   fa.beta = d.beta;

@@ -78,7 +78,7 @@ struct KArgs {
   double* C;
   bool cplx;
   int M, N, mode;    // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
-  int64_t ldc, sC;
+  int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
   double alpha, beta;
 };
 
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
             pt = 1;
           }
           if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-          double* cp = g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldc + n) + pt;
+          double* cp = g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldm + (int64_t)n * g.ldn) + pt;
           const float f = sum[v] + cmp[v];
           const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
           *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
@@ -365,7 +365,7 @@ struct FinArgs {
   int mode;        // 0 real, 1 stacked rows (C re/im = row halves), 2 stacked columns
   double* C;
   bool cplx;
-  int64_t ldc, sC;
+  int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
   double alpha, beta;
 };
 
@@ -378,7 +378,7 @@ __global__ void tc_finalize_kernel(FinArgs f, int batch) {
     const int b = (int)(e / per);
     const int64_t q = e - (int64_t)b * per;
     const int m = (int)(q / f.N), n = (int)(q % f.N);
-    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldc + n);
+    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
     const int parts = f.cplx ? 2 : 1;
     for (int part = 0; part < parts; ++part) {
       int mr = m, nr = n;
@@ -549,7 +549,8 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.M = d.M;
   g.N = d.N;
   g.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
-  g.ldc = d.ldc;
+  g.ldm = d.transC ? 1 : d.ldc;
+  g.ldn = d.transC ? d.ldc : 1;
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
@@ -573,7 +574,8 @@ void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st) {
   fa.mode = p.mode == 1 ? 1 : (p.mode >= 2 ? 2 : 0);
   fa.C = d.C;
   fa.cplx = d.Acplx || d.Bcplx;
-  fa.ldc = d.ldc;
+  fa.ldm = d.transC ? 1 : d.ldc;
+  fa.ldn = d.transC ? d.ldc : 1;
   fa.sC = d.strideC;
   fa.alpha = d.alpha;
   fa.beta = d.beta;

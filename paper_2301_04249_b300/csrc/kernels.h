@@ -18,6 +18,7 @@ struct GemmDesc {
   bool transB = false, Bcplx = false;
   double* C = nullptr;
   int64_t ldc = 0, strideC = 0;
+  bool transC = false;  // element (m, n) at C[n * ldc + m] (tensor-core paths only)
   double alpha = 1.0, beta = 0.0;
   double* work = nullptr;  // split-K partial sums, gemm_f64_workspace() doubles
   // launch configuration chosen by the autotuner: tile index < gemm_f64_tiles()
@@ -63,13 +64,13 @@ void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st);
 // the same contract as gemm_f64: pack A and pack B (digit planes of
 // a_elems / b_elems BF16 each, and a_rows / b_rows row exponents), then the
 // MMA kernel, which writes C itself with one K range per tile or p_elems
-// FP64 partials that the finalize sums in range order.  gemm_oz_init() once
-// per process first.
+// unscaled (sum, compensation) pairs that the finalize combines in range
+// order.  gemm_oz_init() once per process first.
 struct OzLayout {
   int planes;
   int64_t a_elems, b_elems;  // BF16 per digit plane
   int64_t a_rows, b_rows;    // int row exponents
-  int64_t p_elems;           // FP64 partials; 0 = the MMA kernel writes C directly
+  int64_t p_elems;           // float2 partials; 0 = the MMA kernel writes C directly
   int ranges;
   double padded_flops;       // executed tensor-core FLOPs (28 digit-pair products)
 };
@@ -78,8 +79,9 @@ void gemm_oz_init();
 void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
 void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
 void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
-                 const int* eb, double* P, int* err, cudaStream_t st);
-void gemm_oz_finalize(const GemmDesc& d, const double* P, cudaStream_t st);
+                 const int* eb, float2* P, int* err, cudaStream_t st);
+void gemm_oz_finalize(const GemmDesc& d, const int* ea, const int* eb, const float2* P,
+                      cudaStream_t st);
 
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
 // contiguous with dims out_dim[0..nd-1]; strides count elements.  A real

@@ -371,9 +371,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_timed")  # launch lists: --nvtx-include "bench_timed/"
     e0.record(stream)
     g.propagate(args.steps, dt, tol=args.tol, max_micro=args.max_micro)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
@@ -456,6 +458,8 @@ def run_ours(args):
                                "mean service rate, 8 slots",
                    "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
                    "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
+                                             args.tol),
+                   "fp64_ozaki": run_serving(P, P.RTEOM_FP64_OZAKI, args.serving_requests,
                                              args.tol)}
     lad = tm["ladder"]
     peaks = measured_peaks()

@@ -19,11 +19,13 @@ def _mix():
     return [(gen_problem(O, V, N, seed), n) for O, V, N, seed, n in shapes]
 
 
-@pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32])
+@pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_FP64_OZAKI])
 def test_result_identical_alone_and_in_the_mix(precision, monkeypatch):
     if precision == P.RTEOM_SPLIT_TF32:
         monkeypatch.setenv("RTEOM_TC_MIN_FLOPS", "0")   # small shapes on the tensor cores too
-    tol = 1e-10 if precision == P.RTEOM_FP64 else 1e-8   # split form: ~1e-9 fixed-point floor
+    if precision == P.RTEOM_FP64_OZAKI:
+        monkeypatch.setenv("RTEOM_OZ_MIN_FLOPS", "0")
+    tol = 1e-8 if precision == P.RTEOM_SPLIT_TF32 else 1e-10  # split: ~1e-9 fixed-point floor
     jobs = _mix()
     alone = []
     for p, n in jobs:

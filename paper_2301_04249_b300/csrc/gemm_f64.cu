@@ -15,6 +15,8 @@
 // Bounds are checked on every load and store.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -48,6 +50,13 @@ struct Val<true> {
   double x, y;
 };
 
+// Complex operand staged for the three-multiplication complex product
+// (Gauss's trick, error analysis in Higham, SIAM J. Matrix Anal. Appl. 13,
+// 1992): re, im and re + im.
+struct Val3 {
+  double x, y, s;
+};
+
 template <bool CP>
 __device__ __forceinline__ Val<CP> load_val(const double* base, int64_t idx, bool ok) {
   Val<CP> v;
@@ -71,11 +80,17 @@ constexpr int BK = 8;
 template <bool AC, bool BC, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   constexpr bool CC = AC || BC;
+  // complex x complex: three real products per complex multiply-add,
+  // p1 = Re a Re b, p2 = Im a Im b, p3 = (Re a + Im a)(Re b + Im b);
+  // Re = p1 - p2, Im = p3 - p1 - p2
+  constexpr bool M3 = AC && BC;
+  using SA = typename std::conditional<M3, Val3, Val<AC>>::type;
+  using SB = typename std::conditional<M3, Val3, Val<BC>>::type;
   constexpr int RM = BM / TM;  // thread rows; thread (tx, ty) owns rows ty + RM*i
   constexpr int RN = BN / TN;  // thread cols; and cols tx + RN*j
   static_assert(RM * RN == 256, "tile must map onto 256 threads");
-  __shared__ Val<AC> As[BK][BM];
-  __shared__ Val<BC> Bs[BK][BN];
+  __shared__ SA As[BK][BM];
+  __shared__ SB Bs[BK][BN];
 
   // blockIdx.z = batch * splits + split; a split covers K range
   // [split*kslice, min(K, (split+1)*kslice)) and, when splits > 1, writes its
@@ -91,11 +106,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   const int n0 = blockIdx.x * BN;
   const int tx = threadIdx.x % RN, ty = threadIdx.x / RN;
 
-  double acc_r[TM][TN], acc_i[TM][TN];
+  double acc_r[TM][TN], acc_i[TM][TN], acc_s[M3 ? TM : 1][M3 ? TN : 1];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc_r[i][j] = acc_i[i][j] = 0.0;
+  if constexpr (M3) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc_s[i][j] = 0.0;
+  }
 
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
     // stage A slice: BM x BK elements
@@ -111,7 +132,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
       int m = m0 + mm, k = k0 + kk;
       bool ok = (m < g.M) && (k < kend);
       int64_t idx = g.transA ? (int64_t)k * g.lda + m : (int64_t)m * g.lda + k;
-      As[kk][mm] = load_val<AC>(A, ok ? idx : 0, ok);
+      const Val<AC> v = load_val<AC>(A, ok ? idx : 0, ok);
+      if constexpr (M3)
+        As[kk][mm] = Val3{v.x, v.y, v.x + v.y};
+      else
+        As[kk][mm] = v;
     }
     for (int e = threadIdx.x; e < BN * BK; e += 256) {
       int nn, kk;
@@ -125,13 +150,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
       int n = n0 + nn, k = k0 + kk;
       bool ok = (n < g.N) && (k < kend);
       int64_t idx = g.transB ? (int64_t)n * g.ldb + k : (int64_t)k * g.ldb + n;
-      Bs[kk][nn] = load_val<BC>(B, ok ? idx : 0, ok);
+      const Val<BC> v = load_val<BC>(B, ok ? idx : 0, ok);
+      if constexpr (M3)
+        Bs[kk][nn] = Val3{v.x, v.y, v.x + v.y};
+      else
+        Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      Val<AC> a[TM];
-      Val<BC> bv[TN];
+      SA a[TM];
+      SB bv[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + RM * i];
 #pragma unroll
@@ -140,11 +169,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          if constexpr (AC && BC) {
+          if constexpr (M3) {
             acc_r[i][j] = fma(a[i].x, bv[j].x, acc_r[i][j]);
-            acc_r[i][j] = fma(-a[i].y, bv[j].y, acc_r[i][j]);
-            acc_i[i][j] = fma(a[i].x, bv[j].y, acc_i[i][j]);
-            acc_i[i][j] = fma(a[i].y, bv[j].x, acc_i[i][j]);
+            acc_i[i][j] = fma(a[i].y, bv[j].y, acc_i[i][j]);
+            acc_s[i][j] = fma(a[i].s, bv[j].s, acc_s[i][j]);
           } else if constexpr (AC) {
             acc_r[i][j] = fma(a[i].x, bv[j].x, acc_r[i][j]);
             acc_i[i][j] = fma(a[i].y, bv[j].x, acc_i[i][j]);
@@ -159,6 +187,16 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
     __syncthreads();
   }
 
+  if constexpr (M3) {  // p1, p2, p3 -> Re, Im
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const double p1 = acc_r[i][j], p2 = acc_i[i][j];
+        acc_r[i][j] = p1 - p2;
+        acc_i[i][j] = acc_s[i][j] - p1 - p2;
+      }
+  }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     int m = m0 + ty + RM * i;

@@ -423,7 +423,7 @@ Plan plan(const GemmDesc& d) {
   // K ranges: fewest waves x k-tiles per CTA, a range costing about four
   // k-tiles for writing and re-reading its partial tile
   const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / kBN) * d.batch;
-  double best = 0.0;
+  double best = 0.0, cost1 = 0.0;
   p.ranges = 1;
   p.kpr = p.KT;
   for (int r = 1; r <= p.KT; ++r) {
@@ -437,6 +437,12 @@ Plan plan(const GemmDesc& d) {
       p.ranges = r;
       p.kpr = kpr;
     }
+    if (r == 1) cost1 = cost;
+  }
+  // the partials need a second launch: split K only for a clear gain
+  if (p.ranges > 1 && cost1 <= 1.25 * best) {
+    p.ranges = 1;
+    p.kpr = p.KT;
   }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;

@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--no-ozaki", action="store_true", help="skip the emulated-FP64 form")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=16)
+    ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="scaled",
+                    help="scaled: small shapes, all three forms; c4: the survey's request "
+                         "shapes with steps cut to U{4..16}, tensor-core forms only, "
+                         "autotuner off (serial and served runs on equal terms)")
     return ap.parse_args()
 
 
@@ -283,25 +287,32 @@ def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks):
     }
 
 
-def serving_mix(n_req):
-    """Scaled core-hole request mix (seeds 4000 + r): O ~ U{4..8}, V ~ U{20..48},
-    Nchol = 4V, steps ~ U{20..80}, dt = 0.025 au."""
+def serving_mix(n_req, kind="scaled"):
+    """Core-hole request mixes (seeds 4000 + r, dt = 0.025 au, Nchol = 4V).
+    scaled: O ~ U{4..8}, V ~ U{20..48}, steps ~ U{20..80}.
+    c4: the survey's shapes O ~ U{4..24}, V ~ U{40..240}, with steps ~ U{4..16}
+    instead of U{500..4000}."""
     from synth import gen_problem
     rng = np.random.default_rng(4)
     out = []
     for r in range(n_req):
-        O = int(rng.integers(4, 9))
-        V = int(rng.integers(20, 49))
-        steps = int(rng.integers(20, 81))
+        if kind == "c4":
+            O = int(rng.integers(4, 25))
+            V = int(rng.integers(40, 241))
+            steps = int(rng.integers(4, 17))
+        else:
+            O = int(rng.integers(4, 9))
+            V = int(rng.integers(20, 49))
+            steps = int(rng.integers(20, 81))
         out.append((gen_problem(O, V, 4 * V, 4000 + r), steps))
     return out
 
 
-def run_serving(P, precision, n_req, tol):
+def run_serving(P, precision, n_req, tol, kind="scaled"):
     """Serve the mix with Poisson arrivals at twice the mean service rate;
     returns latency percentiles, makespan and the serial (one at a time)
     reference measured on the same requests."""
-    mix = serving_mix(n_req)
+    mix = serving_mix(n_req, kind)
     dt = 0.025
     # serial reference: every request alone, back to back (also its service time)
     serial = []
@@ -452,7 +463,19 @@ def run_ours(args):
 
     value = world * args.steps / elapsed
     serving = None
-    if not args.no_serving:
+    if not args.no_serving and args.serving_mix == "c4":
+        os.environ["RTEOM_AUTOTUNE"] = "0"
+        serving = {"workload": f"c4 shapes: {args.serving_requests} requests, O~U{{4..24}}, "
+                               "V~U{40..240}, Nchol=4V, steps~U{4..16} (survey: U{500..4000}), "
+                               "dt=0.025, Poisson arrivals at 2x the mean service rate, 8 slots, "
+                               "admission by device memory, autotuner off",
+                   "fp64": "not run: one FP64 residual of the largest request takes about 30 s",
+                   "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
+                                             args.tol, "c4"),
+                   "fp64_ozaki": run_serving(P, P.RTEOM_FP64_OZAKI, args.serving_requests,
+                                             args.tol, "c4")}
+        del os.environ["RTEOM_AUTOTUNE"]
+    elif not args.no_serving:
         serving = {"workload": "scaled core-hole mix: 16 requests, O~U{4..8}, V~U{20..48}, "
                                "Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x the "
                                "mean service rate, 8 slots",

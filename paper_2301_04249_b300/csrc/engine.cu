@@ -201,8 +201,49 @@ GemmDesc swapped(const GemmDesc& g) {
   s.transB = !g.transA;
   s.ldb = g.lda;
   s.strideB = g.strideA;
+  s.va = g.vb;
+  s.vb = g.va;
   s.transC = !g.transC;
   return s;
+}
+
+// View with rows over the labels `rows` and columns over `cols` (each at
+// most three labels; an empty group is one index of extent 1).
+View2 make_view(const std::string& rows, const std::string& cols, const int64_t* strideof,
+                const int64_t* dimof) {
+  View2 v;
+  auto fill = [&](const std::string& l, int& n, int* ext, int64_t* str) {
+    n = 0;
+    for (char ch : l) {
+      ext[n] = (int)dimof[(unsigned char)ch];
+      str[n] = strideof[(unsigned char)ch];
+      ++n;
+    }
+    if (n == 0) {
+      ext[0] = 1;
+      str[0] = 0;
+      n = 1;
+    }
+  };
+  fill(rows, v.rdims, v.rext, v.rstr);
+  fill(cols, v.kdims, v.kext, v.kstr);
+  // merge neighbouring indices that are contiguous in memory (fewer splits)
+  auto merge = [](int& n, int* ext, int64_t* str) {
+    for (int d = n - 1; d > 0; --d)
+      if (str[d - 1] == (int64_t)ext[d] * str[d]) {
+        ext[d - 1] *= ext[d];
+        str[d - 1] = str[d];
+        for (int e = d; e < n - 1; ++e) {
+          ext[e] = ext[e + 1];
+          str[e] = str[e + 1];
+        }
+        --n;
+      }
+  };
+  merge(v.rdims, v.rext, v.rstr);
+  merge(v.kdims, v.kext, v.kstr);
+  view_prepare(v);
+  return v;
 }
 
 bool stream_capturing(cudaStream_t st) {
@@ -515,10 +556,32 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
 
   if (!dry && ((A.released && !cA) || (B.released && !cB)))
     throw Error(-3, std::string("contract: freed operand without a cached pack in ") + spec);
-  const Tensor Ause = (bPA && !cA) ? permuted(A, p.a, batch + bM + bK) : A;
-  const Tensor Buse = (bPB && !cB) ? permuted(B, p.b, batch + bK + bN) : B;
+  // The tensor-core packers read strided views of the operands, so those
+  // paths need no permuted input copies (unbatched, at most three labels
+  // per index group).  The output keeps its row-major copy and permute-add
+  // when its layout differs: an epilogue writing a permuted, accumulated
+  // output directly scatters its stores across rows and waits on every old
+  // value, which measured two to three times slower.
+  const bool fused = packed_path && batch.empty() && bM.size() <= 3 && bN.size() <= 3 &&
+                     bK.size() <= 3;
+  if (fused) {
+    int64_t sa[256], sb[256];
+    strides_of(p.a, A, sa);
+    strides_of(p.b, B, sb);
+    g.va = make_view(bM, bK, sa, dimof);
+    g.vb = make_view(bN, bK, sb, dimof);
+  }
+  if (pack_only && !packed_path) {  // only tensor-core packs are made ahead
+    arena.release(mark);
+    return;
+  }
+  const Tensor Ause =
+      (bPA && !cA && !fused && !(pack_only && !A.constant)) ? permuted(A, p.a, batch + bM + bK) : A;
+  const Tensor Buse =
+      (bPB && !cB && !fused && !(pack_only && !B.constant)) ? permuted(B, p.b, batch + bK + bN) : B;
   Tensor Cuse = C;
-  if (bPC) {
+  const bool outcopy = bPC;
+  if (outcopy) {
     Cuse.nd = (int)(batch + bM + bN).size();
     std::string lab = batch + bM + bN;
     for (int k = 0; k < Cuse.nd; ++k) Cuse.dim[k] = dimof[(unsigned char)lab[k]];
@@ -551,9 +614,11 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                                   (cA ? " cA" : "") +
                                   (cB ? " cB" : "")
                             : " s=" + std::to_string(gemm_f64_splits(g))) +
-                       (bPA ? " pA" : "") + (bPB ? " pB" : "") + (bPC ? " pC" : "")
+                       (fused ? std::string(" views") : std::string()) +
+                       (bPA && !fused ? " pA" : "") + (bPB && !fused ? " pB" : "") +
+                       (outcopy ? " pC" : "")
                  : std::string();
-  if (cls == kLadder && !dry) nvtxRangePushA("rteom_ladder");
+  if (cls == kLadder && !dry && !pack_only) nvtxRangePushA("rteom_ladder");
   // packed operand of the tensor-core paths: from the cache, stored in it
   // (constant tensors during the cache fill), or packed into the arena
   auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t bytes0,
@@ -571,6 +636,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       if (plan_cached && keep) return Packed{};  // held by the cache
     }
     const bool store = keep && tc_cache_fill && !dry && persistent_alloc;
+    if (pack_only && !store) return pk;  // a pack made ahead is only worth keeping
     if (store) {
       pk.p0 = persistent_alloc(bytes0);
       pk.p1 = persistent_alloc(bytes1);
@@ -615,6 +681,12 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     launch(cls, flops, [&] { gemm_f64(g, stream); }, label, bytes);
   } else if (use_tc) {
     const TcLayout L = gemm_tc_layout(g);
+    if (pack_only) {
+      if (A.constant && !cA) operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true, g);
+      if (B.constant && !cB) operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false, g);
+      arena.release(mark);
+      return;
+    }
     const Packed pa = operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true, g);
     const Packed pb = operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false, g);
     float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
@@ -633,6 +705,16 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   } else {
     const GemmDesc go = swap ? swapped(g) : g;
     const OzLayout L = gemm_oz_layout(go);
+    if (pack_only) {
+      const int64_t abytes = 2 * L.planes * L.a_elems, arow = 4 * L.a_rows;
+      const int64_t bbytes = 2 * L.planes * L.b_elems, brow = 4 * L.b_rows;
+      if (A.constant && !cA)
+        operand(roleA, A, cA, swap ? bbytes : abytes, swap ? brow : arow, !swap, go);
+      if (B.constant && !cB)
+        operand(roleB, B, cB, swap ? abytes : bbytes, swap ? arow : brow, swap, go);
+      arena.release(mark);
+      return;
+    }
     const Packed pa = swap ? operand(roleB, B, cB, 2 * L.planes * L.a_elems, 4 * L.a_rows, true, go)
                            : operand(roleA, A, cA, 2 * L.planes * L.a_elems, 4 * L.a_rows, true, go);
     const Packed pb = swap ? operand(roleA, A, cA, 2 * L.planes * L.b_elems, 4 * L.b_rows, false, go)
@@ -659,7 +741,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
              },
              "oz finalize");
   }
-  if (bPC) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
+  if (outcopy) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();
   if (dry && std::getenv("RTEOM_PLAN_TRACE"))  // scratch planning: arena top inside this call
     std::fprintf(stderr, "plan %-22s M=%lld N=%lld K=%lld %s arena %.3f GB (peak %.3f GB)\n", spec,

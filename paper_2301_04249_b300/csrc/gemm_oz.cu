@@ -113,6 +113,7 @@ struct PackArgs {
   int64_t s_out;          // elements per batch entry within a plane
   int* expo;              // [batch][Rp] largest biased exponent of each row
   bool rows_fast;         // consecutive threads walk packed rows (source rows contiguous)
+  View2 view;             // strided source view (view.rdims > 0) instead of s_r / s_c
 };
 
 // Value of the embedded real operand at packed (row rp, column kp).
@@ -143,7 +144,8 @@ __device__ __forceinline__ double embedded(const PackArgs& p, int b, int rp, int
     }
   }
   if (!valid) return 0.0;
-  const int64_t off = b * p.s_b + r * p.s_r + c * p.s_c;
+  const int64_t off = b * p.s_b + (p.view.rdims ? view_row(p.view, r) + view_col(p.view, c)
+                                                 : r * p.s_r + c * p.s_c);
   const double x = p.cplx ? p.src[2 * off + part] : p.src[off];
   return neg ? neg_f64(x) : x;
 }
@@ -421,6 +423,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
         }
         const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
         if (row_ok) {
+          const int64_t rbase = (int64_t)b * g.sC + (int64_t)m * g.ldm;
 #pragma unroll
           for (int v = 0; v < HALF; ++v) {
             const int nr = n_tile * BN + h * HALF + v;
@@ -438,8 +441,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
               val = neg_f64(val);
             else if (g.alpha != 1.0)
               val *= g.alpha;
-            double* cp =
-                g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldm + (int64_t)n * g.ldn) + pt;
+            double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
             *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
           }
         }
@@ -619,7 +621,9 @@ void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
   pa.plane_elems = p.a_elems;
   pa.s_out = (int64_t)p.Mp * p.Kp;
   pa.expo = expo;
-  pa.rows_fast = pa.s_r == 1 && pa.s_c != 1;
+  pa.view = d.va;
+  pa.rows_fast = d.va.rdims ? (d.va.rstr[d.va.rdims - 1] == 1 && d.va.kstr[d.va.kdims - 1] != 1)
+                            : (pa.s_r == 1 && pa.s_c != 1);
   oz::pack(pa, p.a_elems, d.batch, st);
 }
 
@@ -642,7 +646,9 @@ void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
   pb.plane_elems = p.b_elems;
   pb.s_out = (int64_t)p.Np * p.Kp;
   pb.expo = expo;
-  pb.rows_fast = pb.s_r == 1 && pb.s_c != 1;
+  pb.view = d.vb;
+  pb.rows_fast = d.vb.rdims ? (d.vb.rstr[d.vb.rdims - 1] == 1 && d.vb.kstr[d.vb.kdims - 1] != 1)
+                            : (pb.s_r == 1 && pb.s_c != 1);
   oz::pack(pb, p.b_elems, d.batch, st);
 }
 

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
       const bool unit = g.alpha == 1.0 || g.alpha == -1.0;
       const float sgn = g.alpha == -1.0 ? -1.0f : 1.0f;
       if (row_ok) {
+        const int64_t rbase = (int64_t)b * g.sC + (int64_t)m * g.ldm;
 #pragma unroll
         for (int v = 0; v < HALF; ++v) {
           const int nr = n_tile * BN + h * HALF + v;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
             pt = 1;
           }
           if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-          double* cp = g.C + (g.cplx ? 2 : 1) * ((int64_t)b * g.sC + (int64_t)m * g.ldm + (int64_t)n * g.ldn) + pt;
+          double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
           const float f = sum[v] + cmp[v];
           const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
           *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
@@ -281,6 +282,7 @@ struct PackArgs {
   float *hi, *lo;
   int64_t s_out;          // elements per batch entry of the packed output
   bool rows_fast;         // consecutive threads walk packed rows (source rows contiguous)
+  View2 view;             // strided source view (view.rdims > 0) instead of s_r / s_c
 };
 
 // Packed row r' / column k' -> (source row, source column, part, sign).
@@ -337,7 +339,8 @@ __global__ void tc_pack_kernel(PackArgs p, int batch) {
     }
     float xf = 0.0f;
     if (valid) {
-      const int64_t off = b * p.s_b + r * p.s_r + c * p.s_c;
+      const int64_t off = b * p.s_b + (p.view.rdims ? view_row(p.view, r) + view_col(p.view, c)
+                                                     : r * p.s_r + c * p.s_c);
       xf = f64_to_f32(p.cplx ? p.src[2 * off + part] : p.src[off]);
       if (neg) xf = -xf;
     }
@@ -423,7 +426,7 @@ Plan plan(const GemmDesc& d) {
   // K ranges: fewest waves x k-tiles per CTA, a range costing about four
   // k-tiles for writing and re-reading its partial tile
   const int64_t tiles = (int64_t)(p.Mp / BM) * (p.Np / kBN) * d.batch;
-  double best = 0.0, cost1 = 0.0;
+  double best = 0.0;
   p.ranges = 1;
   p.kpr = p.KT;
   for (int r = 1; r <= p.KT; ++r) {
@@ -437,12 +440,6 @@ Plan plan(const GemmDesc& d) {
       p.ranges = r;
       p.kpr = kpr;
     }
-    if (r == 1) cost1 = cost;
-  }
-  // the partials need a second launch: split K only for a clear gain
-  if (p.ranges > 1 && cost1 <= 1.25 * best) {
-    p.ranges = 1;
-    p.kpr = p.KT;
   }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
@@ -500,7 +497,9 @@ void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pa.hi = hi;
   pa.lo = lo;
   pa.s_out = (int64_t)p.Mp * p.Kp;
-  pa.rows_fast = pa.s_r == 1 && pa.s_c != 1;
+  pa.view = d.va;
+  pa.rows_fast = d.va.rdims ? (d.va.rstr[d.va.rdims - 1] == 1 && d.va.kstr[d.va.kdims - 1] != 1)
+                            : (pa.s_r == 1 && pa.s_c != 1);
   launch_pack(pa, p.a_elems, d.batch, st);
 }
 
@@ -523,7 +522,9 @@ void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pb.hi = hi;
   pb.lo = lo;
   pb.s_out = (int64_t)p.Np * p.Kp;
-  pb.rows_fast = pb.s_r == 1 && pb.s_c != 1;
+  pb.view = d.vb;
+  pb.rows_fast = d.vb.rdims ? (d.vb.rstr[d.vb.rdims - 1] == 1 && d.vb.kstr[d.vb.kdims - 1] != 1)
+                            : (pb.s_r == 1 && pb.s_c != 1);
   launch_pack(pb, p.b_elems, d.batch, st);
 }
 

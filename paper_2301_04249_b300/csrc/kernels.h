@@ -8,6 +8,59 @@
 namespace rteom {
 
 // ---- contractions ---------------------------------------------------------
+// A strided 2-D view of an operand, read by the tensor-core packers in place
+// of a permuted copy: row r and column k each
+// split row-major into up to three indices with element strides.  rdims == 0
+// means no view (the GemmDesc leading dimensions apply).  The index splits
+// divide by invariant extents with precomputed multipliers (Granlund and
+// Montgomery, PLDI 1994): q = (n * mag) >> sh, exact for 0 <= n < 2^31.
+struct View2 {
+  int rdims = 0, kdims = 0;
+  int rext[3] = {1, 1, 1}, kext[3] = {1, 1, 1};
+  int64_t rstr[3] = {0, 0, 0}, kstr[3] = {0, 0, 0};
+  uint64_t rmag[3] = {0, 0, 0}, kmag[3] = {0, 0, 0};
+  int rsh[3] = {0, 0, 0}, ksh[3] = {0, 0, 0};
+};
+
+// Fills the division multipliers of a view from its extents.
+inline void view_prepare(View2& v) {
+  auto mk = [](int d, uint64_t& mag, int& sh) {
+    int l = 0;
+    while ((1ull << l) < (uint64_t)d) ++l;  // ceil(log2 d)
+    sh = 32 + l;
+    mag = (uint64_t)((((unsigned __int128)1) << sh) / (unsigned)d) + 1;
+  };
+  for (int d = 0; d < 3; ++d) {
+    mk(v.rext[d], v.rmag[d], v.rsh[d]);
+    mk(v.kext[d], v.kmag[d], v.ksh[d]);
+  }
+}
+
+#ifdef __CUDACC__
+__host__ __device__ inline int64_t view_row(const View2& v, int r) {
+  int64_t o = 0;
+#pragma unroll
+  for (int d = 2; d >= 1; --d)
+    if (d < v.rdims) {
+      const int q = (int)(((uint64_t)(unsigned)r * v.rmag[d]) >> v.rsh[d]);
+      o += (int64_t)(r - q * v.rext[d]) * v.rstr[d];
+      r = q;
+    }
+  return o + (int64_t)r * v.rstr[0];  // the outermost index needs no split
+}
+__host__ __device__ inline int64_t view_col(const View2& v, int k) {
+  int64_t o = 0;
+#pragma unroll
+  for (int d = 2; d >= 1; --d)
+    if (d < v.kdims) {
+      const int q = (int)(((uint64_t)(unsigned)k * v.kmag[d]) >> v.ksh[d]);
+      o += (int64_t)(k - q * v.kext[d]) * v.kstr[d];
+      k = q;
+    }
+  return o + (int64_t)k * v.kstr[0];  // the outermost index needs no split
+}
+#endif
+
 struct GemmDesc {
   int M = 0, N = 0, K = 0, batch = 1;
   const double* A = nullptr;
@@ -19,6 +72,9 @@ struct GemmDesc {
   double* C = nullptr;
   int64_t ldc = 0, strideC = 0;
   bool transC = false;  // element (m, n) at C[n * ldc + m] (tensor-core paths only)
+  // tensor-core paths only: views of A (rows m, columns k) and B (rows n,
+  // columns k) replacing lda/ldb and transA/B
+  View2 va, vb;
   double alpha = 1.0, beta = 0.0;
   double* work = nullptr;  // split-K partial sums, gemm_f64_workspace() doubles
   // launch configuration chosen by the autotuner: tile index < gemm_f64_tiles()

@@ -309,4 +309,30 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   E.arena.release(mark);
 }
 
+void prepack_ladder(Engine& E, const ResidualOperands& op, bool same_spin) {
+  const int nO = op.nO, nV = op.nV;
+  const int64_t mark = E.arena.mark();
+  E.pack_only = true;
+  // stand-ins for the amplitude side: same shapes as in compute_residual,
+  // never read (only the constant operand is packed)
+  if (!same_spin) {
+    Tensor vvvv = make_tensor(const_cast<double*>(op.vvvv), false, {nV, nV, nV, nV});
+    vvvv.constant = true;
+    const Tensor tau = E.arena.tensor(true, {nO, nO, nV, nV});
+    const Tensor R = E.arena.tensor(true, {nO, nO, nV, nV});
+    E.contract("ijef,efab->ijab", 1.0, tau, vvvv, 1.0, R, kLadder);
+  } else {
+    const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
+    if (npo > 0 && npv > 0) {
+      Tensor Wm = make_tensor(const_cast<double*>(op.vvvv_as), false, {npv, npv});
+      Wm.constant = true;
+      const Tensor tp = E.arena.tensor(true, {npo, npv});
+      const Tensor Rp = E.arena.tensor(true, {npo, npv});
+      E.contract("pq,qr->pr", 1.0, tp, Wm, 0.0, Rp, kLadder);
+    }
+  }
+  E.pack_only = false;
+  E.arena.release(mark);
+}
+
 }  // namespace rteom

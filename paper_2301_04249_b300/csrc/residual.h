@@ -34,4 +34,10 @@ struct ResidualOperands {
 // unspecified.  Issues only stream-ordered work (capturable).
 void compute_residual(Engine& E, const ResidualOperands& op, const double* t, double* R);
 
+// Packs the constant operand of the alpha-beta ladder (same_spin false) or of
+// the same-spin pair ladder into the engine's cache, through the same
+// contraction calls as compute_residual but without running them (the
+// engine's pack_only mode; needs tc_cache_fill).
+void prepack_ladder(Engine& E, const ResidualOperands& op, bool same_spin);
+
 }  // namespace rteom

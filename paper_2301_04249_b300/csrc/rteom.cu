@@ -392,17 +392,24 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
       if (ladder(a.second) != ladder(b.second)) return ladder(a.second);
       return a.second.bytes < b.second.bytes;
     });
+    // The ladder packs are made first, each FP64 block freed right after its
+    // pack: alpha-beta, then same-spin, then the rest of the cache.
     E.tc_cache_select = true;
+    const int64_t f_ab = 8 * (int64_t)nV * nV * nV * nV, f_ss = 8 * npv * npv;
     for (size_t keep = order.size();; --keep) {
       E.tc_cache_allowed.clear();
-      int64_t cache_bytes = 0;
+      int64_t p_ab = 0, p_ss = 0, p_other = 0;
       for (size_t k = 0; k < keep; ++k) {
         E.tc_cache_allowed.insert(order[k].first);
-        cache_bytes += order[k].second.bytes;
+        const auto& cc = order[k].second;
+        (cc.tensor == vvvv ? p_ab : cc.tensor == vvvv_as ? p_ss : p_other) += cc.bytes;
       }
       need = dry_peak();
-      c->cache_plan_bytes = cache_bytes;
-      if (8 * std::max(need, setup_need) + cache_bytes + later <= (int64_t)fr || keep == 0) break;
+      const int64_t freed_ab = p_ab ? f_ab : 0, freed_ss = p_ss ? f_ss : 0;
+      const int64_t peak = std::max({p_ab, p_ab - freed_ab + p_ss,
+                                     p_ab + p_ss + p_other - freed_ab - freed_ss});
+      c->cache_plan_bytes = p_ab + p_ss + p_other;
+      if (8 * std::max(need, setup_need) + peak + later <= (int64_t)fr || keep == 0) break;
     }
   }
   if (setup_need > need) need = setup_need;
@@ -504,22 +511,27 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   // the autotuner times the GEMM shapes the process has not seen.  In FP64
   // the first residual of the propagation runs eagerly for the autotuner.
   if (split) {
-    E.tuning = E.autotune;
     E.tc_cache_fill = true;
-    compute_residual(E, c->op, c->T_N, c->R_K);
-    E.tc_cache_fill = false;
-    E.tuning = false;
+    // the ladder contractions read only their packed operands once cached:
+    // pack them first and free the FP64 ladder blocks (the largest arrays of
+    // the context) before the rest of the cache is filled
+    prepack_ladder(E, op, false);
     RT_CUDA(cudaStreamSynchronize(st));
-    // the ladder contractions now read only their packed operands: free the
-    // FP64 ladder blocks (the largest arrays of the context)
     if (E.tc_cached(vvvv)) {
       c->dfree(vvvv);
       op.vvvv_released = true;
     }
+    prepack_ladder(E, op, true);
+    RT_CUDA(cudaStreamSynchronize(st));
     if (E.tc_cached(vvvv_as)) {
       c->dfree(vvvv_as);
       op.vvvv_as_released = true;
     }
+    E.tuning = E.autotune;
+    compute_residual(E, c->op, c->T_N, c->R_K);
+    E.tc_cache_fill = false;
+    E.tuning = false;
+    RT_CUDA(cudaStreamSynchronize(st));
   } else {
     c->tune_first = E.autotune;
   }

@@ -1,11 +1,12 @@
 """O=30, V=300, Nchol=1200 (the split-precision workload): the split-TF32
-residual against the FP64 residual of the same GPU path.
+residual and the emulated-FP64 residual against the FP64 residual of the
+same GPU path.
 
 The oracle cannot run at this size (its (ae|bf) block alone is 66 GB and one
 residual takes hours on the host), so the FP64 path, pinned to the oracle at
 the smaller workloads, is the reference here.  Bound: 1e-5 of the largest
-residual element, as at O=8, V=100 (measured 1.7e-6).  Memory: one context
-at a time (split 200 GB, FP64 148 GB of the 275 GB device).
+residual element for the split form, as at O=8, V=100 (measured 1.7e-6);
+1e-12 for the emulated FP64 form.  Memory: one context at a time.
 """
 import numpy as np
 import pytest
@@ -25,13 +26,13 @@ def _amplitudes(p, rng):
     return t
 
 
-def test_c3_split_residual_tracks_fp64_residual():
+def test_c3_split_and_emulated_residuals_track_fp64_residual():
     p, _ = workload("c3_split")
     t = _amplitudes(p, np.random.default_rng(0))
     rng = np.random.default_rng(1)
     picks = None
     samples = {}
-    for prec in (P.RTEOM_SPLIT_TF32, P.RTEOM_FP64):
+    for prec in (P.RTEOM_SPLIT_TF32, P.RTEOM_FP64_OZAKI, P.RTEOM_FP64):
         with P.Propagator.from_problem(p, precision=prec) as g:
             R, E = g.residual(t)
         if picks is None:
@@ -40,6 +41,9 @@ def test_c3_split_residual_tracks_fp64_residual():
                          max(np.abs(x).max() for x in R))
         del R
     (Rs, Es, _), (Rf, Ef, scale) = samples[P.RTEOM_SPLIT_TF32], samples[P.RTEOM_FP64]
+    Ro, Eo, _ = samples[P.RTEOM_FP64_OZAKI]
     err = max(np.abs(a - b).max() for a, b in zip(Rs, Rf)) / scale
     assert err < 1e-5, err
-    assert Es == Ef  # the energy is FP64 in both forms
+    err_oz = max(np.abs(a - b).max() for a, b in zip(Ro, Rf)) / scale
+    assert err_oz < 1e-12, err_oz
+    assert Es == Ef == Eo  # the energy is FP64 in every form

@@ -556,29 +556,40 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
 
   if (!dry && ((A.released && !cA) || (B.released && !cB)))
     throw Error(-3, std::string("contract: freed operand without a cached pack in ") + spec);
-  // The tensor-core packers read strided views of the operands, so those
-  // paths need no permuted input copies (unbatched, at most three labels
-  // per index group).  The output keeps its row-major copy and permute-add
-  // when its layout differs: an epilogue writing a permuted, accumulated
-  // output directly scatters its stores across rows and waits on every old
-  // value, which measured two to three times slower.
-  const bool fused = packed_path && batch.empty() && bM.size() <= 3 && bN.size() <= 3 &&
-                     bK.size() <= 3;
-  if (fused) {
+  // The tensor-core packers read strided views of the operands in place of
+  // permuted copies (unbatched, at most three labels per index group), where
+  // the view keeps their loads coalesced: after merging contiguous indices,
+  // either the columns (K) or the rows form one unit-stride run.  Other
+  // operands are permuted first, which measured faster.  The output keeps its
+  // row-major copy and permute-add when its layout differs: an epilogue
+  // writing a permuted, accumulated output directly scatters its stores
+  // across rows and waits on every old value, which measured two to three
+  // times slower.
+  bool fusedA = false, fusedB = false;
+  if (packed_path && batch.empty() && bM.size() <= 3 && bN.size() <= 3 && bK.size() <= 3) {
+    auto coalesced = [](const View2& v) {
+      return (v.kdims == 1 && v.kstr[0] == 1) || (v.rdims == 1 && v.rstr[0] == 1);
+    };
     int64_t sa[256], sb[256];
     strides_of(p.a, A, sa);
     strides_of(p.b, B, sb);
-    g.va = make_view(bM, bK, sa, dimof);
-    g.vb = make_view(bN, bK, sb, dimof);
+    const View2 va = make_view(bM, bK, sa, dimof), vb = make_view(bN, bK, sb, dimof);
+    fusedA = bPA && coalesced(va);
+    fusedB = bPB && coalesced(vb);
+    if (fusedA) g.va = va;
+    if (fusedB) g.vb = vb;
   }
+  const bool fused = fusedA || fusedB;
   if (pack_only && !packed_path) {  // only tensor-core packs are made ahead
     arena.release(mark);
     return;
   }
-  const Tensor Ause =
-      (bPA && !cA && !fused && !(pack_only && !A.constant)) ? permuted(A, p.a, batch + bM + bK) : A;
-  const Tensor Buse =
-      (bPB && !cB && !fused && !(pack_only && !B.constant)) ? permuted(B, p.b, batch + bK + bN) : B;
+  const Tensor Ause = (bPA && !cA && !fusedA && !(pack_only && !A.constant))
+                          ? permuted(A, p.a, batch + bM + bK)
+                          : A;
+  const Tensor Buse = (bPB && !cB && !fusedB && !(pack_only && !B.constant))
+                          ? permuted(B, p.b, batch + bK + bN)
+                          : B;
   Tensor Cuse = C;
   const bool outcopy = bPC;
   if (outcopy) {
@@ -615,7 +626,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                                   (cB ? " cB" : "")
                             : " s=" + std::to_string(gemm_f64_splits(g))) +
                        (fused ? std::string(" views") : std::string()) +
-                       (bPA && !fused ? " pA" : "") + (bPB && !fused ? " pB" : "") +
+                       (bPA && !fusedA ? " pA" : "") + (bPB && !fusedB ? " pB" : "") +
                        (outcopy ? " pC" : "")
                  : std::string();
   if (cls == kLadder && !dry && !pack_only) nvtxRangePushA("rteom_ladder");

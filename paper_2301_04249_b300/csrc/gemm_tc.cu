@@ -388,8 +388,22 @@ __global__ void tc_finalize_kernel(FinArgs f, int batch) {
       if (f.mode == 1) mr = m + part * f.M;
       if (f.mode == 2) nr = n + part * f.N;
       float s = 0.0f, cm = 0.0f;
-      for (int z = 0; z < f.ranges; ++z) {
-        const float2 pz = f.P[(((int64_t)b * f.ranges + z) * f.Mp + mr) * f.Np + nr];
+      // ranges in order, four loads in flight at a time
+      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + mr) * f.Np + nr;
+      const int64_t zs = (int64_t)f.Mp * f.Np;
+      int z = 0;
+      for (; z + 4 <= f.ranges; z += 4) {
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = pp[(z + u) * zs];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          two_sum_acc(s, cm, q[u].x);
+          cm += q[u].y;
+        }
+      }
+      for (; z < f.ranges; ++z) {
+        const float2 pz = pp[z * zs];
         two_sum_acc(s, cm, pz.x);
         cm += pz.y;
       }

@@ -40,7 +40,6 @@ MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
 LADDER_TC_PROFILE = os.path.join(HERE, "profiles", "ladder_tc_tf32_c2.txt")
 LADDER_OZ_PROFILE = os.path.join(HERE, "profiles", "ladder_oz_bf16_c2.txt")
-OZ_PRODUCTS = 28  # digit-pair BF16 products per emulated FP64 product
 
 
 def parse_args():
@@ -53,7 +52,7 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 form")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 and split-BF16 forms")
     ap.add_argument("--no-ozaki", action="store_true", help="skip the emulated-FP64 form")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=16)
@@ -247,22 +246,25 @@ def split_summary(split, args, fp64_value, world, C_fp64, peaks):
     }}
 
 
-def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks):
-    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of the
-    emulated-FP64 form measured on the same workload and step counts."""
+def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks, name="fp64_ozaki", planes=7,
+                  profile=LADDER_OZ_PROFILE):
+    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of a
+    digit-sliced form (emulated FP64: 7 planes; split-BF16: 3 planes)
+    measured on the same workload and step counts."""
     if run is None:
         return None
+    products = planes * (planes + 1) // 2
     lad = run["tm"]["ladder"]
     v = world * args.steps / run["elapsed"]
     bf16 = peaks.get("bf16_tflops")
     avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
     fl = lad["flops"] / max(lad["launches"], 1)  # FP64-equivalent
     eq = fl / avg_s / 1e12 if lad["launches"] else None
-    ach = OZ_PRODUCTS * eq if eq else None
+    ach = products * eq if eq else None
     n = min(len(C_fp64), len(run["C"]))
     Cf = np.asarray(C_fp64)[:n]
     dC = float(np.abs(np.asarray(run["C"])[:n] - Cf).max())
-    return {"fp64_ozaki": {
+    return {name: {
         "value": v, "unit": UNIT, "ms_per_step": 1e3 * run["elapsed"] / args.steps,
         "speedup_vs_fp64": v / fp64_value,
         "micro_iterations_per_step": run["micro"] / args.steps,
@@ -272,18 +274,20 @@ def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks):
         "fp64_equivalent_tflops_total": sum(x["flops"] for x in run["tm"].values())
                                        / run["elapsed"] / 1e12,
         "roofline": {"bound": "tensor",
-                     "kernel": "oz_gemm_kernel (tcgen05 kind::f16, BF16 digit planes, ladder)",
+                     "kernel": f"oz_gemm_kernel<{planes}> (tcgen05 kind::f16, BF16 digit planes, "
+                               "ladder)",
                      "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
                      "frac": ach / bf16 if (ach and bf16) else None,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured, burst)",
                      "fp64_equivalent_tflops": eq,
                      "frac_of_fp64_nominal": eq / FP64_NOMINAL_TFLOPS if eq else None,
-                     "traffic": ladder_traffic_per_launch(LADDER_OZ_PROFILE, "gemm_oz.cu"),
-                     "flops_per_launch_executed": OZ_PRODUCTS * fl,
+                     "traffic": ladder_traffic_per_launch(profile, "gemm_oz.cu")
+                                if profile else None,
+                     "flops_per_launch_executed": products * fl,
                      "avg_launch_ms": avg_s * 1e3, "launches": lad["launches"],
-                     "note": "executed = 28 BF16 digit-pair products per FP64-equivalent "
-                             "multiply-add of the real-embedded GEMM; the mean is over the "
-                             "three ladder launches of a residual"}},
+                     "note": f"executed = {products} BF16 digit-pair products per "
+                             "FP64-equivalent multiply-add of the real-embedded GEMM; the mean "
+                             "is over the three ladder launches of a residual"}},
     }
 
 
@@ -454,6 +458,7 @@ def run_ours(args):
         return dict(elapsed=el_s, tm=tms, micro=i1["micro"] - i0["micro"], C=Cf, launches=nl)
 
     split = None if args.no_split else run_form(P.RTEOM_SPLIT_TF32)
+    split_bf16 = None if args.no_split else run_form(P.RTEOM_SPLIT_BF16)
     ozaki = None if args.no_ozaki else run_form(P.RTEOM_FP64_OZAKI)
     if rank != 0:
         if world > 1:
@@ -538,6 +543,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "forms": {**(split_summary(split, args, value, world, fp64_hist, peaks) or {}),
+                  **(ozaki_summary(split_bf16, args, value, world, fp64_hist, peaks,
+                                   "split_bf16", 3, None) or {}),
                   **(ozaki_summary(ozaki, args, value, world, fp64_hist, peaks) or {})},
         "serving": serving,
         "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},

@@ -52,7 +52,15 @@ extern "C" {
 
 /* precision forms */
 #define RTEOM_FP64        0   /* every contraction and update in FP64           */
-#define RTEOM_SPLIT_BF16  1   /* reserved (not built): split-BF16 contractions  */
+#define RTEOM_SPLIT_BF16  1   /* contractions of at least 5e7 FLOP (and smaller
+                                 ones the autotuner finds faster there) on the
+                                 BF16 tensor cores as three 8-bit digit planes
+                                 per operand with per-row power-of-two scales
+                                 (x carried to about 2^-24 of its row scale),
+                                 the 6 leading digit-pair products summed
+                                 exactly in FP32 over chunks of 256 of K and
+                                 accumulated as compensated pairs; every other
+                                 step FP64 */
 #define RTEOM_SPLIT_TF32  2   /* contractions of at least 5e7 FLOP (and smaller
                                  ones the autotuner finds faster there) on the
                                  tensor cores as split-TF32 products (x = hi +
@@ -95,8 +103,8 @@ typedef struct rteom_ctx rteom_ctx;
  *             NULL; t1_gs/t2_gs only enter E_N^corr of Eq. 3:
  *             E = sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
  *  core_index spatial index c of the ionised orbital, 0 <= c < O
- *  precision  RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI
- *             (RTEOM_SPLIT_BF16: RTEOM_ERR_ARG)
+ *  precision  RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 or
+ *             RTEOM_FP64_OZAKI
  *  flags      RTEOM_FLAG_* bits
  *  cuda_stream cudaStream_t to run on, or NULL for a non-blocking stream
  *             created and owned by the context
@@ -235,8 +243,7 @@ typedef struct rteom_server rteom_server;
  *  mem_budget_bytes  device memory the running requests may hold (0: 80 % of
  *                    the free memory at creation)
  *  max_active        slots: requests running at once (>= 1)
- *  precision         RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI for
- *                    every request
+ *  precision         one of the RTEOM_* precision forms, for every request
  */
 int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_active,
                         int precision);

@@ -177,14 +177,15 @@ std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
 // The emulated-FP64 kernel tiles A' in 128 rows and B' in 32 or 64: a GEMM
 // whose A' has few rows runs as C^T = B^T A^T (output written transposed)
 // when that pads much less.
-int64_t oz_padded(int64_t ra, int64_t rb) {
-  return (ra + 127) / 128 * 128 * (rb <= 32 ? 32 : (rb + 63) / 64 * 64);
+int64_t oz_padded(int64_t ra, int64_t rb, int S) {
+  const int64_t bn = rb <= 32 ? 32 : (S <= 3 && rb > 64 ? 128 : 64);
+  return (ra + 127) / 128 * 128 * ((rb + bn - 1) / bn * bn);
 }
 
-bool oz_swap(const GemmDesc& g) {
+bool oz_swap(const GemmDesc& g, int S) {
   const int64_t ra = (g.Acplx && !g.Bcplx) ? 2 * g.M : g.M, rb = g.Bcplx ? 2 * g.N : g.N;
   const int64_t sa = (g.Bcplx && !g.Acplx) ? 2 * g.N : g.N, sb = g.Acplx ? 2 * g.M : g.M;
-  return 4 * oz_padded(sa, sb) < 3 * oz_padded(ra, rb);
+  return 4 * oz_padded(sa, sb, S) < 3 * oz_padded(ra, rb, S);
 }
 
 GemmDesc swapped(const GemmDesc& g) {
@@ -291,10 +292,10 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
     b1 = bytes_alloc(4 * L.b_elems);
     if (L.p_elems) P = bytes_alloc(8 * L.p_elems);
   }
-  const bool oz_sw = oz_ok && oz_swap(base);
+  const bool oz_sw = oz_ok && oz_swap(base, oz_planes);
   const GemmDesc ozd = oz_sw ? swapped(base) : base;
   if (oz_ok) {
-    const OzLayout L = gemm_oz_layout(ozd);
+    const OzLayout L = gemm_oz_layout(ozd, oz_planes);
     a0 = bytes_alloc(2 * L.planes * L.a_elems);
     a1 = bytes_alloc(4 * L.a_rows);
     b0 = bytes_alloc(2 * L.planes * L.b_elems);
@@ -309,13 +310,13 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
     if (tc_ok)
       gemm_tc_pack_a(base, static_cast<float*>(a0), static_cast<float*>(a1), stream);
     else
-      gemm_oz_pack_a(ozd, static_cast<uint16_t*>(a0), static_cast<int*>(a1), stream);
+      gemm_oz_pack_a(ozd, oz_planes, static_cast<uint16_t*>(a0), static_cast<int*>(a1), stream);
   };
   auto pack_b = [&] {
     if (tc_ok)
       gemm_tc_pack_b(base, static_cast<float*>(b0), static_cast<float*>(b1), stream);
     else
-      gemm_oz_pack_b(ozd, static_cast<uint16_t*>(b0), static_cast<int*>(b1), stream);
+      gemm_oz_pack_b(ozd, oz_planes, static_cast<uint16_t*>(b0), static_cast<int*>(b1), stream);
   };
   // operands the cache would hold are packed outside the timing (with the
   // orientation swapped, the packed A' comes from B and B' from A)
@@ -338,10 +339,10 @@ void Engine::tuning_scratch(const GemmDesc& g, bool tc_ok, bool oz_ok, bool a_co
                       tc_err, stream);
           gemm_tc_finalize(base, static_cast<float2*>(P), stream);
         } else {
-          gemm_oz_mma(ozd, static_cast<uint16_t*>(a0), static_cast<int*>(a1),
+          gemm_oz_mma(ozd, oz_planes, static_cast<uint16_t*>(a0), static_cast<int*>(a1),
                       static_cast<uint16_t*>(b0), static_cast<int*>(b1), static_cast<float2*>(P),
                       tc_err, stream);
-          gemm_oz_finalize(ozd, static_cast<int*>(a1), static_cast<int*>(b1),
+          gemm_oz_finalize(ozd, oz_planes, static_cast<int*>(a1), static_cast<int*>(b1),
                            static_cast<float2*>(P), stream);
         }
       } else {
@@ -542,7 +543,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   const Packed* cA = nullptr;
   const Packed* cB = nullptr;
   // emulated FP64 may run the GEMM transposed; the packs then change roles
-  const bool swap = use_oz && oz_swap(g);
+  const bool swap = use_oz && oz_swap(g, oz_planes);
   const char* roleA = swap ? "sB" : "A";
   const char* roleB = swap ? "sA" : "B";
   if (packed_path && A.constant) {
@@ -668,9 +669,9 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                uint16_t* planes = static_cast<uint16_t*>(pk.p0);
                int* expo = static_cast<int*>(pk.p1);
                if (is_a)
-                 gemm_oz_pack_a(gd, planes, expo, stream);
+                 gemm_oz_pack_a(gd, oz_planes, planes, expo, stream);
                else
-                 gemm_oz_pack_b(gd, planes, expo, stream);
+                 gemm_oz_pack_b(gd, oz_planes, planes, expo, stream);
              }
            },
            trace_on() ? std::string(use_tc ? "tc pack " : "oz pack ") + role + " " + spec
@@ -715,7 +716,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       launch(kElementwise, 0.0, [&] { gemm_tc_finalize(g, P, stream); }, "tc finalize");
   } else {
     const GemmDesc go = swap ? swapped(g) : g;
-    const OzLayout L = gemm_oz_layout(go);
+    const OzLayout L = gemm_oz_layout(go, oz_planes);
     if (pack_only) {
       const int64_t abytes = 2 * L.planes * L.a_elems, arow = 4 * L.a_rows;
       const int64_t bbytes = 2 * L.planes * L.b_elems, brow = 4 * L.b_rows;
@@ -739,7 +740,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     // as many BF16 FLOPs, one product per digit pair)
     launch(cls, flops,
            [&] {
-             gemm_oz_mma(go, static_cast<uint16_t*>(pa.p0), static_cast<int*>(pa.p1),
+             gemm_oz_mma(go, oz_planes, static_cast<uint16_t*>(pa.p0), static_cast<int*>(pa.p1),
                          static_cast<uint16_t*>(pb.p0), static_cast<int*>(pb.p1), P, tc_err,
                          stream);
            },
@@ -747,7 +748,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     if (L.ranges > 1)
       launch(kElementwise, 0.0,
              [&] {
-               gemm_oz_finalize(go, static_cast<int*>(pa.p1), static_cast<int*>(pb.p1), P,
+               gemm_oz_finalize(go, oz_planes, static_cast<int*>(pa.p1), static_cast<int*>(pb.p1), P,
                                 stream);
              },
              "oz finalize");

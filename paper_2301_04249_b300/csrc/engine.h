@@ -35,9 +35,11 @@ class Engine {
   bool tensor_cores = false;
   double tc_min_flops = 5e7;
   int* tc_err = nullptr;  // also collects timeouts of the emulated-FP64 kernel
-  // FP64 emulation: contractions of at least oz_min_flops run as sliced BF16
-  // products on the tensor cores with FP64-level accuracy
+  // Digit slicing: contractions of at least oz_min_flops run as products of
+  // oz_planes BF16 digit planes on the tensor cores (7 planes: FP64-level
+  // accuracy; 3 planes: the split-BF16 form)
   bool fp64_emulation = false;
+  int oz_planes = 7;
   double oz_min_flops = 5e7;
   // Packed tensor-core operands of constant tensors, keyed by tensor, spec
   // and role.  Entries are created only while tc_cache_fill is set (an eager

@@ -48,26 +48,28 @@ namespace oz {
 
 using namespace tc5;
 
-constexpr int S = 7;                       // digit planes per operand
 constexpr int BM = 128;                    // rows of A' per tile (TMEM lanes)
 constexpr int BK = 32;                     // K per k tile (BF16, 64 bytes per row)
-constexpr int CHUNK_KT = 4;                // k tiles per exact chunk (128 of K)
-constexpr int STAGES = 2;
 constexpr uint32_t A_TILE = BM * BK * 2;   // 8 KB
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int kZeroExp = INT_MIN / 4;      // scale exponent of an all-zero row
-static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
 
-// Per output-tile width BN (rows of B' per tile): 64, or 32 for B' of at
-// most 32 rows.
-template <int BN>
+// S digit planes per operand (7: FP64-accurate; 3: the split-BF16 form) and
+// output-tile width BN (rows of B' per tile).  A diagonal sums at most S
+// digit pairs, so a chunk of K stays exact in FP32 while S * K * 2^14 <
+// 2^24: 128 of K for S = 7, 256 for S = 3.
+template <int S, int BN>
 struct Cfg {
+  static constexpr int CHUNK_KT = S > 4 ? 4 : 8;  // k tiles per exact chunk
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
-  static constexpr uint32_t TMEM_COLS = S * BN <= 256 ? 256 : 512;  // 7 diagonals, rounded up
+  static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 4 ? (200u * 1024u / STAGE_BYTES) : 4;
+  static constexpr uint32_t TMEM_COLS = S * BN <= 128 ? 128 : (S * BN <= 256 ? 256 : 512);
   static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 256;
   static_assert(S * BN <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
+  static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
+  static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
 // Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
@@ -198,18 +200,19 @@ __global__ void oz_expo_kernel(PackArgs p, int batch) {
   }
 }
 
-// Digit planes: X = round(x 2^(55 - E)) on the integer ALUs, then balanced
-// base-256 digits from the least significant one.  A warp packs one 8-row x
-// 32-column block (four core matrices per plane, 512 contiguous bytes):
-// lane t takes row t/4 and the eight columns 8*(t%4).., and writes 16 bytes
-// to each plane.
+// Digit planes: X = round(x 2^(8S - 1 - E)) on the integer ALUs, then
+// balanced base-256 digits from the least significant one.  A warp packs one
+// 8-row x 32-column block (four core matrices per plane, 512 contiguous
+// bytes): lane t takes row t/4 and the eight columns 8*(t%4).., and writes
+// 16 bytes to each plane.
+template <int S>
 __device__ __forceinline__ void digits_of(double x, int E, int (&d)[S]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((u >> 52) & 0x7FF);
   long long X = 0;
   if (ex != 0 && E != kZeroExp) {
     const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = ex - 1020 - E;  // <= 2 because |x| < 2^E
+    const int sh = ex - 1076 + 8 * S - E;  // |x| < 2^E keeps |X| <= 2^(8S-1)
     unsigned long long a = 0;
     if (sh >= 0)
       a = m << sh;
@@ -226,6 +229,7 @@ __device__ __forceinline__ void digits_of(double x, int E, int (&d)[S]) {
   d[0] = (int)X;
 }
 
+template <int S>
 __global__ void oz_digits_kernel(PackArgs p, int batch) {
   const int KT = p.Kp / BK;
   const int64_t groups = (int64_t)(p.Rp / 8) * KT;  // 8-row x 32-column blocks per batch entry
@@ -243,8 +247,8 @@ __global__ void oz_digits_kernel(PackArgs p, int batch) {
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       int d0[S], d1[S];
-      digits_of(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
-      digits_of(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
+      digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
+      digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const __nv_bfloat162 h = __halves2bfloat162(__int2bfloat16_rn(d0[s]), __int2bfloat16_rn(d1[s]));
@@ -279,9 +283,11 @@ struct KArgs {
   double alpha, beta;
 };
 
-template <int BN>
+template <int S, int BN>
 __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
-  using CF = Cfg<BN>;
+  using CF = Cfg<S, BN>;
+  constexpr int CHUNK_KT = CF::CHUNK_KT;
+  constexpr int STAGES = CF::STAGES;
   constexpr uint32_t B_TILE = CF::B_TILE;
   constexpr uint32_t STAGE_BYTES = CF::STAGE_BYTES;
   constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
@@ -536,13 +542,14 @@ struct Plan {
   int64_t p_elems;           // float2 partials (0 with one range)
 };
 
-Plan plan(const GemmDesc& d) {
+Plan plan(const GemmDesc& d, int S) {
   Plan p;
   p.mode = (d.Acplx ? 1 : 0) + (d.Bcplx ? 2 : 0);
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
-  p.bn = Br <= 32 ? 32 : 64;
+  // widest tile whose S diagonal accumulators fit the tensor memory
+  p.bn = Br <= 32 ? 32 : (S <= 3 && Br > 64 ? 128 : 64);
   p.Mp = roundup(std::max(Ar, 1), BM);
   p.Np = roundup(std::max(Br, 1), p.bn);
   p.Kp = roundup(std::max(Ak, 1), BK);
@@ -573,7 +580,7 @@ Plan plan(const GemmDesc& d) {
 
 int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
 
-void pack(PackArgs pa, int64_t elems, int batch, cudaStream_t st) {
+void pack(PackArgs pa, int64_t elems, int batch, int S, cudaStream_t st) {
   const int64_t rows = (int64_t)batch * pa.Rp;
   RT_CUDA(cudaMemsetAsync(pa.expo, 0, sizeof(int) * rows, st));
   if (pa.rows_fast) {
@@ -586,39 +593,44 @@ void pack(PackArgs pa, int64_t elems, int batch, cudaStream_t st) {
   }
   RT_CHECK_LAUNCH();
   const int64_t units = elems / 256;  // 8 x 32 blocks, one warp each
-  oz_digits_kernel<<<(int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16), 256, 0, st>>>(
-      pa, batch);
+  const int grid = (int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16);
+  if (S == 3)
+    oz_digits_kernel<3><<<grid, 256, 0, st>>>(pa, batch);
+  else
+    oz_digits_kernel<7><<<grid, 256, 0, st>>>(pa, batch);
   RT_CHECK_LAUNCH();
 }
 
 }  // namespace oz
 
-OzLayout gemm_oz_layout(const GemmDesc& d) {
-  const oz::Plan p = oz::plan(d);
+OzLayout gemm_oz_layout(const GemmDesc& d, int S) {
+  const oz::Plan p = oz::plan(d, S);
   OzLayout l;
-  l.planes = oz::S;
+  l.planes = S;
   l.a_elems = p.a_elems;
   l.b_elems = p.b_elems;
   l.a_rows = (int64_t)p.Mp * d.batch;
   l.b_rows = (int64_t)p.Np * d.batch;
   l.p_elems = p.p_elems;
   l.ranges = p.ranges;
-  l.padded_flops = 2.0 * oz::S * (oz::S + 1) / 2 * (double)p.Mp * p.Np * p.Kp * d.batch;
+  l.padded_flops = 2.0 * S * (S + 1) / 2 * (double)p.Mp * p.Np * p.Kp * d.batch;
   return l;
 }
 
 void gemm_oz_init() {
-  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel<64>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)oz::Cfg<64>::SMEM));
-  RT_CUDA(cudaFuncSetAttribute(oz::oz_gemm_kernel<32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)oz::Cfg<32>::SMEM));
+  auto set = [](auto kernel, size_t smem) {
+    RT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  };
+  set(oz::oz_gemm_kernel<7, 64>, oz::Cfg<7, 64>::SMEM);
+  set(oz::oz_gemm_kernel<7, 32>, oz::Cfg<7, 32>::SMEM);
+  set(oz::oz_gemm_kernel<3, 128>, oz::Cfg<3, 128>::SMEM);
+  set(oz::oz_gemm_kernel<3, 64>, oz::Cfg<3, 64>::SMEM);
+  set(oz::oz_gemm_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
 }
 
-void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st) {
+void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const oz::Plan p = oz::plan(d);
+  const oz::Plan p = oz::plan(d, S);
   oz::PackArgs pa{};
   pa.src = d.A;
   pa.cplx = d.Acplx;
@@ -638,12 +650,12 @@ void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
   pa.view = d.va;
   pa.rows_fast = d.va.rdims ? (d.va.rstr[d.va.rdims - 1] == 1 && d.va.kstr[d.va.kdims - 1] != 1)
                             : (pa.s_r == 1 && pa.s_c != 1);
-  oz::pack(pa, p.a_elems, d.batch, st);
+  oz::pack(pa, p.a_elems, d.batch, S, st);
 }
 
-void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st) {
+void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const oz::Plan p = oz::plan(d);
+  const oz::Plan p = oz::plan(d, S);
   oz::PackArgs pb{};
   pb.src = d.B;
   pb.cplx = d.Bcplx;
@@ -663,13 +675,13 @@ void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t
   pb.view = d.vb;
   pb.rows_fast = d.vb.rdims ? (d.vb.rstr[d.vb.rdims - 1] == 1 && d.vb.kstr[d.vb.kdims - 1] != 1)
                             : (pb.s_r == 1 && pb.s_c != 1);
-  oz::pack(pb, p.b_elems, d.batch, st);
+  oz::pack(pb, p.b_elems, d.batch, S, st);
 }
 
-void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
+void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, const uint16_t* B,
                  const int* eb, float2* P, int* err, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const oz::Plan p = oz::plan(d);
+  const oz::Plan p = oz::plan(d, S);
   if (p.Mp / oz::BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
     throw Error(-1, "gemm_oz: grid too large");
   oz::KArgs g{};
@@ -699,17 +711,24 @@ void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint
   g.alpha = d.alpha;
   g.beta = d.beta;
   dim3 grid(p.Np / p.bn, p.Mp / oz::BM, d.batch * p.ranges);
-  if (p.bn == 32)
-    oz::oz_gemm_kernel<32><<<grid, oz::THREADS, oz::Cfg<32>::SMEM, st>>>(g);
+  using namespace oz;
+  if (S == 3 && p.bn == 128)
+    oz_gemm_kernel<3, 128><<<grid, THREADS, Cfg<3, 128>::SMEM, st>>>(g);
+  else if (S == 3 && p.bn == 64)
+    oz_gemm_kernel<3, 64><<<grid, THREADS, Cfg<3, 64>::SMEM, st>>>(g);
+  else if (S == 3)
+    oz_gemm_kernel<3, 32><<<grid, THREADS, Cfg<3, 32>::SMEM, st>>>(g);
+  else if (p.bn == 32)
+    oz_gemm_kernel<7, 32><<<grid, THREADS, Cfg<7, 32>::SMEM, st>>>(g);
   else
-    oz::oz_gemm_kernel<64><<<grid, oz::THREADS, oz::Cfg<64>::SMEM, st>>>(g);
+    oz_gemm_kernel<7, 64><<<grid, THREADS, Cfg<7, 64>::SMEM, st>>>(g);
   RT_CHECK_LAUNCH();
 }
 
-void gemm_oz_finalize(const GemmDesc& d, const int* ea, const int* eb, const float2* P,
+void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
                       cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const oz::Plan p = oz::plan(d);
+  const oz::Plan p = oz::plan(d, S);
   if (p.ranges == 1) return;
   oz::FinArgs fa{};
   fa.P = P;

@@ -130,13 +130,15 @@ struct OzLayout {
   int ranges;
   double padded_flops;       // executed tensor-core FLOPs (28 digit-pair products)
 };
-OzLayout gemm_oz_layout(const GemmDesc& d);
+// S = 7 digit planes (FP64-accurate) or 3 (the split-BF16 form, about 2^-24
+// of the row scales).
+OzLayout gemm_oz_layout(const GemmDesc& d, int S);
 void gemm_oz_init();
-void gemm_oz_pack_a(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
-void gemm_oz_pack_b(const GemmDesc& d, uint16_t* planes, int* expo, cudaStream_t st);
-void gemm_oz_mma(const GemmDesc& d, const uint16_t* A, const int* ea, const uint16_t* B,
+void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st);
+void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st);
+void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, const uint16_t* B,
                  const int* eb, float2* P, int* err, cudaStream_t st);
-void gemm_oz_finalize(const GemmDesc& d, const int* ea, const int* eb, const float2* P,
+void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
                       cudaStream_t st);
 
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is

@@ -352,10 +352,12 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   // scratch arena for set-up contractions and, later, the residual, sized
   // by dry runs of the residual as it will run
   // forms with packed tensor-core operands (and a cache of the constant ones)
-  const bool split = c->precision == RTEOM_SPLIT_TF32 || c->precision == RTEOM_FP64_OZAKI;
+  const bool split = c->precision != RTEOM_FP64;
+  const bool sliced = c->precision == RTEOM_FP64_OZAKI || c->precision == RTEOM_SPLIT_BF16;
   if (const char* v = std::getenv("RTEOM_AUTOTUNE")) E.autotune = std::atoi(v) != 0;
   E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;
-  E.fp64_emulation = c->precision == RTEOM_FP64_OZAKI;
+  E.fp64_emulation = sliced;
+  E.oz_planes = c->precision == RTEOM_SPLIT_BF16 ? 3 : 7;
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
   if (const char* v = std::getenv("RTEOM_OZ_MIN_FLOPS")) E.oz_min_flops = std::atof(v);
   auto dry_peak = [&]() {
@@ -499,7 +501,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
       E.tensor_cores = true;
     } else {
       gemm_oz_init();
-      E.fp64_emulation = true;
+      E.fp64_emulation = true;  // digit slicing, oz_planes as planned above
     }
     E.tc_err = reinterpret_cast<int*>(c->maxdiff + 1);
     E.persistent_alloc = [c](int64_t bytes) {
@@ -663,8 +665,10 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   if (nocc < 1 || nvir < 1 || nchol < 0) return bad(RTEOM_ERR_ARG, "need nocc >= 1, nvir >= 1, nchol >= 0");
   if (core_index < 0 || core_index >= nocc) return bad(RTEOM_ERR_ARG, "core_index outside the occupied orbitals");
   if (!eps || (nchol > 0 && !L)) return bad(RTEOM_ERR_ARG, "eps (and L when nchol > 0) must be given");
-  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 && precision != RTEOM_FP64_OZAKI)
-    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_TF32 or RTEOM_FP64_OZAKI");
+  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 && precision != RTEOM_FP64_OZAKI &&
+      precision != RTEOM_SPLIT_BF16)
+    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 "
+                              "or RTEOM_FP64_OZAKI");
   if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)

@@ -64,7 +64,8 @@ double estimate_bytes(int O, int V, int nchol, int precision) {
   const double amps = 4.0 * 2.0 * (2.0 * nO * nV + 3.0 * nO * nO * nV * nV);
   const double arena = 2.0 * 64.0 * nO * nO * nV * nV + 2.0 * 16.0 * 64.0 * nV * nV;
   double doubles = ints + (setup > arena ? setup : arena) + amps;
-  if (precision == RTEOM_SPLIT_TF32) doubles += 1.5 * ints + 2.0 * 16.0 * nO * nO * nV * nV;
+  if (precision == RTEOM_SPLIT_TF32 || precision == RTEOM_SPLIT_BF16)
+    doubles += 1.5 * ints + 2.0 * 16.0 * nO * nO * nV * nV;
   if (precision == RTEOM_FP64_OZAKI) doubles += 2.0 * ints + 3.0 * 16.0 * nO * nO * nV * nV;
   return 1.25 * 8.0 * doubles + 64.0 * 1024 * 1024;
 }
@@ -236,7 +237,7 @@ int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_act
   *out = nullptr;
   if (max_active < 1 || mem_budget_bytes < 0 ||
       (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
-       precision != RTEOM_FP64_OZAKI))
+       precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16))
     return RTEOM_ERR_ARG;
   std::unique_ptr<rteom_server> s(new rteom_server());
   if (cudaGetDevice(&s->device) != cudaSuccess) return RTEOM_ERR_CUDA;

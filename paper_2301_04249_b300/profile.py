@@ -1,7 +1,7 @@
 """Evaluate CCSD residuals of a named workload eagerly, for profilers.
 
   python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde] [--residuals 2]
-         [--precision fp64|split_tf32|fp64_ozaki]
+         [--precision fp64|split_tf32|split_bf16|fp64_ozaki]
 
 Each evaluation launches every kernel of one residual on the library's
 stream outside CUDA graphs, with the particle-particle ladder GEMMs inside
@@ -27,12 +27,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c2_formaldehyde")
     ap.add_argument("--residuals", type=int, default=2)
-    ap.add_argument("--precision", choices=["fp64", "split_tf32", "fp64_ozaki"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "split_tf32", "split_bf16", "fp64_ozaki"],
+                    default="fp64")
     a = ap.parse_args()
     p, _ = workload(a.workload)
     rng = np.random.default_rng(0)
     prec = {"fp64": P.RTEOM_FP64, "split_tf32": P.RTEOM_SPLIT_TF32,
-            "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
+            "split_bf16": P.RTEOM_SPLIT_BF16, "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
     with P.Propagator.from_problem(p, precision=prec) as g:
         shapes = P.block_shapes(p.nocc, p.nvir)
         t = [0.01 * (rng.standard_normal(s) + 1j * rng.standard_normal(s)) for s in shapes]

@@ -1,12 +1,13 @@
-"""Split-TF32 form (RTEOM_SPLIT_TF32) against the FP64 oracle and FP64 path.
-
-The split form runs contractions of at least 5e7 FLOP on the tensor cores
-as hi*hi + hi*lo + lo*hi TF32 products with FP32 accumulation (slices of at
-most 512 of K, summed in FP64); everything else stays FP64.  Targets: the
-cumulant within 1e-6 absolute of the FP64 oracle and the quasiparticle peak
-within 0.005 eV (1.84e-4 Ha).  The packed operands round the amplitudes to
-about 2^-22 relative, which puts a floor near 1e-9 under the micro-iteration
-change, so these runs use tol 1e-8 (production uses the paper's 1e-4).
+"""Split-precision forms against the FP64 oracle and FP64 path: split-TF32
+(RTEOM_SPLIT_TF32: hi*hi + hi*lo + lo*hi TF32 products, FP32 accumulation
+over slices of at most 512 of K) and split-BF16 (RTEOM_SPLIT_BF16: three
+8-bit BF16 digit planes per operand with per-row scales, the 6 leading digit
+pairs summed exactly in FP32).  Contractions of at least 5e7 FLOP run on the
+tensor cores; everything else stays FP64.  Targets: the cumulant within 1e-6
+absolute of the FP64 oracle and the quasiparticle peak within 0.005 eV
+(1.84e-4 Ha).  The packed operands carry about 22-24 bits, which puts a
+floor near 1e-9 under the micro-iteration change, so these runs use tol 1e-8
+(production uses the paper's 1e-4).
 """
 import os
 
@@ -33,16 +34,26 @@ def _golden(name):
     return d[:, 1] + 1j * d[:, 2], float(meta["eps_core"]), float(meta["e_corr"])
 
 
-def _split(p, **kw):
+FORMS = {"tf32": (P.RTEOM_SPLIT_TF32, "RTEOM_TC_MIN_FLOPS"),
+         "bf16": (P.RTEOM_SPLIT_BF16, "RTEOM_OZ_MIN_FLOPS")}
+
+
+@pytest.fixture(params=sorted(FORMS))
+def form(request):
+    """(precision, environment variable that sets its tensor-core threshold)."""
+    return FORMS[request.param]
+
+
+def _split(p, form, **kw):
     return P.Propagator(p.eps, p.L, p.nocc, p.nvir, p.t1_gs, p.t2_gs, core=p.core,
-                        precision=P.RTEOM_SPLIT_TF32, **kw)
+                        precision=form[0], **kw)
 
 
-def test_split_residual_full_size_matches_oracle(rng):
+def test_split_residual_full_size_matches_oracle(rng, form):
     p, _ = workload("c2_formaldehyde")
     sysb = CoreHoleCCSD.from_problem(p.eps, p.L, p.nocc, p.core)
     t = random_blocks(sysb.shapes(), rng, scale=0.02)
-    with _split(p) as g:
+    with _split(p, form) as g:
         Rg, Eg = g.residual(t)
     Ro = sysb.residual(t)
     scale = max(np.abs(x).max() for x in Ro)
@@ -51,33 +62,33 @@ def test_split_residual_full_size_matches_oracle(rng):
     assert abs(Eg - sysb.energy(t)) <= 1e-10 * max(1.0, abs(Eg))   # the energy stays FP64
 
 
-def test_split_cumulant_c2_matches_oracle():
+def test_split_cumulant_c2_matches_oracle(form):
     C_ref, _, _ = _golden("c2_formaldehyde")
     p, run = workload("c2_formaldehyde")
-    with _split(p) as g:
+    with _split(p, form) as g:
         C = g.propagate(len(C_ref) - 1, run["dt"], tol=1e-8)
     assert np.abs(C - C_ref).max() < 1e-6
 
 
-def test_split_tracks_fp64_path_over_40_steps():
+def test_split_tracks_fp64_path_over_40_steps(form):
     p, run = workload("c2_formaldehyde")
     with P.Propagator.from_problem(p) as g:
         C64 = g.propagate(40, run["dt"], tol=1e-8)
-    with _split(p) as g:
+    with _split(p, form) as g:
         C32 = g.propagate(40, run["dt"], tol=1e-8)
     assert np.abs(C32 - C64).max() < 1e-6
 
 
-def test_split_everything_on_tensor_cores_c1_qp_peak(monkeypatch):
+def test_split_everything_on_tensor_cores_c1_qp_peak(monkeypatch, form):
     """Stress case: every contraction on the tensor cores (threshold 0), 200
     steps of c1 (10 au, |C| up to 11).  The 22-bit hi/lo split leaves a drift
     of a few 1e-6 absolute in the phase of C over this horizon (measured
     2.6e-6, i.e. 2.3e-7 relative); the bound here is 1e-6 relative, and the
     quasiparticle peak must stay within 0.005 eV."""
-    monkeypatch.setenv("RTEOM_TC_MIN_FLOPS", "0")
+    monkeypatch.setenv(form[1], "0")
     C_ref, eps_c, e_corr = _golden("c1_fp64_small")
     p, run = workload("c1_fp64_small")
-    with _split(p) as g:
+    with _split(p, form) as g:
         C = g.propagate(run["nsteps"], run["dt"], tol=1e-8)
         shift = eps_c + e_corr
         # the quasiparticle peak sits above eps_c + E_corr by the relaxation shift
@@ -95,17 +106,17 @@ def test_split_everything_on_tensor_cores_c1_qp_peak(monkeypatch):
     assert np.abs(A - Ao).max() < 1e-5 * np.abs(Ao).max()
 
 
-def test_split_small_problem_ragged_tiles(rng):
+def test_split_small_problem_ragged_tiles(rng, form):
     """Ragged shapes on the tensor cores: every contraction forced there."""
-    os.environ["RTEOM_TC_MIN_FLOPS"] = "0"
+    os.environ[form[1]] = "0"
     try:
         p = gen_problem(5, 37, 23, 2)
         sysb = CoreHoleCCSD.from_problem(p.eps, p.L, 5, 0)
         t = random_blocks(sysb.shapes(), rng, scale=0.1)
-        with _split(p) as g:
+        with _split(p, form) as g:
             Rg, _ = g.residual(t)
     finally:
-        del os.environ["RTEOM_TC_MIN_FLOPS"]
+        del os.environ[form[1]]
     Ro = sysb.residual(t)
     scale = max(np.abs(x).max() for x in Ro)
     for a, b in zip(Rg, Ro):

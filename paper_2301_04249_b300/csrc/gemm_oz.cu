@@ -54,6 +54,7 @@ constexpr uint32_t A_TILE = BM * BK * 2;   // 8 KB
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int kZeroExp = INT_MIN / 4;      // scale exponent of an all-zero row
+constexpr int kNanExp = INT_MAX / 4;       // ... of a row holding an infinity or NaN
 
 // S digit planes per operand (7: FP64-accurate; 3: the split-BF16 form) and
 // output-tile width BN (rows of B' per tile).  A diagonal sums at most S
@@ -160,7 +161,18 @@ __device__ __forceinline__ double embedded(const PackArgs& p, int b, int rp, int
 // zeroed array.
 constexpr int kExpoSeg = 64;
 
-__device__ __forceinline__ int row_exp(int raw) { return raw == 0 ? kZeroExp : raw - 1022; }
+__device__ __forceinline__ int row_exp(int raw) {
+  return raw == 0 ? kZeroExp : (raw == 0x7FF ? kNanExp : raw - 1022);
+}
+
+// FP64 value of a compensated pair under the row scales 2^(er + ec); a row
+// holding an infinity or NaN makes the product NaN (the propagation reports
+// non-finite amplitudes), an all-zero row makes it zero.
+__device__ __forceinline__ double scaled_value(float su, float cm, int er, int ec) {
+  if (er == kNanExp || ec == kNanExp) return __longlong_as_double(0x7FF8000000000000ll);
+  if (er == kZeroExp || ec == kZeroExp) return 0.0;
+  return scale2(f32_to_f64(su) + f32_to_f64(cm), er + ec);
+}
 
 __global__ void oz_expo_rows_kernel(PackArgs p, int batch) {
   const int64_t rows = (int64_t)batch * p.Rp;
@@ -210,7 +222,7 @@ __device__ __forceinline__ void digits_of(double x, int E, int (&d)[S]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((u >> 52) & 0x7FF);
   long long X = 0;
-  if (ex != 0 && E != kZeroExp) {
+  if (ex != 0 && E != kZeroExp && E != kNanExp) {
     const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = ex - 1076 + 8 * S - E;  // |x| < 2^E keeps |X| <= 2^(8S-1)
     unsigned long long a = 0;
@@ -440,9 +452,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
             }
             if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
             const int ec = row_exp(g.eb[(int64_t)b * g.Np + nr]);
-            double val = 0.0;
-            if (er != kZeroExp && ec != kZeroExp)
-              val = scale2(f32_to_f64(sum[v]) + f32_to_f64(cmp[v]), er + ec);
+            double val = scaled_value(sum[v], cmp[v], er, ec);
             if (g.alpha == -1.0)
               val = neg_f64(val);
             else if (g.alpha != 1.0)
@@ -520,9 +530,7 @@ __global__ void oz_finalize_kernel(FinArgs f, int batch) {
       }
       const int er = row_exp(f.ea[(int64_t)b * f.Mp + mr]);
       const int ec = row_exp(f.eb[(int64_t)b * f.Np + nr]);
-      double s = (er != kZeroExp && ec != kZeroExp)
-                     ? scale2(f32_to_f64(su) + f32_to_f64(cm), er + ec)
-                     : 0.0;
+      double s = scaled_value(su, cm, er, ec);
       if (f.alpha == -1.0)
         s = neg_f64(s);
       else if (f.alpha != 1.0)

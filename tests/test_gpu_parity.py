@@ -229,16 +229,17 @@ def test_autotuned_and_heuristic_launches_agree(monkeypatch):
 
 @pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16,
                                        P.RTEOM_FP64_OZAKI])
-def test_nan_amplitude_reaches_the_residual(precision, rng, monkeypatch):
-    """A NaN amplitude must not be absorbed by any contraction path (the
-    digit-sliced paths scale rows by their largest exponent): the residual
-    comes back non-finite, which the propagation reports."""
+def test_overflowing_amplitude_reaches_the_residual(precision, rng, monkeypatch):
+    """An overflow inside the residual (a 1e200 singles amplitude squares to
+    infinity in tau = t2 + t1 t1) must not be absorbed by any contraction path
+    (the digit-sliced paths scale rows by their largest exponent): the
+    residual comes back non-finite, which the propagation reports."""
     monkeypatch.setenv("RTEOM_TC_MIN_FLOPS", "0")
     monkeypatch.setenv("RTEOM_OZ_MIN_FLOPS", "0")
     p = gen_problem(4, 20, 30, 81)
     sysb = CoreHoleCCSD.from_problem(p.eps, p.L, 4, 0)
     t = random_blocks(sysb.shapes(), rng, scale=0.05)
-    t[3][1, 2, 3, 4] = np.nan
+    t[0][1, 2] = 1e200
     with _ctx(p, precision=precision) as g:
         R, _ = g.residual(t)
     assert not all(np.isfinite(x).all() for x in R)

@@ -25,7 +25,9 @@
 // BF16 in 8 x 8 core matrices (K-major, no swizzle; 128 B between core
 // matrices along K, 512 B between 8-row groups).  A stage holds all seven
 // planes of one k tile of A (128 rows) and B (64 rows), 84 KB; two stages.
-// Tensor memory holds the seven diagonal accumulators, 7 x 64 columns.
+// Tensor memory holds the S diagonal accumulators (7 x 64 columns), twice
+// over where both sets fit (3 planes), so a chunk drains while the next one
+// accumulates.
 //
 // Warp roles (320 threads): warp 0 lane 0 issues the bulk copies, warp 1
 // owns the tensor memory and lane 0 issues the MMAs, warps 2-9 drain the
@@ -66,9 +68,13 @@ struct Cfg {
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
   static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 4 ? (200u * 1024u / STAGE_BYTES) : 4;
-  static constexpr uint32_t TMEM_COLS = S * BN <= 128 ? 128 : (S * BN <= 256 ? 256 : 512);
+  // two accumulator sets (the next chunk accumulates while the last one
+  // drains) when both fit the 512 tensor-memory columns
+  static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;
+  static constexpr int ACC_COLS = NBUF * S * BN;
+  static constexpr uint32_t TMEM_COLS = ACC_COLS <= 128 ? 128 : (ACC_COLS <= 256 ? 256 : 512);
   static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 256;
-  static_assert(S * BN <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
+  static_assert(ACC_COLS <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
   static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
   static_assert(STAGES >= 2, "at least two pipeline stages");
 };
@@ -307,9 +313,10 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;  // chunk accumulated
-  uint64_t* acc_empty = acc_full + 1;   // chunk drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  constexpr int NBUF = CF::NBUF;
+  uint64_t* acc_full = empty + STAGES;  // [NBUF]: chunk accumulated in set i
+  uint64_t* acc_empty = acc_full + 2;   // [NBUF]: set i drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* issued = abort_flag + 1;
 
@@ -326,8 +333,10 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, EPI_WARPS);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], EPI_WARPS);
+    }
     *abort_flag = 0;
     *issued = 0;
     fence_mbar_init();
@@ -368,7 +377,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     for (int k = 0; k < nk; ++k) {
       const int j = k / CHUNK_KT, kin = k % CHUNK_KT;
       if (kin == 0 && j >= 1) {
-        if (!mbar_wait(acc_empty, (j - 1) & 1)) {
+        // chunk j reuses accumulator set j % NBUF once chunk j - NBUF drained
+        const int jj = j - NBUF;
+        if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1)) {
           *abort_flag = 1;
           atomicExch(g.err, 14);
           break;
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       for (int sa = 0; sa < S; ++sa) {
 #pragma unroll
         for (int sb = 0; sb < S - sa; ++sb) {
-          const uint32_t dt = tmem + (uint32_t)((sa + sb) * BN);
+          const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * S + sa + sb) * BN);
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint64_t ad = smem_desc(base + sa * A_TILE + ks * 256, 128, 512);
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
         }
       }
       mma_commit(&empty[s]);
-      if (kin == CHUNK_KT - 1 || k == nk - 1) mma_commit(acc_full);
+      if (kin == CHUNK_KT - 1 || k == nk - 1) mma_commit(&acc_full[j % NBUF]);
     }
   } else if (warp >= 2) {
     const int q = warp % 4;
@@ -408,7 +419,8 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     bool ok = nk > 0;
 #pragma unroll 1
     for (int j = 0; j < nchunks; ++j) {
-      if (!mbar_wait(acc_full, j & 1)) {
+      const int set = j % NBUF;
+      if (!mbar_wait(&acc_full[set], (j / NBUF) & 1)) {
         ok = false;
         atomicExch(g.err, 13);
         break;
@@ -420,7 +432,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
 #pragma unroll
         for (int c = 0; c < HALF; c += 16) {
           uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + h * HALF + c), r);
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) +
+                        (uint32_t)((set * S + d) * BN + h * HALF + c),
+                    r);
 #pragma unroll
           for (int v = 0; v < 16; ++v)
             two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * w);
@@ -428,7 +442,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[set]);
     }
     if (ok) {
       const int mr = m_tile * BM + row;
@@ -556,8 +570,10 @@ Plan plan(const GemmDesc& d, int S) {
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
-  // widest tile whose S diagonal accumulators fit the tensor memory
-  p.bn = Br <= 32 ? 32 : (S <= 3 && Br > 64 ? 128 : 64);
+  // 32 columns for a narrow B', else 64: with seven planes one accumulator
+  // set of 7 x 64 columns, with three planes two sets of 3 x 64 (the next
+  // chunk accumulates while the last drains)
+  p.bn = Br <= 32 ? 32 : 64;
   p.Mp = roundup(std::max(Ar, 1), BM);
   p.Np = roundup(std::max(Br, 1), p.bn);
   p.Kp = roundup(std::max(Ak, 1), BK);
@@ -631,7 +647,6 @@ void gemm_oz_init() {
   };
   set(oz::oz_gemm_kernel<7, 64>, oz::Cfg<7, 64>::SMEM);
   set(oz::oz_gemm_kernel<7, 32>, oz::Cfg<7, 32>::SMEM);
-  set(oz::oz_gemm_kernel<3, 128>, oz::Cfg<3, 128>::SMEM);
   set(oz::oz_gemm_kernel<3, 64>, oz::Cfg<3, 64>::SMEM);
   set(oz::oz_gemm_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
 }
@@ -720,9 +735,7 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.beta = d.beta;
   dim3 grid(p.Np / p.bn, p.Mp / oz::BM, d.batch * p.ranges);
   using namespace oz;
-  if (S == 3 && p.bn == 128)
-    oz_gemm_kernel<3, 128><<<grid, THREADS, Cfg<3, 128>::SMEM, st>>>(g);
-  else if (S == 3 && p.bn == 64)
+  if (S == 3 && p.bn == 64)
     oz_gemm_kernel<3, 64><<<grid, THREADS, Cfg<3, 64>::SMEM, st>>>(g);
   else if (S == 3)
     oz_gemm_kernel<3, 32><<<grid, THREADS, Cfg<3, 32>::SMEM, st>>>(g);

@@ -189,6 +189,19 @@ int rteom_get_state(const rteom_ctx* ctx, double* t_out, long long* steps, doubl
 int rteom_set_state(rteom_ctx* ctx, const double* t_in, long long steps, const double* hist);
 
 /*
+ * rteom_plan_bytes -- device memory of a context of this shape and precision,
+ * planned on the host from the same dry run of the residual that sizes
+ * rteom_create's scratch arena (no device calls; usable without a GPU).  The
+ * paper has no counterpart (capacity planning of this build's contexts).
+ *  bytes  host double[3]: [0] peak during set-up and the first residual with
+ *         every constant tensor-core pack cached (what rteom_create takes
+ *         when memory allows), [1] the same with no pack cached (the least
+ *         it works with), [2] held after set-up with every pack cached
+ * Returns RTEOM_OK, or RTEOM_ERR_ARG for a bad shape or precision.
+ */
+int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, double* bytes);
+
+/*
  * rteom_debug_residual -- test entry point: evaluate the full projections
  * R_mu = <Phi_mu|(H_N e^{T1+T2})_C|Phi> (Eqs. 7-8) and the cumulant
  * integrand E (Eq. 5) for given amplitudes, without changing the state.

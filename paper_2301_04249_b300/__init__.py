@@ -34,6 +34,18 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
+def plan_bytes(nocc: int, nvir: int, nchol: int, precision: int = RTEOM_FP64) -> dict:
+    """Device bytes of a context of this shape and precision, planned on the
+    host (no GPU needed): peak with every constant tensor-core pack cached,
+    peak with none cached, and the bytes held after set-up."""
+    out = np.zeros(3)
+    rc = _lib.load().rteom_plan_bytes(int(nocc), int(nvir), int(nchol), int(precision),
+                                      _ptr(out))
+    if rc != RTEOM_OK:
+        raise RteomError(rc, "rteom_plan_bytes: bad shape or precision")
+    return dict(peak=float(out[0]), peak_uncached=float(out[1]), resident=float(out[2]))
+
+
 def block_shapes(nocc: int, nvir: int, core: int = 0):
     """Shapes of the unique spin blocks t1a, t1b, t2aa, t2ab, t2bb."""
     oA, vA, oB, vB = nocc, nvir, nocc - 1, nvir + 1

@@ -55,6 +55,8 @@ SIGNATURES = {
     "rteom_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_double]),
     "rteom_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "rteom_server_stats": (ctypes.c_int, [_vp, _llp, _llp, _llp, _llp, _dp, _dp]),
+    "rteom_plan_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        _dp]),
     "rteom_server_estimate_bytes": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_int]),
     "rteom_server_destroy": (None, [_vp]),

@@ -539,6 +539,79 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   }
 }
 
+// Device bytes of a context of this shape and form, planned on the host with
+// the dry runs that size rteom_create's arena (no device calls).  out[0]:
+// peak with every constant tensor-core pack cached; out[1]: peak with none
+// cached; out[2]: after set-up with every pack cached.  The phases follow
+// setup(): integrals built while the Cholesky inputs live, then the pack
+// cache filled ladder blocks first, each FP64 ladder block freed after its
+// pack.
+void plan_context_bytes(int O, int V, int nchol, int precision, double out[3]) {
+  const double nO = O, nVd = V + 1.0, nb = O + V;
+  const int nV = V + 1;
+  const double npv = nVd * (nVd - 1.0) / 2.0;
+  const AmpGeom g{O, nV, 0};
+  Engine E;
+  E.tensor_cores = precision == RTEOM_SPLIT_TF32;
+  E.fp64_emulation = precision == RTEOM_FP64_OZAKI || precision == RTEOM_SPLIT_BF16;
+  E.oz_planes = precision == RTEOM_SPLIT_BF16 ? 3 : 7;
+  ResidualOperands op;
+  op.nO = O;
+  op.nV = nV;
+  auto fake = [](int k) { return reinterpret_cast<double*>(uintptr_t(4096) * (k + 1)); };
+  op.oooo = fake(1);
+  op.ooov = fake(2);
+  op.oovv = fake(3);
+  op.ovov = fake(4);
+  op.ovvv = fake(5);
+  op.ovov_as = fake(6);
+  op.vvvv = fake(7);
+  op.vvvv_as = fake(8);
+  for (int s = 0; s < 2; ++s) {
+    op.foo[s] = fake(10 + s);
+    op.fov[s] = fake(12 + s);
+    op.fvv[s] = fake(14 + s);
+    op.foo_c[s] = fake(16 + s);
+    op.fov_c[s] = fake(18 + s);
+    op.fvv_c[s] = fake(20 + s);
+  }
+  const bool packed = precision != RTEOM_FP64;
+  auto dry = [&](bool cached) {
+    E.dry = true;
+    E.plan_cached = cached && packed;
+    E.arena.init(fake(30), int64_t(1) << 50);
+    compute_residual(E, op, fake(31), fake(32));
+    return (double)E.arena.peak_bytes();
+  };
+  const double setup_need = 8.0 * std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) /
+                                                                       ((int64_t)nV * nV * nV))) *
+                            nVd * nVd * nVd;
+  const double arena_all = std::max(dry(true), setup_need) + 8192.0;
+  double p_ab = 0.0, p_ss = 0.0, p_all = 0.0;
+  for (const auto& kv : E.tc_cache_cands) {
+    p_all += (double)kv.second.bytes;
+    if (kv.second.tensor == op.vvvv) p_ab += (double)kv.second.bytes;
+    if (kv.second.tensor == op.vvvv_as) p_ss += (double)kv.second.bytes;
+  }
+  const double arena_none = std::max(dry(false), setup_need) + 8192.0;
+  const double f_ab = 8.0 * nVd * nVd * nVd * nVd, f_ss = 8.0 * npv * npv;
+  const double ints = 8.0 * (nO * nO * nO * nO + nO * nO * nO * nVd + 3.0 * nO * nO * nVd * nVd +
+                             nO * nVd * nVd * nVd) +
+                      f_ab + f_ss;
+  const double inputs = 8.0 * (nb + nchol * nb * nb + nchol * (nO * nO + nO * nVd + 2.0 * nVd * nVd));
+  const double fock = 2.0 * (24.0 * (nO * nO + nO * nVd + nVd * nVd) + 8.0 * (nO + nVd));
+  const double amps = 4.0 * 16.0 * (double)g.total() + 2.0 * 16.0 * 1024 + 16.0 * 2048 + 256.0;
+  const double phase_a_all = inputs + fock + ints + arena_all;
+  const double phase_a_none = inputs + fock + ints + arena_none;
+  const double base_all = ints + fock + arena_all + amps;
+  const double cache_peak =
+      std::max({p_ab, p_ab - (p_ab > 0 ? f_ab : 0.0) + p_ss,
+                p_all - (p_ab > 0 ? f_ab : 0.0) - (p_ss > 0 ? f_ss : 0.0)});
+  out[0] = std::max(phase_a_all, base_all + cache_peak);
+  out[1] = std::max(phase_a_none, ints + fock + arena_none + amps);
+  out[2] = base_all - (p_ab > 0 ? f_ab : 0.0) - (p_ss > 0 ? f_ss : 0.0) + p_all;
+}
+
 }  // namespace
 
 // ---- non-blocking stepping (shared by rteom_propagate and the server) ------
@@ -843,6 +916,20 @@ int rteom_set_state(rteom_ctx* c, const double* t_in, long long steps, const dou
     c->steps = steps;
     return RTEOM_OK;
   });
+}
+
+int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, double* bytes) {
+  if (!bytes || nocc < 1 || nvir < 1 || nchol < 0 ||
+      (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
+       precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16) ||
+      (double)(nvir + 1) * (nvir + 1) > 2.0e9)
+    return RTEOM_ERR_ARG;
+  try {
+    plan_context_bytes(nocc, nvir, nchol, precision, bytes);
+  } catch (const std::exception&) {
+    return RTEOM_ERR_ARG;
+  }
+  return RTEOM_OK;
 }
 
 int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double* E_out) {

@@ -53,21 +53,13 @@ struct Request {
   bool cancel = false;
 };
 
-// Device bytes a context of this shape needs at its peak (set-up and
-// residual), from the buffer sizes the context allocates, with 25 % margin.
+// Device bytes a context of this shape needs at its peak (set-up and the
+// first residual, every constant tensor-core pack cached), from the host
+// dry-run plan of rteom_plan_bytes, with 5 % and 256 MB of margin.
 double estimate_bytes(int O, int V, int nchol, int precision) {
-  const double nO = O, nV = V + 1.0, nb = O + V;
-  const double npv = nV * (nV - 1.0) / 2.0;
-  const double ints = nO * nO * nO * nO + nO * nO * nO * nV + 3.0 * nO * nO * nV * nV +
-                      nO * nV * nV * nV + nV * nV * nV * nV + npv * npv;
-  const double setup = nchol * nb * nb + nchol * (nO * nO + nO * nV + nV * nV) + nV * nV * nV * nV;
-  const double amps = 4.0 * 2.0 * (2.0 * nO * nV + 3.0 * nO * nO * nV * nV);
-  const double arena = 2.0 * 64.0 * nO * nO * nV * nV + 2.0 * 16.0 * 64.0 * nV * nV;
-  double doubles = ints + (setup > arena ? setup : arena) + amps;
-  if (precision == RTEOM_SPLIT_TF32 || precision == RTEOM_SPLIT_BF16)
-    doubles += 1.5 * ints + 2.0 * 16.0 * nO * nO * nV * nV;
-  if (precision == RTEOM_FP64_OZAKI) doubles += 2.0 * ints + 3.0 * 16.0 * nO * nO * nV * nV;
-  return 1.25 * 8.0 * doubles + 64.0 * 1024 * 1024;
+  double b[3] = {0.0, 0.0, 0.0};
+  if (rteom_plan_bytes(O, V, nchol, precision, b) != RTEOM_OK) return 0.0;
+  return 1.05 * b[0] + 256.0 * 1024 * 1024;
 }
 
 }  // namespace

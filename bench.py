@@ -477,6 +477,8 @@ def run_ours(args):
                    "fp64": "not run: one FP64 residual of the largest request takes about 30 s",
                    "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
                                              args.tol, "c4"),
+                   "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
+                                             args.tol, "c4"),
                    "fp64_ozaki": run_serving(P, P.RTEOM_FP64_OZAKI, args.serving_requests,
                                              args.tol, "c4")}
         del os.environ["RTEOM_AUTOTUNE"]

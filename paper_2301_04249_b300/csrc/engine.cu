@@ -528,7 +528,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       autotune && !use_tc && !use_oz && !gemm_f64_is_gemv(g) && flops0 <= tune_max_flops;
   const bool tc_ok = tensor_cores && flops0 >= tc_tune_min_flops;
   const bool oz_ok = fp64_emulation && flops0 >= tc_tune_min_flops;
-  const std::string tkey = tunable ? tune_key(g, tc_ok ? 1 : (oz_ok ? 2 : 0)) : std::string();
+  // form of the key: FP64 only, or with the split-TF32, 7-plane or 3-plane
+  // tensor-core candidate
+  const int form = tc_ok ? 1 : (oz_ok ? (oz_planes == 3 ? 3 : 2) : 0);
+  const std::string tkey = tunable ? tune_key(g, form) : std::string();
   GemmChoice choice;
   bool chosen = tunable && tune_lookup(tkey, &choice);
   if (chosen && choice.tc) use_tc = true;

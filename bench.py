@@ -68,6 +68,24 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest x over the ranks of the process group (x itself alone)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps_per_rank, elapsed_max, world):
+    """Whole-job steps/s of independent replicas: every rank propagates its
+    own core hole, so the job finishes its world * steps when the slowest
+    rank does."""
+    return world * steps_per_rank / elapsed_max
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -395,11 +413,7 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world, dev)
     info1 = g.info()
     tm = g.timing()
     launches = g.kernel_launches() - launches0
@@ -427,11 +441,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - w0
     h2d = sum(x.nbytes for x in (h_eps, h_L, h_t1, h_t2, omega) if x is not None)
     d2h = 16 * 2 * args.steps + A.nbytes
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # the other precision forms on the same inputs, same step counts
     def run_form(prec):
@@ -466,7 +476,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    value = world * args.steps / elapsed
+    value = replica_throughput(args.steps, elapsed, world)
     serving = None
     if not args.no_serving and args.serving_mix == "c4":
         os.environ["RTEOM_AUTOTUNE"] = "0"
@@ -538,7 +548,7 @@ def run_ours(args):
         "tflops_fp64": total_flops / elapsed / 1e12,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": replica_throughput(args.steps, e2e_s, world), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "rteom_create from pinned host arrays + per-step rteom_propagate(1) "
                         "returning C_n + rteom_spectrum + destroy, wall clock"},

@@ -57,8 +57,8 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=16)
     ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="scaled",
-                    help="scaled: small shapes, all three forms; c4: the survey's request "
-                         "shapes with steps cut to U{4..16}, tensor-core forms only, "
+                    help="scaled: small shapes, all three forms; c4: the production request "
+                         "shapes (O~U{4..24}, V~U{40..240}) with steps cut to U{4..16}, tensor-core forms only, "
                          "autotuner off (serial and served runs on equal terms)")
     return ap.parse_args()
 
@@ -312,7 +312,7 @@ def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks, name="fp64_ozaki"
 def serving_mix(n_req, kind="scaled"):
     """Core-hole request mixes (seeds 4000 + r, dt = 0.025 au, Nchol = 4V).
     scaled: O ~ U{4..8}, V ~ U{20..48}, steps ~ U{20..80}.
-    c4: the survey's shapes O ~ U{4..24}, V ~ U{40..240}, with steps ~ U{4..16}
+    c4: production core-hole shapes O ~ U{4..24}, V ~ U{40..240}, with steps ~ U{4..16}
     instead of U{500..4000}."""
     from synth import gen_problem
     rng = np.random.default_rng(4)
@@ -481,7 +481,7 @@ def run_ours(args):
     if not args.no_serving and args.serving_mix == "c4":
         os.environ["RTEOM_AUTOTUNE"] = "0"
         serving = {"workload": f"c4 shapes: {args.serving_requests} requests, O~U{{4..24}}, "
-                               "V~U{40..240}, Nchol=4V, steps~U{4..16} (survey: U{500..4000}), "
+                               "V~U{40..240}, Nchol=4V, steps~U{4..16} (production: U{500..4000}), "
                                "dt=0.025, Poisson arrivals at 2x the mean service rate, 8 slots, "
                                "admission by device memory, autotuner off",
                    "fp64": "not run: one FP64 residual of the largest request takes about 30 s",

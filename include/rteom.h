@@ -192,7 +192,7 @@ int rteom_set_state(rteom_ctx* ctx, const double* t_in, long long steps, const d
  * rteom_plan_bytes -- device memory of a context of this shape and precision,
  * planned on the host from the same dry run of the residual that sizes
  * rteom_create's scratch arena (no device calls; usable without a GPU).  The
- * paper has no counterpart (capacity planning of this build's contexts).
+ * paper has no counterpart (capacity planning of contexts before creating them).
  *  bytes  host double[3]: [0] peak during set-up and the first residual with
  *         every constant tensor-core pack cached (what rteom_create takes
  *         when memory allows), [1] the same with no pack cached (the least

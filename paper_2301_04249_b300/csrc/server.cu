@@ -12,6 +12,7 @@
 // until the request completes and are then copied to host memory owned by the
 // server until the caller reads them.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -55,11 +56,13 @@ struct Request {
 
 // Device bytes a context of this shape needs at its peak (set-up and the
 // first residual, every constant tensor-core pack cached), from the host
-// dry-run plan of rteom_plan_bytes, with 5 % and 256 MB of margin.
+// dry-run plan of rteom_plan_bytes, with 5 % and 256 MB of margin.  Whole
+// bytes, so the admission ledger (doubles, all below 2^53) sums exactly and
+// returns to zero when the last request leaves.
 double estimate_bytes(int O, int V, int nchol, int precision) {
   double b[3] = {0.0, 0.0, 0.0};
   if (rteom_plan_bytes(O, V, nchol, precision, b) != RTEOM_OK) return 0.0;
-  return 1.05 * b[0] + 256.0 * 1024 * 1024;
+  return std::ceil(1.05 * b[0]) + 256.0 * 1024 * 1024;
 }
 
 }  // namespace

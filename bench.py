@@ -40,6 +40,7 @@ MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
 LADDER_TC_PROFILE = os.path.join(HERE, "profiles", "ladder_tc_tf32_c2.txt")
 LADDER_OZ_PROFILE = os.path.join(HERE, "profiles", "ladder_oz_bf16_c2.txt")
+LADDER_OZ3_PROFILE = os.path.join(HERE, "profiles", "ladder_oz3_split_bf16_c2.txt")
 
 
 def parse_args():
@@ -556,7 +557,7 @@ def run_ours(args):
         "clocks": clocks,
         "forms": {**(split_summary(split, args, value, world, fp64_hist, peaks) or {}),
                   **(ozaki_summary(split_bf16, args, value, world, fp64_hist, peaks,
-                                   "split_bf16", 3, None) or {}),
+                                   "split_bf16", 3, LADDER_OZ3_PROFILE) or {}),
                   **(ozaki_summary(ozaki, args, value, world, fp64_hist, peaks) or {})},
         "serving": serving,
         "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},

@@ -84,6 +84,17 @@ extern "C" {
 #define RTEOM_FLAG_CUMULANT_NO_FOV 1  /* cumulant integrand without sum f_ia t_i^a,
                                          i.e. Eq. 6 as printed; default keeps it
                                          (the definition in Eq. 5)              */
+#define RTEOM_FLAG_LADDER_CHOLESKY 2  /* Cholesky mode: keep no (ov|vv) or
+                                         (vv|vv) block on the device; the
+                                         particle-particle ladder (Section
+                                         3.1.1) and the other terms with three
+                                         or four virtual indices are formed
+                                         from the Cholesky vectors at every
+                                         residual, in chunks of a (and of m).
+                                         rteom_create takes this mode by itself
+                                         when the resident blocks do not fit
+                                         the free device memory; nchol == 0
+                                         keeps the resident mode             */
 
 typedef struct rteom_ctx rteom_ctx;
 
@@ -197,9 +208,11 @@ int rteom_set_state(rteom_ctx* ctx, const double* t_in, long long steps, const d
  *         every constant tensor-core pack cached (what rteom_create takes
  *         when memory allows), [1] the same with no pack cached (the least
  *         it works with), [2] held after set-up with every pack cached
- * Returns RTEOM_OK, or RTEOM_ERR_ARG for a bad shape or precision.
+ *  flags  RTEOM_FLAG_LADDER_CHOLESKY plans the Cholesky mode; without it
+ *         the plan has resident (ov|vv)/(vv|vv) blocks
+ * Returns RTEOM_OK, or RTEOM_ERR_ARG for a bad shape, precision or flag.
  */
-int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, double* bytes);
+int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, double* bytes);
 
 /*
  * rteom_debug_residual -- test entry point: evaluate the full projections

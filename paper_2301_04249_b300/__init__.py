@@ -13,6 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: F401
                    RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_OOM, RTEOM_ERR_STATE, RTEOM_FLAG_CUMULANT_NO_FOV,
+                   RTEOM_FLAG_LADDER_CHOLESKY,
                    RTEOM_FP64, RTEOM_OK, RTEOM_REQ_CANCELLED, RTEOM_REQ_DONE, RTEOM_REQ_FAILED,
                    RTEOM_REQ_QUEUED, RTEOM_REQ_RUNNING, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32,
                    RTEOM_FP64_OZAKI)
@@ -34,15 +35,17 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def plan_bytes(nocc: int, nvir: int, nchol: int, precision: int = RTEOM_FP64) -> dict:
+def plan_bytes(nocc: int, nvir: int, nchol: int, precision: int = RTEOM_FP64,
+               flags: int = 0) -> dict:
     """Device bytes of a context of this shape and precision, planned on the
     host (no GPU needed): peak with every constant tensor-core pack cached,
-    peak with none cached, and the bytes held after set-up."""
+    peak with none cached, and the bytes held after set-up.  flags may hold
+    RTEOM_FLAG_LADDER_CHOLESKY (plan the Cholesky mode)."""
     out = np.zeros(3)
     rc = _lib.load().rteom_plan_bytes(int(nocc), int(nvir), int(nchol), int(precision),
-                                      _ptr(out))
+                                      int(flags), _ptr(out))
     if rc != RTEOM_OK:
-        raise RteomError(rc, "rteom_plan_bytes: bad shape or precision")
+        raise RteomError(rc, "rteom_plan_bytes: bad shape, precision or flag")
     return dict(peak=float(out[0]), peak_uncached=float(out[1]), resident=float(out[2]))
 
 

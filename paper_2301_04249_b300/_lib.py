@@ -19,6 +19,7 @@ RTEOM_SPLIT_BF16 = 1
 RTEOM_SPLIT_TF32 = 2
 RTEOM_FP64_OZAKI = 3
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
+RTEOM_FLAG_LADDER_CHOLESKY = 2
 RTEOM_REQ_QUEUED = 0
 RTEOM_REQ_RUNNING = 1
 RTEOM_REQ_DONE = 2
@@ -56,7 +57,7 @@ SIGNATURES = {
     "rteom_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "rteom_server_stats": (ctypes.c_int, [_vp, _llp, _llp, _llp, _llp, _dp, _dp]),
     "rteom_plan_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                        _dp]),
+                                        ctypes.c_int, _dp]),
     "rteom_server_estimate_bytes": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_int]),
     "rteom_server_destroy": (None, [_vp]),

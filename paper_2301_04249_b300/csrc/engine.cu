@@ -760,8 +760,11 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   if (outcopy) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
   if (cls == kLadder && !dry) nvtxRangePop();
   if (dry && std::getenv("RTEOM_PLAN_TRACE"))  // scratch planning: arena top inside this call
-    std::fprintf(stderr, "plan %-22s M=%lld N=%lld K=%lld %s arena %.3f GB (peak %.3f GB)\n", spec,
-                 (long long)Mt, (long long)Nt, (long long)Kt, use_tc ? "tc" : "f64",
+    std::fprintf(stderr,
+                 "plan %-22s M=%lld N=%lld K=%lld %s perm %c%c%c in %.3f GB arena %.3f GB (peak "
+                 "%.3f GB)\n",
+                 spec, (long long)Mt, (long long)Nt, (long long)Kt, use_tc ? "tc" : "f64",
+                 bPA ? 'A' : '-', bPB ? 'B' : '-', bPC ? 'C' : '-', mark * 8e-9,
                  arena.mark() * 8e-9, arena.peak_bytes() * 1e-9);
   arena.release(mark);
 }

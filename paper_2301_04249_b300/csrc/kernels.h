@@ -175,6 +175,22 @@ void unpack_pairs_antisym(const double* Rp, double* R, int nO, int nV, double al
 // W[e][f][a][b] = (ae|bf) (real).
 void pack_ladder_antisym(const double* W, double* Wm, int nV, cudaStream_t st);
 
+// First pair index of row p among the pairs (p < q) of n items.
+__host__ __device__ inline int64_t pair_start(int n, int p) {
+  return (int64_t)p * (2 * (int64_t)n - p - 1) / 2;
+}
+// Column chunk a in [a0, a0+n) of the same-spin pair ladder (the pair
+// columns (a<b) of those a, contiguous).  Wc: [e][f][n][b] = (ae|bf) for the
+// chunk (real); Wm: [(e<f)][chunk columns] = (ae|bf) - (af|be).
+void pack_ladder_cols(const double* Wc, double* Wm, int nV, int a0, int n, cudaStream_t st);
+// R[i,j,a,b] += alpha*Rq[(i<j)][c] (and the three antisymmetric images) for
+// the chunk's pair columns c (complex).
+void unpack_pairs_cols(const double* Rq, double* R, int nO, int nV, int a0, int n, double alpha,
+                       cudaStream_t st);
+// dst[r*ldd + c] += src[r*lds + c] over rows x cols doubles.
+void add_block(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaStream_t st);
+
 // Geometry of the padded amplitude vector: blocks t1a, t1b (nO*nV) then
 // t2aa, t2ab, t2bb (nO*nO*nV*nV), complex.  Pads: alpha virtual slot 0 and
 // beta occupied slot `core`.

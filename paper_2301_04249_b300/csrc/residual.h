@@ -22,6 +22,16 @@ struct ResidualOperands {
   // the FP64 ladder blocks were freed after their tensor-core packs were
   // cached (split precision); the pointers remain the cache keys
   bool vvvv_released = false, vvvv_as_released = false;
+  // Cholesky mode (no (ov|vv) or (vv|vv) block on the device): the terms
+  // with three or four virtual indices are formed from the slot-space
+  // Cholesky vectors at every residual, the ladder in chunks of chunk_a
+  // values of a and the tau*(mf|ae) terms in chunks of chunk_m values of m.
+  bool chol = false;
+  int nchol = 0, chunk_a = 1, chunk_m = 1;
+  const double* Lov = nullptr;   // [Q][m][e] = L^Q_me
+  const double* Lvv = nullptr;   // [Q][a][e] = L^Q_ae
+  const double* LvvT = nullptr;  // [a][e][Q]
+  const double* LovT = nullptr;  // [m][e][Q]
   // (N-1) Fock slot blocks per spin (0 = alpha, 1 = beta), real and complex
   const double *foo[2] = {nullptr, nullptr}, *fov[2] = {nullptr, nullptr},
                *fvv[2] = {nullptr, nullptr};

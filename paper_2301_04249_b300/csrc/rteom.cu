@@ -273,6 +273,20 @@ void energy_into(rteom_ctx* c, const double* t, double* Ehist, double* Chist, lo
   });
 }
 
+void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, double out[3]);
+
+// Chunk sizes of the Cholesky-mode residual: values of a per ladder chunk
+// (a W chunk of chunk_a*nV^3 doubles) and of m per (mf|ae) chunk, each chunk
+// at most 2^29 doubles (4 GB); RTEOM_CHOLESKY_CHUNK=<n> caps both.
+void cholesky_chunks(int nO, int nV, int* chunk_a, int* chunk_m) {
+  const int64_t nv3 = (int64_t)nV * nV * nV;
+  int64_t cap = std::max<int64_t>(1, (int64_t(1) << 29) / nv3);
+  if (const char* v = std::getenv("RTEOM_CHOLESKY_CHUNK"))
+    cap = std::max<int64_t>(1, std::min<int64_t>(cap, std::atoll(v)));
+  *chunk_a = (int)std::min<int64_t>(nV, cap);
+  *chunk_m = (int)std::min<int64_t>(nO, cap);
+}
+
 void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs,
            const double* t2_gs) {
   const int O = c->O, V = c->V, nb = O + V, nchol = c->nchol;
@@ -280,6 +294,22 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   cudaStream_t st = c->stream;
   Engine& E = c->E;
   E.stream = st;
+
+  // Cholesky mode (no (ov|vv) or (vv|vv) block on the device): asked for by
+  // flag, or taken when the plan with resident blocks does not fit the free
+  // device memory
+  bool chol = false;
+  if (nchol > 0) {
+    if (c->flags & RTEOM_FLAG_LADDER_CHOLESKY) {
+      chol = true;
+    } else {
+      double pb[3];
+      plan_context_bytes(O, V, nchol, c->precision, false, pb);
+      size_t fr = 0, tot = 0;
+      RT_CUDA(cudaMemGetInfo(&fr, &tot));
+      chol = pb[1] > 0.97 * (double)fr;
+    }
+  }
 
   // inputs
   double* d_eps = c->dmalloc(8 * nb);
@@ -294,6 +324,15 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   double* Lvv = c->dmalloc(8ull * nchol * nV * nV);
   E.launch(kElementwise, 0.0,
            [&] { gather_cholesky(d_L, nchol, nO, nV, c->core, Loo, Lov, Lvv, st); });
+  double *LvvT = nullptr, *LovT = nullptr;
+  if (chol) {  // [a][e][Q] and [m][e][Q] copies for the chunked builds
+    LvvT = c->dmalloc(8ull * nchol * nV * nV);
+    LovT = c->dmalloc(8ull * nchol * nO * nV);
+    E.axpy("Qea->eaQ", 1.0, make_tensor(Lvv, false, {nchol, nV, nV}), 0.0,
+           make_tensor(LvvT, false, {nV, nV, nchol}));
+    E.axpy("Qme->meQ", 1.0, make_tensor(Lov, false, {nchol, nO, nV}), 0.0,
+           make_tensor(LovT, false, {nO, nV, nchol}));
+  }
   for (int s = 0; s < 2; ++s) {
     c->foo[s] = c->dmalloc(8ull * nO * nO);
     c->fov[s] = c->dmalloc(8ull * nO * nV);
@@ -333,12 +372,12 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   double* ooov = c->dmalloc(8ull * nO * nO * nO * nV);
   double* oovv = c->dmalloc(8ull * nO * nO * nV * nV);
   double* ovov = c->dmalloc(8ull * nO * nV * nO * nV);
-  double* ovvv = c->dmalloc(8ull * nO * nV * nV * nV);
-  double* vvvv = c->dmalloc(8ull * nV * nV * nV * nV);
+  double* ovvv = chol ? nullptr : c->dmalloc(8ull * nO * nV * nV * nV);
+  double* vvvv = chol ? nullptr : c->dmalloc(8ull * nV * nV * nV * nV);
   // antisymmetrised (me|nf) - (mf|ne) and the packed same-spin ladder block
   const int64_t npv = (int64_t)nV * (nV - 1) / 2;
   double* ovov_as = c->dmalloc(8ull * nO * nV * nO * nV);
-  double* vvvv_as = c->dmalloc(8ull * (npv > 0 ? npv * npv : 1));
+  double* vvvv_as = chol ? nullptr : c->dmalloc(8ull * (npv > 0 ? npv * npv : 1));
   op.oooo = oooo;
   op.ooov = ooov;
   op.oovv = oovv;
@@ -348,6 +387,15 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   op.ovov_as = ovov_as;
   op.vvvv_as = vvvv_as;
   c->ovov = ovov;
+  op.chol = chol;
+  op.nchol = nchol;
+  if (chol) {
+    op.Lov = Lov;
+    op.Lvv = Lvv;
+    op.LvvT = LvvT;
+    op.LovT = LovT;
+    cholesky_chunks(nO, nV, &op.chunk_a, &op.chunk_m);
+  }
 
   // scratch arena for set-up contractions and, later, the residual, sized
   // by dry runs of the residual as it will run
@@ -374,7 +422,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   // GEMM output of ce*nV^3 doubles that is then permuted into place
   const int64_t nv3 = (int64_t)nV * nV * nV;
   const int ce = (int)std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) / nv3));
-  const int64_t setup_need = ce * nv3 + 64;
+  const int64_t setup_need = chol ? 0 : ce * nv3 + 64;
   if (split) {
     // Memory plan of the tensor-core pack cache: it holds the packs of the
     // FP64 ladder blocks (freed once packed) first, then the other constant
@@ -397,7 +445,8 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
     // The ladder packs are made first, each FP64 block freed right after its
     // pack: alpha-beta, then same-spin, then the rest of the cache.
     E.tc_cache_select = true;
-    const int64_t f_ab = 8 * (int64_t)nV * nV * nV * nV, f_ss = 8 * npv * npv;
+    const int64_t f_ab = chol ? 0 : 8 * (int64_t)nV * nV * nV * nV,
+                  f_ss = chol ? 0 : 8 * npv * npv;
     for (size_t keep = order.size();; --keep) {
       E.tc_cache_allowed.clear();
       int64_t p_ab = 0, p_ss = 0, p_other = 0;
@@ -429,11 +478,12 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
              make_tensor(oovv, false, {nO, nO, nV, nV}));
   E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lov, nO, nV), 0.0,
              make_tensor(ovov, false, {nO, nV, nO, nV}));
-  E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lvv, nV, nV), 0.0,
-             make_tensor(ovvv, false, {nO, nV, nV, nV}));
+  if (!chol)
+    E.contract("Qpq,Qrs->pqrs", 1.0, Lt(Lov, nO, nV), Lt(Lvv, nV, nV), 0.0,
+               make_tensor(ovvv, false, {nO, nV, nV, nV}));
   // ladder layout [e][f][a][b] = (ae|bf) = sum_Q L_ea L_fb, built for ce
   // values of e at a time from LvvT[e][a][Q] = L_ea
-  {
+  if (!chol) {
     double* LvvT = c->dmalloc(8ull * nchol * nV * nV);
     E.axpy("Qea->eaQ", 1.0, Lt(Lvv, nV, nV), 0.0, make_tensor(LvvT, false, {nV, nV, nchol}));
     for (int e0 = 0; e0 < nV; e0 += ce) {
@@ -453,7 +503,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
     E.axpy("mfne->menf", -1.0, src, 1.0, dst);
   }
   // packed antisymmetric ladder block for the same-spin T2 blocks
-  E.launch(kElementwise, 0.0, [&] { pack_ladder_antisym(vvvv, vvvv_as, nV, st); });
+  if (!chol) E.launch(kElementwise, 0.0, [&] { pack_ladder_antisym(vvvv, vvvv_as, nV, st); });
 
   // E_N^corr (Eq. 3) from the closed-shell ground-state amplitudes
   c->partial = c->dmalloc(16ull * 2048);
@@ -475,8 +525,12 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   RT_CUDA(cudaMemcpyAsync(&c->eps_core, d_eps + c->core, 8, cudaMemcpyDeviceToHost, st));
   RT_CUDA(cudaStreamSynchronize(st));
   // inputs no longer needed on the device
-  for (void* p : {(void*)d_L, (void*)Loo, (void*)Lov, (void*)Lvv, (void*)d_t1, (void*)d_t2})
+  for (void* p : {(void*)d_L, (void*)Loo, (void*)d_t1, (void*)d_t2})
     if (p) c->dfree(p);
+  if (!chol) {  // the Cholesky mode keeps its slot-space blocks
+    c->dfree(Lov);
+    c->dfree(Lvv);
+  }
 
   // amplitudes T(0) = 0 and the history C_0 = E_0 = 0
   const size_t ab = 16ull * c->g.total();
@@ -517,17 +571,19 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
     // the ladder contractions read only their packed operands once cached:
     // pack them first and free the FP64 ladder blocks (the largest arrays of
     // the context) before the rest of the cache is filled
-    prepack_ladder(E, op, false);
-    RT_CUDA(cudaStreamSynchronize(st));
-    if (E.tc_cached(vvvv)) {
-      c->dfree(vvvv);
-      op.vvvv_released = true;
-    }
-    prepack_ladder(E, op, true);
-    RT_CUDA(cudaStreamSynchronize(st));
-    if (E.tc_cached(vvvv_as)) {
-      c->dfree(vvvv_as);
-      op.vvvv_as_released = true;
+    if (!chol) {
+      prepack_ladder(E, op, false);
+      RT_CUDA(cudaStreamSynchronize(st));
+      if (E.tc_cached(vvvv)) {
+        c->dfree(vvvv);
+        op.vvvv_released = true;
+      }
+      prepack_ladder(E, op, true);
+      RT_CUDA(cudaStreamSynchronize(st));
+      if (E.tc_cached(vvvv_as)) {
+        c->dfree(vvvv_as);
+        op.vvvv_as_released = true;
+      }
     }
     E.tuning = E.autotune;
     compute_residual(E, c->op, c->T_N, c->R_K);
@@ -545,8 +601,9 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
 // cached; out[2]: after set-up with every pack cached.  The phases follow
 // setup(): integrals built while the Cholesky inputs live, then the pack
 // cache filled ladder blocks first, each FP64 ladder block freed after its
-// pack.
-void plan_context_bytes(int O, int V, int nchol, int precision, double out[3]) {
+// pack.  chol: the Cholesky mode (no (ov|vv)/(vv|vv) blocks; the slot-space
+// Cholesky blocks stay).
+void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, double out[3]) {
   const double nO = O, nVd = V + 1.0, nb = O + V;
   const int nV = V + 1;
   const double npv = nVd * (nVd - 1.0) / 2.0;
@@ -565,8 +622,18 @@ void plan_context_bytes(int O, int V, int nchol, int precision, double out[3]) {
   op.ovov = fake(4);
   op.ovvv = fake(5);
   op.ovov_as = fake(6);
-  op.vvvv = fake(7);
-  op.vvvv_as = fake(8);
+  op.vvvv = chol ? nullptr : fake(7);
+  op.vvvv_as = chol ? nullptr : fake(8);
+  if (chol) {
+    op.ovvv = nullptr;
+    op.chol = true;
+    op.nchol = nchol;
+    op.Lov = fake(22);
+    op.Lvv = fake(23);
+    op.LvvT = fake(24);
+    op.LovT = fake(25);
+    cholesky_chunks(O, nV, &op.chunk_a, &op.chunk_m);
+  }
   for (int s = 0; s < 2; ++s) {
     op.foo[s] = fake(10 + s);
     op.fov[s] = fake(12 + s);
@@ -583,22 +650,33 @@ void plan_context_bytes(int O, int V, int nchol, int precision, double out[3]) {
     compute_residual(E, op, fake(31), fake(32));
     return (double)E.arena.peak_bytes();
   };
-  const double setup_need = 8.0 * std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) /
-                                                                       ((int64_t)nV * nV * nV))) *
-                            nVd * nVd * nVd;
+  const double setup_need =
+      chol ? 0.0
+           : 8.0 *
+                 std::max<int64_t>(1, std::min<int64_t>(nV, (int64_t(1) << 28) /
+                                                                ((int64_t)nV * nV * nV))) *
+                 nVd * nVd * nVd;
   const double arena_all = std::max(dry(true), setup_need) + 8192.0;
   double p_ab = 0.0, p_ss = 0.0, p_all = 0.0;
   for (const auto& kv : E.tc_cache_cands) {
     p_all += (double)kv.second.bytes;
-    if (kv.second.tensor == op.vvvv) p_ab += (double)kv.second.bytes;
-    if (kv.second.tensor == op.vvvv_as) p_ss += (double)kv.second.bytes;
+    if (!chol && kv.second.tensor == op.vvvv) p_ab += (double)kv.second.bytes;
+    if (!chol && kv.second.tensor == op.vvvv_as) p_ss += (double)kv.second.bytes;
   }
   const double arena_none = std::max(dry(false), setup_need) + 8192.0;
-  const double f_ab = 8.0 * nVd * nVd * nVd * nVd, f_ss = 8.0 * npv * npv;
-  const double ints = 8.0 * (nO * nO * nO * nO + nO * nO * nO * nVd + 3.0 * nO * nO * nVd * nVd +
-                             nO * nVd * nVd * nVd) +
-                      f_ab + f_ss;
-  const double inputs = 8.0 * (nb + nchol * nb * nb + nchol * (nO * nO + nO * nVd + 2.0 * nVd * nVd));
+  const double f_ab = chol ? 0.0 : 8.0 * nVd * nVd * nVd * nVd,
+               f_ss = chol ? 0.0 : 8.0 * npv * npv;
+  // integral blocks (the Cholesky mode keeps L_ov, L_vv and their transposes
+  // instead of (ov|vv), (vv|vv) and the pair block)
+  const double ints =
+      8.0 * (nO * nO * nO * nO + nO * nO * nO * nVd + 3.0 * nO * nO * nVd * nVd) +
+      (chol ? 8.0 * nchol * (2.0 * nO * nVd + 2.0 * nVd * nVd)
+            : 8.0 * nO * nVd * nVd * nVd + f_ab + f_ss);
+  // inputs on the device during set-up: eps, L, L_oo (and, with resident
+  // blocks, L_ov, L_vv and the transposed L_vv of the chunked ladder build)
+  const double inputs =
+      8.0 * (nb + nchol * nb * nb + nchol * nO * nO) +
+      (chol ? 0.0 : 8.0 * nchol * (nO * nVd + 2.0 * nVd * nVd));
   const double fock = 2.0 * (24.0 * (nO * nO + nO * nVd + nVd * nVd) + 8.0 * (nO + nVd));
   const double amps = 4.0 * 16.0 * (double)g.total() + 2.0 * 16.0 * 1024 + 16.0 * 2048 + 256.0;
   const double phase_a_all = inputs + fock + ints + arena_all;
@@ -742,7 +820,8 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
       precision != RTEOM_SPLIT_BF16)
     return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 "
                               "or RTEOM_FP64_OZAKI");
-  if (flags & ~RTEOM_FLAG_CUMULANT_NO_FOV) return bad(RTEOM_ERR_ARG, "unknown flag bits");
+  if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY))
+    return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)
     return bad(RTEOM_ERR_ARG, "nvir too large: (nvir+1)^2 pair indices must fit 32 bits");
@@ -918,14 +997,16 @@ int rteom_set_state(rteom_ctx* c, const double* t_in, long long steps, const dou
   });
 }
 
-int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, double* bytes) {
+int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, double* bytes) {
   if (!bytes || nocc < 1 || nvir < 1 || nchol < 0 ||
+      (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY)) ||
       (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
        precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16) ||
       (double)(nvir + 1) * (nvir + 1) > 2.0e9)
     return RTEOM_ERR_ARG;
   try {
-    plan_context_bytes(nocc, nvir, nchol, precision, bytes);
+    plan_context_bytes(nocc, nvir, nchol, precision,
+                       (flags & RTEOM_FLAG_LADDER_CHOLESKY) && nchol > 0, bytes);
   } catch (const std::exception&) {
     return RTEOM_ERR_ARG;
   }

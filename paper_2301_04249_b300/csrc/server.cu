@@ -61,7 +61,7 @@ struct Request {
 // returns to zero when the last request leaves.
 double estimate_bytes(int O, int V, int nchol, int precision) {
   double b[3] = {0.0, 0.0, 0.0};
-  if (rteom_plan_bytes(O, V, nchol, precision, b) != RTEOM_OK) return 0.0;
+  if (rteom_plan_bytes(O, V, nchol, precision, 0, b) != RTEOM_OK) return 0.0;
   return std::ceil(1.05 * b[0]) + 256.0 * 1024 * 1024;
 }
 

@@ -226,6 +226,83 @@ __global__ void pack_ladder_kernel(const double* __restrict__ W, double* __restr
   }
 }
 
+// Column chunks of the pair ladder: the pairs (a<b) with a in [a0, a0+n) are
+// the contiguous pair indices [pair_start(a0), pair_start(a0+n)).  The largest
+// a of the chunk whose first pair index is <= k, by bisection.
+__device__ __forceinline__ void pair_in_chunk(int64_t k, int nV, int a0, int n, int& a, int& b) {
+  int lo = a0, hi = a0 + n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pair_start(nV, mid) <= k)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  a = lo;
+  b = a + 1 + (int)(k - pair_start(nV, a));
+}
+
+// Wm[(e<f)][c] = Wc[e][f][a-a0][b] - Wc[f][e][a-a0][b] for the pair columns c
+// of the chunk; Wc holds (ae|bf) for a in the chunk: [e][f][n][b] (real).
+__global__ void pack_ladder_cols_kernel(const double* __restrict__ Wc, double* __restrict__ Wm,
+                                        int nV, int a0, int n, int64_t p0, int64_t ncols) {
+  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  for (int64_t r = blockIdx.x; r < npv; r += gridDim.x) {
+    int e, f;
+    pair_of(r, nV, e, f);
+    const double* we = Wc + ((int64_t)e * nV + f) * n * nV;
+    const double* wf = Wc + ((int64_t)f * nV + e) * n * nV;
+    for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) {
+      int a, b;
+      pair_in_chunk(p0 + c, nV, a0, n, a, b);
+      const int64_t o = (int64_t)(a - a0) * nV + b;
+      Wm[r * ncols + c] = we[o] - wf[o];
+    }
+  }
+}
+
+// R[i,j,a,b] += alpha*Rq[P][c], with the three antisymmetric images, for the
+// pair columns c of the chunk (complex).
+__global__ void unpack_pairs_cols_kernel(const double2* __restrict__ Rq, double2* R, int nO,
+                                         int nV, int a0, int n, int64_t p0, int64_t ncols,
+                                         double alpha) {
+  const int64_t npo = (int64_t)nO * (nO - 1) / 2;
+  for (int64_t r = blockIdx.x; r < npo; r += gridDim.x) {
+    int i, j;
+    pair_of(r, nO, i, j);
+    for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) {
+      int a, b;
+      pair_in_chunk(p0 + c, nV, a0, n, a, b);
+      double2 v = Rq[r * ncols + c];
+      v.x *= alpha;
+      v.y *= alpha;
+      auto at = [&](int p, int q, int u, int w) -> double2& {
+        return R[(((int64_t)p * nO + q) * nV + u) * nV + w];
+      };
+      double2& r0 = at(i, j, a, b);
+      r0.x += v.x;
+      r0.y += v.y;
+      double2& r1 = at(j, i, a, b);
+      r1.x -= v.x;
+      r1.y -= v.y;
+      double2& r2 = at(i, j, b, a);
+      r2.x -= v.x;
+      r2.y -= v.y;
+      double2& r3 = at(j, i, b, a);
+      r3.x += v.x;
+      r3.y += v.y;
+    }
+  }
+}
+
+// dst[r*ldd + c] += src[r*lds + c]
+__global__ void add_block_kernel(double* __restrict__ dst, int64_t ldd,
+                                 const double* __restrict__ src, int64_t lds, int64_t rows,
+                                 int64_t cols) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) dst[r * ldd + c] += src[r * lds + c];
+}
+
 // ---------------------------------------------------------------- amplitude geometry
 struct Elem {
   int blk, i, j, a, b;
@@ -682,6 +759,34 @@ void pack_ladder_antisym(const double* W, double* Wm, int nV, cudaStream_t st) {
   int64_t npv = (int64_t)nV * (nV - 1) / 2;
   if (npv == 0) return;
   pack_ladder_kernel<<<grid_for(npv * npv, 16), kThreads, 0, st>>>(W, Wm, nV);
+  RT_CHECK_LAUNCH();
+}
+
+void pack_ladder_cols(const double* Wc, double* Wm, int nV, int a0, int n, cudaStream_t st) {
+  const int64_t npv = (int64_t)nV * (nV - 1) / 2;
+  const int64_t p0 = pair_start(nV, a0), ncols = pair_start(nV, a0 + n) - p0;
+  if (npv == 0 || ncols == 0) return;
+  pack_ladder_cols_kernel<<<(int)std::min<int64_t>(npv, 148 * 16), kThreads, 0, st>>>(
+      Wc, Wm, nV, a0, n, p0, ncols);
+  RT_CHECK_LAUNCH();
+}
+
+void unpack_pairs_cols(const double* Rq, double* R, int nO, int nV, int a0, int n, double alpha,
+                       cudaStream_t st) {
+  const int64_t npo = (int64_t)nO * (nO - 1) / 2;
+  const int64_t p0 = pair_start(nV, a0), ncols = pair_start(nV, a0 + n) - p0;
+  if (npo == 0 || ncols == 0) return;
+  unpack_pairs_cols_kernel<<<(int)std::min<int64_t>(npo, 148 * 16), kThreads, 0, st>>>(
+      reinterpret_cast<const double2*>(Rq), reinterpret_cast<double2*>(R), nO, nV, a0, n, p0,
+      ncols, alpha);
+  RT_CHECK_LAUNCH();
+}
+
+void add_block(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return;
+  add_block_kernel<<<(int)std::min<int64_t>(rows, 148 * 16), kThreads, 0, st>>>(dst, ldd, src,
+                                                                                 lds, rows, cols);
   RT_CHECK_LAUNCH();
 }
 

@@ -1,12 +1,17 @@
 """Evaluate CCSD residuals of a named workload eagerly, for profilers.
 
   python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde] [--residuals 2]
-         [--precision fp64|split_tf32|split_bf16|fp64_ozaki]
+         [--precision fp64|split_tf32|split_bf16|fp64_ozaki] [--cholesky] [--steps N]
 
 Each evaluation launches every kernel of one residual on the library's
 stream outside CUDA graphs, with the particle-particle ladder GEMMs inside
 the NVTX range "rteom_ladder" (select them with
 `ncu --nvtx --nvtx-include "rteom_ladder/"`).  Prints the per-class timing.
+With --steps N it propagates N Adams-Moulton steps from T(0) = 0 instead
+(no host amplitude arrays) and prints the set-up time, the device memory
+the context took and the time per step.  --cholesky asks for the Cholesky
+mode (RTEOM_FLAG_LADDER_CHOLESKY); rteom_create also takes it by itself
+when the resident blocks do not fit.
 """
 from __future__ import annotations
 
@@ -14,6 +19,7 @@ import argparse
 import json
 import os
 import sys
+import time
 
 import numpy as np
 
@@ -29,12 +35,33 @@ def main():
     ap.add_argument("--residuals", type=int, default=2)
     ap.add_argument("--precision", choices=["fp64", "split_tf32", "split_bf16", "fp64_ozaki"],
                     default="fp64")
+    ap.add_argument("--cholesky", action="store_true")
+    ap.add_argument("--steps", type=int, default=0)
     a = ap.parse_args()
-    p, _ = workload(a.workload)
+    p, run = workload(a.workload)
     rng = np.random.default_rng(0)
     prec = {"fp64": P.RTEOM_FP64, "split_tf32": P.RTEOM_SPLIT_TF32,
             "split_bf16": P.RTEOM_SPLIT_BF16, "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
-    with P.Propagator.from_problem(p, precision=prec) as g:
+    flags = P.RTEOM_FLAG_LADDER_CHOLESKY if a.cholesky else 0
+    if a.steps > 0:
+        import torch
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        with P.Propagator.from_problem(p, precision=prec, flags=flags) as g:
+            setup_s = time.perf_counter() - t0
+            held = free0 - torch.cuda.mem_get_info()[0]
+            g.set_timing(True)
+            t0 = time.perf_counter()
+            g.propagate(a.steps, run["dt"], tol=1e-4)
+            wall = time.perf_counter() - t0
+            info = g.info()
+            print(json.dumps(dict(workload=a.workload, precision=a.precision,
+                                  setup_s=setup_s, device_bytes_held=held,
+                                  steps=a.steps, s_per_step=wall / a.steps,
+                                  micro_per_step=info["micro"] / a.steps,
+                                  timing=g.timing())))
+        return
+    with P.Propagator.from_problem(p, precision=prec, flags=flags) as g:
         shapes = P.block_shapes(p.nocc, p.nvir)
         t = [0.01 * (rng.standard_normal(s) + 1j * rng.standard_normal(s)) for s in shapes]
         for k in (2, 4):

@@ -53,3 +53,39 @@ def test_server_estimate_follows_the_plan():
     b = P.plan_bytes(8, 60, 240, P.RTEOM_SPLIT_TF32)["peak"]
     est = P.Server.estimate_bytes(8, 60, 240, P.RTEOM_SPLIT_TF32)
     assert b < est <= 1.05 * b + 512 * 2 ** 20
+
+
+def _chol_floor_bytes(O, V, nchol):
+    """Cholesky mode: integral blocks without (ov|vv), (vv|vv) and the pair
+    block, plus the slot-space L_ov, L_vv and their transposes."""
+    nO, nV = O, V + 1
+    ints = nO ** 4 + nO ** 3 * nV + 3 * nO ** 2 * nV ** 2 + 2 * nchol * (nO * nV + nV ** 2)
+    amps = 2 * nO * nV + 3 * nO ** 2 * nV ** 2
+    return 8.0 * ints + 4 * 16.0 * amps
+
+
+@pytest.mark.parametrize("O,V,nchol", [(4, 20, 60), (8, 100, 400), (30, 300, 1200)])
+@pytest.mark.parametrize("precision", FORMS)
+def test_cholesky_mode_plan_covers_its_buffers_and_is_smaller(O, V, nchol, precision):
+    F = P.RTEOM_FLAG_LADDER_CHOLESKY
+    b = P.plan_bytes(O, V, nchol, precision, F)
+    floor = _chol_floor_bytes(O, V, nchol)
+    assert b["peak"] >= floor and b["peak_uncached"] >= floor
+    if V >= 100:  # below that the chunk scratch outweighs the blocks it replaces
+        assert b["peak_uncached"] < P.plan_bytes(O, V, nchol, precision)["peak_uncached"]
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_config5_fits_one_b300_only_in_cholesky_mode(precision):
+    """O=50, V=450, Nchol=1800: the resident (vv|vv) block alone is 331 GB;
+    the Cholesky mode fits the 288 GB device (packs left uncached where the
+    cache would not fit)."""
+    dev = 275040 * 2 ** 20
+    assert P.plan_bytes(50, 450, 1800, precision)["peak_uncached"] > dev
+    chol = P.plan_bytes(50, 450, 1800, precision, P.RTEOM_FLAG_LADDER_CHOLESKY)
+    assert chol["peak_uncached"] < 0.9 * dev
+
+
+def test_plan_rejects_unknown_flags():
+    with pytest.raises(P.RteomError):
+        P.plan_bytes(4, 10, 5, P.RTEOM_FP64, 1 << 7)

@@ -37,6 +37,7 @@ struct GemmArgs {
   double* C;
   int64_t ldc, sC;
   double alpha, beta;
+  int ntn;  // column tiles: blockIdx.x = row tile * ntn + column tile
 };
 
 template <bool CP>
@@ -102,8 +103,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   double* C = g.C + (CC ? 2 : 1) * g.sC * blockIdx.z;
   const int kbeg = sp * g.kslice;
   const int kend = min(g.K, kbeg + g.kslice);
-  const int m0 = blockIdx.y * BM;
-  const int n0 = blockIdx.x * BN;
+  const int m0 = (int)(blockIdx.x / g.ntn) * BM;
+  const int n0 = (int)(blockIdx.x % g.ntn) * BN;
   const int tx = threadIdx.x % RN, ty = threadIdx.x / RN;
 
   double acc_r[TM][TN], acc_i[TM][TN], acc_s[M3 ? TM : 1][M3 ? TN : 1];
@@ -280,7 +281,7 @@ Tile tile_of(const GemmDesc& d) {
 
 template <bool AC, bool BC>
 void launch_typed(const GemmArgs& g, Tile t, int batch, int splits, cudaStream_t st) {
-  dim3 grid((g.N + t.bn - 1) / t.bn, (g.M + t.bm - 1) / t.bm, batch * splits);
+  dim3 grid(g.ntn * ((g.M + t.bm - 1) / t.bm), 1, batch * splits);
   if (t.bm == 64 && t.bn == 64)
     gemm_kernel<AC, BC, 64, 64, 4, 4><<<grid, 256, 0, st>>>(g);
   else if (t.bm == 32 && t.bn == 64)
@@ -475,12 +476,14 @@ void gemm_f64(const GemmDesc& d, cudaStream_t st) {
   }
   const int splits = gemm_f64_splits(d);
   if (splits > 1 && d.work == nullptr) throw Error(-1, "gemm_f64: split-K needs a workspace");
-  if ((d.M + tile_of(d).bm - 1) / tile_of(d).bm > 65535)
-    throw Error(-1, "gemm_f64: too many row tiles for the grid");
+  if ((int64_t)((d.N + tile_of(d).bn - 1) / tile_of(d).bn) *
+          ((d.M + tile_of(d).bm - 1) / tile_of(d).bm) > 0x7fffffff)
+    throw Error(-1, "gemm_f64: too many tiles for the grid");
   GemmArgs g;
   g.M = d.M;
   g.N = d.N;
   g.K = d.K;
+  g.ntn = (d.N + tile_of(d).bn - 1) / tile_of(d).bn;
   g.kslice = splits > 1 ? (d.K + splits - 1) / splits : std::max(d.K, 1);
   g.splits = splits;
   g.A = d.A;

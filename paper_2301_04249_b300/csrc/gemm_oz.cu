@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
   int* issued = abort_flag + 1;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y, z = blockIdx.z;
+  // output tiles on one grid axis (row tiles exceed 65535 for long M)
+  const int n_tiles = g.Np / BN;
+  const int n_tile = (int)(blockIdx.x % n_tiles), m_tile = (int)(blockIdx.x / n_tiles);
+  const int z = blockIdx.z;
   const int b = z / g.ranges, rg = z % g.ranges;
   const int kt0 = rg * g.kpr;
   const int kt1 = min(g.KT, kt0 + g.kpr);
@@ -705,7 +708,8 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
                  const int* eb, float2* P, int* err, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d, S);
-  if (p.Mp / oz::BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
+  if ((int64_t)(p.Np / p.bn) * (p.Mp / oz::BM) > 0x7fffffff ||
+      (int64_t)d.batch * p.ranges > 65535)
     throw Error(-1, "gemm_oz: grid too large");
   oz::KArgs g{};
   g.A = reinterpret_cast<const __nv_bfloat16*>(A);
@@ -733,7 +737,7 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid(p.Np / p.bn, p.Mp / oz::BM, d.batch * p.ranges);
+  dim3 grid((p.Np / p.bn) * (p.Mp / oz::BM), 1, d.batch * p.ranges);
   using namespace oz;
   if (S == 3 && p.bn == 64)
     oz_gemm_kernel<3, 64><<<grid, THREADS, Cfg<3, 64>::SMEM, st>>>(g);

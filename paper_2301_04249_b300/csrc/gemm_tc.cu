@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
   int* issued = abort_flag + 1;  // bulk-load stages issued by the producer
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
+  // output tiles on one grid axis (row tiles exceed 65535 for long M)
+  const int n_tiles = g.Np / BN;
+  const int n_tile = (int)(blockIdx.x % n_tiles), m_tile = (int)(blockIdx.x / n_tiles);
   const int z = blockIdx.z;
   const int b = z / g.ranges, rg = z % g.ranges;
   const int kt0 = rg * g.kpr;
@@ -547,7 +549,7 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   using namespace tc;
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const Plan p = plan(d);
-  if (p.Mp / BM > 65535 || (int64_t)d.batch * p.ranges > 65535)
+  if ((int64_t)(p.Np / kBN) * (p.Mp / BM) > 0x7fffffff || (int64_t)d.batch * p.ranges > 65535)
     throw Error(-1, "gemm_tc: grid too large");
   KArgs g{};
   g.Ahi = Ahi;
@@ -575,7 +577,7 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid(p.Np / kBN, p.Mp / BM, d.batch * p.ranges);
+  dim3 grid((p.Np / kBN) * (p.Mp / BM), 1, d.batch * p.ranges);
   tc_gemm_kernel<kBN, kStages><<<grid, THREADS, kSmemBytes, st>>>(g);
   RT_CHECK_LAUNCH();
 }

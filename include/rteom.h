@@ -285,6 +285,23 @@ int rteom_server_submit(rteom_server* s, int nocc, int nvir, int nchol, const do
                         int max_micro, long long* request_id);
 
 /*
+ * rteom_server_submit_sweep -- queue one propagation per core hole c in
+ * cores[] of the same molecule (Section 3: the core-hole calculations of one
+ * system are independent and can run at the same time).  The host inputs
+ * are copied once and shared by the requests until each has built its
+ * context; every request builds its own (N-1) Fock matrix and integral
+ * blocks on the device, since both depend on c.
+ *  cores        host int[ncores], each 0 <= c < nocc; ncores >= 1
+ *  request_ids  host long long[ncores]: the ids, in the order of cores
+ * The other arguments are those of rteom_server_submit.  A bad argument
+ * returns RTEOM_ERR_ARG and queues nothing.
+ */
+int rteom_server_submit_sweep(rteom_server* s, int nocc, int nvir, int nchol, const double* eps,
+                              const double* L, const double* t1_gs, const double* t2_gs,
+                              const int* cores, int ncores, int flags, int nsteps, double dt,
+                              double tol, int max_micro, long long* request_ids);
+
+/*
  * rteom_server_poll -- state of a request.  status: RTEOM_REQ_*; error: the
  * RTEOM_ERR_* code of a failed request; C_out (host, 2*(nsteps+1) doubles or
  * NULL) receives C_0..C_nsteps once the request is DONE; times (host [3] or

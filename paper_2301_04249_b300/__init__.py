@@ -226,6 +226,26 @@ class Server:
         self._nsteps[rid.value] = int(nsteps)
         return rid.value
 
+    def submit_sweep(self, p, cores, nsteps: int, dt: float, tol: float = 1e-4,
+                     max_micro: int = 50, flags: int = 0) -> list:
+        """Queue one propagation per core hole in ``cores`` of the molecule p
+        (host inputs copied once and shared); returns the ids in order."""
+        eps, L = _f64(p.eps), _f64(p.L)
+        t1, t2 = _f64(p.t1_gs), _f64(p.t2_gs)
+        nchol = 0 if L is None else int(L.shape[0])
+        cs = np.ascontiguousarray(cores, dtype=np.int32)
+        ids = np.zeros(cs.size, dtype=np.int64)
+        rc = self._lib.rteom_server_submit_sweep(
+            self._h, int(p.nocc), int(p.nvir), nchol, _ptr(eps), _ptr(L), _ptr(t1), _ptr(t2),
+            cs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(cs.size), int(flags),
+            int(nsteps), float(dt), float(tol), int(max_micro),
+            ids.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+        if rc != 0:
+            raise RteomError(rc, "rteom_server_submit_sweep failed")
+        for rid in ids:
+            self._nsteps[int(rid)] = int(nsteps)
+        return [int(r) for r in ids]
+
     def poll(self, rid: int):
         """(status, error, C or None, (t_submit, t_admit, t_done))."""
         st, er = ctypes.c_int(), ctypes.c_int()

@@ -51,6 +51,11 @@ SIGNATURES = {
     "rteom_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                            _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, _llp]),
+    "rteom_server_submit_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 _dp, _dp, _dp, _dp,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, _llp]),
     "rteom_server_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), _dp, _dp]),
     "rteom_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_double]),

@@ -37,11 +37,17 @@ double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
 }
 
+// Host copies of one molecule's inputs, shared by the requests of a sweep
+// over core holes and dropped once the last of them has built its context.
+struct Inputs {
+  std::vector<double> eps, L, t1, t2;
+  bool has_t1 = false, has_t2 = false;
+};
+
 struct Request {
   long long id = 0;
   int O = 0, V = 0, nchol = 0, core = 0, flags = 0;
-  std::vector<double> eps, L, t1, t2;
-  bool has_t1 = false, has_t2 = false;
+  std::shared_ptr<const Inputs> in;
   int nsteps = 0, max_micro = 1;
   double dt = 0.0, tol = 0.0;
   int status = RTEOM_REQ_QUEUED;
@@ -110,14 +116,7 @@ struct rteom_server {
     } else if (status == RTEOM_REQ_FAILED) {
       ++n_failed;
     }
-    r->eps.clear();
-    r->L.clear();
-    r->t1.clear();
-    r->t2.clear();
-    r->eps.shrink_to_fit();
-    r->L.shrink_to_fit();
-    r->t1.shrink_to_fit();
-    r->t2.shrink_to_fit();
+    r->in.reset();  // a cancelled or failed request may still hold its inputs
     cv_done.notify_all();
   }
 
@@ -153,10 +152,12 @@ struct rteom_server {
         }
       }
       for (Request* r : admitting) {
-        int rc = rteom_create(&r->ctx, r->O, r->V, r->nchol, r->eps.data(),
-                              r->nchol ? r->L.data() : nullptr, r->has_t1 ? r->t1.data() : nullptr,
-                              r->has_t2 ? r->t2.data() : nullptr, r->core, precision, r->flags,
+        const Inputs& in = *r->in;
+        int rc = rteom_create(&r->ctx, r->O, r->V, r->nchol, in.eps.data(),
+                              r->nchol ? in.L.data() : nullptr, in.has_t1 ? in.t1.data() : nullptr,
+                              in.has_t2 ? in.t2.data() : nullptr, r->core, precision, r->flags,
                               nullptr);
+        r->in.reset();  // the context holds its own device copies now
         if (rc != RTEOM_OK) {
           finish(r, RTEOM_REQ_FAILED, rc, rteom_last_error(nullptr));
           continue;
@@ -224,6 +225,67 @@ struct rteom_server {
   }
 };
 
+namespace {
+
+std::shared_ptr<const Inputs> copy_inputs(int nocc, int nvir, int nchol, const double* eps,
+                                          const double* L, const double* t1_gs,
+                                          const double* t2_gs) {
+  auto in = std::make_shared<Inputs>();
+  const size_t nb = (size_t)nocc + nvir;
+  in->eps.assign(eps, eps + nb);
+  if (nchol) in->L.assign(L, L + (size_t)nchol * nb * nb);
+  if (t1_gs) {
+    in->t1.assign(t1_gs, t1_gs + (size_t)nocc * nvir);
+    in->has_t1 = true;
+  }
+  if (t2_gs) {
+    in->t2.assign(t2_gs, t2_gs + (size_t)nocc * nocc * nvir * nvir);
+    in->has_t2 = true;
+  }
+  return in;
+}
+
+bool bad_request(const rteom_server* s, int nocc, int nvir, int nchol, const double* eps,
+                 const double* L, int nsteps, double dt, double tol, int max_micro) {
+  return !s || !eps || nocc < 1 || nvir < 1 || nchol < 0 || (nchol > 0 && !L) || nsteps < 0 ||
+         !(dt > 0) || !(tol > 0) || max_micro < 1;
+}
+
+// Queue requests for the given core holes, all sharing one input copy.
+void enqueue(rteom_server* s, int nocc, int nvir, int nchol, std::shared_ptr<const Inputs> in,
+             const int* cores, int ncores, int flags, int nsteps, double dt, double tol,
+             int max_micro, long long* ids) {
+  const double est = estimate_bytes(nocc, nvir, nchol, s->precision);
+  std::vector<std::unique_ptr<Request>> rs;
+  for (int k = 0; k < ncores; ++k) {
+    std::unique_ptr<Request> r(new Request());
+    r->O = nocc;
+    r->V = nvir;
+    r->nchol = nchol;
+    r->core = cores[k];
+    r->flags = flags;
+    r->in = in;
+    r->nsteps = nsteps;
+    r->dt = dt;
+    r->tol = tol;
+    r->max_micro = max_micro;
+    r->estimate = est;
+    rs.push_back(std::move(r));
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (int k = 0; k < ncores; ++k) {
+    Request* r = rs[k].get();
+    r->id = s->next_id++;
+    r->t_submit = seconds_since(s->t0);
+    ids[k] = r->id;
+    s->queue.push_back(r);
+    s->all[r->id] = std::move(rs[k]);
+  }
+  s->cv_work.notify_all();
+}
+
+}  // namespace
+
 extern "C" {
 
 int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_active,
@@ -254,38 +316,24 @@ int rteom_server_submit(rteom_server* s, int nocc, int nvir, int nchol, const do
                         const double* L, const double* t1_gs, const double* t2_gs, int core_index,
                         int flags, int nsteps, double dt, double tol, int max_micro,
                         long long* request_id) {
-  if (!s || !request_id || !eps || nocc < 1 || nvir < 1 || nchol < 0 || (nchol > 0 && !L) ||
-      nsteps < 0 || !(dt > 0) || !(tol > 0) || max_micro < 1)
+  if (!request_id || bad_request(s, nocc, nvir, nchol, eps, L, nsteps, dt, tol, max_micro))
     return RTEOM_ERR_ARG;
-  std::unique_ptr<Request> r(new Request());
-  const size_t nb = (size_t)nocc + nvir;
-  r->O = nocc;
-  r->V = nvir;
-  r->nchol = nchol;
-  r->core = core_index;
-  r->flags = flags;
-  r->eps.assign(eps, eps + nb);
-  if (nchol) r->L.assign(L, L + (size_t)nchol * nb * nb);
-  if (t1_gs) {
-    r->t1.assign(t1_gs, t1_gs + (size_t)nocc * nvir);
-    r->has_t1 = true;
-  }
-  if (t2_gs) {
-    r->t2.assign(t2_gs, t2_gs + (size_t)nocc * nocc * nvir * nvir);
-    r->has_t2 = true;
-  }
-  r->nsteps = nsteps;
-  r->dt = dt;
-  r->tol = tol;
-  r->max_micro = max_micro;
-  r->estimate = estimate_bytes(nocc, nvir, nchol, s->precision);
-  std::lock_guard<std::mutex> lock(s->mu);
-  r->id = s->next_id++;
-  r->t_submit = seconds_since(s->t0);
-  *request_id = r->id;
-  s->queue.push_back(r.get());
-  s->all[r->id] = std::move(r);
-  s->cv_work.notify_all();
+  enqueue(s, nocc, nvir, nchol, copy_inputs(nocc, nvir, nchol, eps, L, t1_gs, t2_gs),
+          &core_index, 1, flags, nsteps, dt, tol, max_micro, request_id);
+  return RTEOM_OK;
+}
+
+int rteom_server_submit_sweep(rteom_server* s, int nocc, int nvir, int nchol, const double* eps,
+                              const double* L, const double* t1_gs, const double* t2_gs,
+                              const int* cores, int ncores, int flags, int nsteps, double dt,
+                              double tol, int max_micro, long long* request_ids) {
+  if (!request_ids || !cores || ncores < 1 ||
+      bad_request(s, nocc, nvir, nchol, eps, L, nsteps, dt, tol, max_micro))
+    return RTEOM_ERR_ARG;
+  for (int k = 0; k < ncores; ++k)
+    if (cores[k] < 0 || cores[k] >= nocc) return RTEOM_ERR_ARG;
+  enqueue(s, nocc, nvir, nchol, copy_inputs(nocc, nvir, nchol, eps, L, t1_gs, t2_gs), cores,
+          ncores, flags, nsteps, dt, tol, max_micro, request_ids);
   return RTEOM_OK;
 }
 

@@ -99,3 +99,37 @@ def test_cancel_running_request():
         assert s.wait(rid, 60.0)
         status, _, C, _ = s.poll(rid)
     assert status == P.RTEOM_REQ_CANCELLED and C is None
+
+
+def test_core_hole_sweep_matches_lone_propagations():
+    """One molecule, several core holes (Section 3: independent, run at the
+    same time) through one shared input copy: each result equals the lone
+    propagation of that core hole, bitwise."""
+    p = gen_problem(4, 16, 24, 31)
+    cores = [0, 1, 3]
+    alone = []
+    for c in cores:
+        with P.Propagator(p.eps, p.L, p.nocc, p.nvir, p.t1_gs, p.t2_gs, core=c) as g:
+            alone.append(g.propagate(20, DT, tol=1e-8))
+    with P.Server(max_active=4) as s:
+        ids = s.submit_sweep(p, cores, 20, DT, tol=1e-8)
+        for rid in ids:
+            assert s.wait(rid, 300.0)
+        res = [s.poll(rid) for rid in ids]
+        st = s.stats()
+    for (status, err, C, _), ref in zip(res, alone):
+        assert status == P.RTEOM_REQ_DONE, err
+        assert np.array_equal(C, ref)
+    assert not np.array_equal(res[0][2], res[1][2])  # the core holes differ
+    assert st["done"] == len(cores) and st["failed"] == 0 and st["mem_in_use"] == 0
+
+
+def test_sweep_with_a_core_outside_the_occupied_space_queues_nothing():
+    p = gen_problem(4, 10, 12, 32)
+    with P.Server(max_active=1) as s:
+        with pytest.raises(P.RteomError):
+            s.submit_sweep(p, [0, 4], 5, DT)
+        with pytest.raises(P.RteomError):
+            s.submit_sweep(p, [], 5, DT)
+        st = s.stats()
+    assert st["queued"] == 0 and st["running"] == 0 and st["done"] == 0

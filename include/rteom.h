@@ -234,7 +234,11 @@ int rteom_debug_residual(rteom_ctx* ctx, const double* t_in, double* R_out, doub
  * zeroes the counters after reading.  Inside the captured residual graphs only the
  * ladder launches carry event nodes, so ms[] of the other classes counts
  * only eagerly launched work (set-up, rteom_debug_residual); launches[] and
- * flops[] count every launch.
+ * flops[] count every launch.  on = 2 runs the residuals of rteom_propagate
+ * eagerly (no graphs, the same kernels) with an event pair around every
+ * launch, so every class is timed; with the environment variable
+ * RTEOM_TRACE=<file> each timed launch also appends one JSON line (class,
+ * contraction, FLOPs, ms) to that file.
  */
 int rteom_set_timing(rteom_ctx* ctx, int on);
 int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* flops,

@@ -161,8 +161,11 @@ class Propagator:
         self._check(self._lib.rteom_debug_residual(self._ctx, _ptr(t), _ptr(R), _ptr(E)))
         return split_blocks(R, self.nocc, self.nvir), complex(E[0], E[1])
 
-    def set_timing(self, on: bool):
-        self._check(self._lib.rteom_set_timing(self._ctx, int(bool(on))))
+    def set_timing(self, on):
+        """0/False off, 1/True on, 2 on with the residuals run outside graphs
+        (every launch timed)."""
+        on = 2 if on == 2 else int(bool(on))
+        self._check(self._lib.rteom_set_timing(self._ctx, on))
 
     def timing(self, reset: bool = False):
         ms = (ctypes.c_double * 4)()

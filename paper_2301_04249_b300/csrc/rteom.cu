@@ -52,6 +52,7 @@ struct rteom_ctx {
   long long graph_kernels = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
   bool tune_first = false;  // run the next residual eagerly for the autotuner
+  bool eager_timing = false;  // rteom_set_timing(ctx, 2): residuals outside graphs
   long long cache_plan_bytes = 0;  // tensor-core pack cache planned at set-up
   bool graph_timed[2] = {false, false};            // captured with event-record nodes
   std::vector<Engine::GraphPair> graph_pairs[2];
@@ -184,7 +185,7 @@ void collect_graph_timing(rteom_ctx* c) {
 void run_residual(rteom_ctx* c, int which) {
   const double* t = which == 0 ? c->T_N : c->T_K;
   double* R = which == 0 ? c->R_N : c->R_K;
-  if (c->E.timing && !c->E.graph_timing_ok) {  // eager, every kernel bracketed by events
+  if (c->E.timing && (!c->E.graph_timing_ok || c->eager_timing)) {  // eager, every kernel timed
     compute_residual(c->E, c->op, t, R);
     return;
   }
@@ -1044,6 +1045,7 @@ int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double
 int rteom_set_timing(rteom_ctx* c, int on) {
   if (!c) return RTEOM_ERR_ARG;
   c->E.timing = on != 0;
+  c->eager_timing = on == 2;
   return RTEOM_OK;
 }
 

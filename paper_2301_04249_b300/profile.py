@@ -37,6 +37,8 @@ def main():
                     default="fp64")
     ap.add_argument("--cholesky", action="store_true")
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--eager-timing", action="store_true",
+                    help="with --steps: residuals outside graphs, every launch timed")
     a = ap.parse_args()
     p, run = workload(a.workload)
     rng = np.random.default_rng(0)
@@ -50,7 +52,7 @@ def main():
         with P.Propagator.from_problem(p, precision=prec, flags=flags) as g:
             setup_s = time.perf_counter() - t0
             held = free0 - torch.cuda.mem_get_info()[0]
-            g.set_timing(True)
+            g.set_timing(2 if a.eager_timing else 1)
             t0 = time.perf_counter()
             g.propagate(a.steps, run["dt"], tol=1e-4)
             wall = time.perf_counter() - t0

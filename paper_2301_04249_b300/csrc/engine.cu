@@ -558,6 +558,59 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     auto it = tc_cache_.find(key(roleB, B));
     if (it != tc_cache_.end()) cB = &it->second;
   }
+  // held operands: a pack made earlier in the chunk loop, or room for one
+  // below this call's scratch.  A pack depends on its own tensor's extents
+  // and K only, so the key leaves out the other operand's extent (chunks of
+  // different widths share it).
+  auto hkey = [&](const char* role, const Tensor& T, bool is_a) {
+    return std::string(role) + "|" + spec + "|" + std::to_string((uintptr_t)T.p) + "|" +
+           std::to_string(is_a ? Mt : Nt) + "," + std::to_string(Kt) + "," + std::to_string(Bt);
+  };
+  bool holdA = false, holdB = false;
+  if (packed_path) {
+    if (!cA && !A.constant && held_.count(A.p)) {
+      auto it = held_packs_.find(hkey(roleA, A, true));
+      if (it != held_packs_.end())
+        cA = &it->second;
+      else
+        holdA = true;
+    }
+    if (!cB && !B.constant && held_.count(B.p)) {
+      auto it = held_packs_.find(hkey(roleB, B, false));
+      if (it != held_packs_.end())
+        cB = &it->second;
+      else
+        holdB = true;
+    }
+  }
+  Packed heldA, heldB;
+  if (holdA || holdB) {  // nothing of this call is in the arena yet
+    int64_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;  // bytes of the A-role and B-role packs
+    if (use_tc) {
+      const TcLayout L = gemm_tc_layout(g);
+      a0 = a1 = 4 * L.a_elems;
+      b0 = b1 = 4 * L.b_elems;
+    } else {
+      const OzLayout L = gemm_oz_layout(swap ? swapped(g) : g, oz_planes);
+      a0 = 2 * L.planes * L.a_elems;
+      a1 = 4 * L.a_rows;
+      b0 = 2 * L.planes * L.b_elems;
+      b1 = 4 * L.b_rows;
+      if (swap) {  // the tensor A is packed in the B role of the transposed GEMM
+        std::swap(a0, b0);
+        std::swap(a1, b1);
+      }
+    }
+    if (holdA) {
+      heldA.p0 = arena.alloc((a0 + 7) / 8);
+      heldA.p1 = arena.alloc((a1 + 7) / 8);
+    }
+    if (holdB) {
+      heldB.p0 = arena.alloc((b0 + 7) / 8);
+      heldB.p1 = arena.alloc((b1 + 7) / 8);
+    }
+    mark = arena.mark();  // the held packs outlive this call
+  }
 
   if (!dry && ((A.released && !cA) || (B.released && !cB)))
     throw Error(-3, std::string("contract: freed operand without a cached pack in ") + spec);
@@ -589,10 +642,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     arena.release(mark);
     return;
   }
-  const Tensor Ause = (bPA && !cA && !fusedA && !(pack_only && !A.constant))
+  const Tensor Ause = (bPA && !cA && !fusedA && !(pack_only && !A.constant && !holdA))
                           ? permuted(A, p.a, batch + bM + bK)
                           : A;
-  const Tensor Buse = (bPB && !cB && !fusedB && !(pack_only && !B.constant))
+  const Tensor Buse = (bPB && !cB && !fusedB && !(pack_only && !B.constant && !holdB))
                           ? permuted(B, p.b, batch + bK + bN)
                           : B;
   Tensor Cuse = C;
@@ -641,7 +694,9 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                      int64_t bytes1, bool is_a, const GemmDesc& gd) -> Packed {
     if (cached) return *cached;
     Packed pk;
-    const std::string ck = T.constant ? key(role, T) : std::string();
+    const bool held = (&T == &A && holdA) || (&T == &B && holdB);
+    const std::string ck =
+        held ? hkey(role, T, &T == &A) : (T.constant ? key(role, T) : std::string());
     const int64_t bytes = bytes0 + bytes1;
     const bool keep = T.constant && (!tc_cache_select || tc_cache_allowed.count(ck) ||
                                       (!tc_cache_cands.count(ck) && bytes <= (int64_t(1) << 28)));
@@ -652,8 +707,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       if (plan_cached && keep) return Packed{};  // held by the cache
     }
     const bool store = keep && tc_cache_fill && !dry && persistent_alloc;
-    if (pack_only && !store) return pk;  // a pack made ahead is only worth keeping
-    if (store) {
+    if (pack_only && !store && !held) return pk;  // a pack made ahead is only worth keeping
+    if (held) {
+      pk = &T == &A ? heldA : heldB;
+    } else if (store) {
       pk.p0 = persistent_alloc(bytes0);
       pk.p1 = persistent_alloc(bytes1);
     } else {
@@ -684,6 +741,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       tc_cache_[ck] = pk;
       tc_cached_.insert(T.p);
     }
+    if (held) held_packs_[ck] = pk;
     return pk;
   };
   if (!packed_path) {
@@ -698,8 +756,10 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   } else if (use_tc) {
     const TcLayout L = gemm_tc_layout(g);
     if (pack_only) {
-      if (A.constant && !cA) operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true, g);
-      if (B.constant && !cB) operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false, g);
+      if ((A.constant || holdA) && !cA)
+        operand("A", A, cA, 4 * L.a_elems, 4 * L.a_elems, true, g);
+      if ((B.constant || holdB) && !cB)
+        operand("B", B, cB, 4 * L.b_elems, 4 * L.b_elems, false, g);
       arena.release(mark);
       return;
     }
@@ -724,9 +784,9 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     if (pack_only) {
       const int64_t abytes = 2 * L.planes * L.a_elems, arow = 4 * L.a_rows;
       const int64_t bbytes = 2 * L.planes * L.b_elems, brow = 4 * L.b_rows;
-      if (A.constant && !cA)
+      if ((A.constant || holdA) && !cA)
         operand(roleA, A, cA, swap ? bbytes : abytes, swap ? brow : arow, !swap, go);
-      if (B.constant && !cB)
+      if ((B.constant || holdB) && !cB)
         operand(roleB, B, cB, swap ? abytes : bbytes, swap ? arow : brow, swap, go);
       arena.release(mark);
       return;

@@ -162,6 +162,18 @@ class Engine {
   bool tc_cached(const double* p) const { return tc_cached_.count(p) != 0; }
   bool graph_timing_ok = true;
 
+  // Held operands (chunk loops that read one tensor in every chunk).  While
+  // the tensor at p is held, each tensor-core pack made of it is placed in
+  // the arena below the contraction's own scratch and reused by the later
+  // contractions with the same spec, shape and role.  The caller keeps the
+  // tensor unchanged while it is held and calls drop_holds() before it
+  // releases the arena below the first of those packs.
+  void hold(const double* p) { held_.insert(p); }
+  void drop_holds() {
+    held_.clear();
+    held_packs_.clear();
+  }
+
  private:
   struct Pending {
     cudaEvent_t a, b;
@@ -179,6 +191,8 @@ class Engine {
   };
   std::map<std::string, Packed> tc_cache_;
   std::set<const double*> tc_cached_;  // tensors with at least one cached pack
+  std::set<const double*> held_;
+  std::map<std::string, Packed> held_packs_;
   std::vector<Pending> pending_;
   std::vector<cudaEvent_t> free_events_;
   cudaEvent_t get_event();

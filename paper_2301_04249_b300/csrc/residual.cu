@@ -23,6 +23,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
   const int nO = op.nO, nV = op.nV, nQ = op.nchol;
   const bool chol = op.chol;
   const AmpGeom g{nO, nV, op.core};
+  E.drop_holds();  // none from an evaluation that did not finish
   const int64_t mark = E.arena.mark();
   Arena& A = E.arena;
   auto blk = [&](const double* base, int b) { return const_cast<double*>(base) + 2 * g.off(b); };
@@ -342,6 +343,20 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
       Tensor tauT = new2();  // tau_ab with e and f swapped: [i][j][f][e]
       axpy("ijef->ijfe", 1.0, tau_ab, 0.0, tauT);
       const int64_t zs = (int64_t)nO * nO * nV;
+      // the four tau operands enter every chunk: packed once, with the
+      // shapes of a full chunk
+      {
+        const int n = std::min(op.chunk_m, nO);
+        const Tensor X = make_tensor(nullptr, false, {nV, nV, n, nV});
+        const Tensor Zc = make_tensor(nullptr, true, {n, nO, nO, nV});
+        for (const Tensor* T : {&tau_ss[0], &tau_ss[1], &tau_ab}) E.hold(T->p);
+        E.hold(tauT.p);
+        E.pack_only = true;
+        for (int s = 0; s < 2; ++s) ein("ijef,efma->mija", 1.0, tau_ss[s], X, 0.0, Zc);
+        ein("ijef,efma->mija", 1.0, tau_ab, X, 0.0, Zc);
+        ein("ijfe,femb->mijb", 1.0, tauT, X, 0.0, Zc);
+        E.pack_only = false;
+      }
       for (int m0 = 0; m0 < nO; m0 += op.chunk_m) {
         const int n = std::min(op.chunk_m, nO - m0);
         const int64_t mc = A.mark();
@@ -355,6 +370,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
         ein("ijfe,femb->mijb", 1.0, tauT, X, 0.0, slice(Z2));  // (me|bf) = X[f][e][m][b]
         A.release(mc);
       }
+      E.drop_holds();
       A.release(mt);
     }
     for (int s = 0; s < 2; ++s) {
@@ -468,6 +484,26 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
         E.launch(kElementwise, 0.0,
                  [&] { pack_pairs(tau_ss[s].p, tpk[s].p, nO, nV, E.stream); });
       }
+    // tau_ab and the pair-packed tau enter every chunk: their tensor-core
+    // packs are made once, here, with the shapes of a full chunk
+    {
+      const int n = std::min(op.chunk_a, nV);
+      const int64_t ncols = pair_start(nV, n) - pair_start(nV, 0);
+      const Tensor Wc = make_tensor(nullptr, false, {nV, nV, n, nV});
+      const Tensor Rc = make_tensor(nullptr, true, {nO, nO, n, nV});
+      E.hold(tau_ab.p);
+      E.pack_only = true;
+      E.contract("ijef,efab->ijab", 1.0, tau_ab, Wc, 0.0, Rc, kLadder);
+      if (tpk[0].p && ncols > 0) {
+        const Tensor Wm = make_tensor(nullptr, false, {npv, ncols});
+        const Tensor Rq = make_tensor(nullptr, true, {npo, ncols});
+        for (int s = 0; s < 2; ++s) {
+          E.hold(tpk[s].p);
+          E.contract("pq,qr->pr", 1.0, tpk[s], Wm, 0.0, Rq, kLadder);
+        }
+      }
+      E.pack_only = false;
+    }
     for (int a0 = 0; a0 < nV; a0 += op.chunk_a) {
       const int n = std::min(op.chunk_a, nV - a0);
       const int64_t mc = A.mark();
@@ -500,6 +536,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
       }
       A.release(mc);
     }
+    E.drop_holds();
     A.release(ml);
   }
   E.arena.release(mark);

@@ -558,10 +558,12 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     auto it = tc_cache_.find(key(roleB, B));
     if (it != tc_cache_.end()) cB = &it->second;
   }
-  // held operands: a pack made earlier in the chunk loop, or room for one
-  // below this call's scratch.  A pack depends on its own tensor's extents
-  // and K only, so the key leaves out the other operand's extent (chunks of
-  // different widths share it).
+  // held operands: a pack made by the pack-only pass ahead of the chunk
+  // loop (room for it is taken below this call's scratch, so it stays at the
+  // loop's level).  A pack depends on its own tensor's extent and K only, so
+  // the key leaves out the other operand's extent and narrower chunks share
+  // it; a chunk whose GEMM takes another orientation (another role) packs
+  // into its own scratch.
   auto hkey = [&](const char* role, const Tensor& T, bool is_a) {
     return std::string(role) + "|" + spec + "|" + std::to_string((uintptr_t)T.p) + "|" +
            std::to_string(is_a ? Mt : Nt) + "," + std::to_string(Kt) + "," + std::to_string(Bt);
@@ -573,14 +575,14 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       if (it != held_packs_.end())
         cA = &it->second;
       else
-        holdA = true;
+        holdA = pack_only;  // made only by the pass ahead of the loop
     }
     if (!cB && !B.constant && held_.count(B.p)) {
       auto it = held_packs_.find(hkey(roleB, B, false));
       if (it != held_packs_.end())
         cB = &it->second;
       else
-        holdB = true;
+        holdB = pack_only;
     }
   }
   Packed heldA, heldB;

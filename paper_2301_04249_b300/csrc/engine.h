@@ -163,11 +163,11 @@ class Engine {
   bool graph_timing_ok = true;
 
   // Held operands (chunk loops that read one tensor in every chunk).  While
-  // the tensor at p is held, each tensor-core pack made of it is placed in
-  // the arena below the contraction's own scratch and reused by the later
-  // contractions with the same spec, shape and role.  The caller keeps the
-  // tensor unchanged while it is held and calls drop_holds() before it
-  // releases the arena below the first of those packs.
+  // the tensor at p is held, a pack_only contraction packs it into the arena
+  // below its own scratch, and the later contractions with the same spec,
+  // role, own extent and K reuse that pack.  The caller makes the packs
+  // ahead of the loop, keeps the tensor unchanged while it is held and calls
+  // drop_holds() before it releases the arena below those packs.
   void hold(const double* p) { held_.insert(p); }
   void drop_holds() {
     held_.clear();

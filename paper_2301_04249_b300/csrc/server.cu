@@ -65,9 +65,11 @@ struct Request {
 // dry-run plan of rteom_plan_bytes, with 5 % and 256 MB of margin.  Whole
 // bytes, so the admission ledger (doubles, all below 2^53) sums exactly and
 // returns to zero when the last request leaves.
-double estimate_bytes(int O, int V, int nchol, int precision) {
+double estimate_bytes(int O, int V, int nchol, int precision, int flags = 0) {
   double b[3] = {0.0, 0.0, 0.0};
-  if (rteom_plan_bytes(O, V, nchol, precision, 0, b) != RTEOM_OK) return 0.0;
+  if (rteom_plan_bytes(O, V, nchol, precision, flags & RTEOM_FLAG_LADDER_CHOLESKY, b) !=
+      RTEOM_OK)
+    return 0.0;
   return std::ceil(1.05 * b[0]) + 256.0 * 1024 * 1024;
 }
 
@@ -138,6 +140,7 @@ struct rteom_server {
             queue.pop_front();
             r->status = RTEOM_REQ_CANCELLED;
             r->t_done = seconds_since(t0);
+            r->in.reset();
             cv_done.notify_all();
             continue;
           }
@@ -255,7 +258,7 @@ bool bad_request(const rteom_server* s, int nocc, int nvir, int nchol, const dou
 void enqueue(rteom_server* s, int nocc, int nvir, int nchol, std::shared_ptr<const Inputs> in,
              const int* cores, int ncores, int flags, int nsteps, double dt, double tol,
              int max_micro, long long* ids) {
-  const double est = estimate_bytes(nocc, nvir, nchol, s->precision);
+  const double est = estimate_bytes(nocc, nvir, nchol, s->precision, flags);
   std::vector<std::unique_ptr<Request>> rs;
   for (int k = 0; k < ncores; ++k) {
     std::unique_ptr<Request> r(new Request());

@@ -95,6 +95,21 @@ extern "C" {
                                          when the resident blocks do not fit
                                          the free device memory; nchol == 0
                                          keeps the resident mode             */
+#define RTEOM_FLAG_ANDERSON        4  /* Anderson-accelerated micro-iterations
+                                         (no counterpart in the paper, which
+                                         names faster solvers of the implicit
+                                         step as future work, Section 3):
+                                         x_{k+1} = g_k - sum_j gamma_j dG_j
+                                         over the last 3 differences of
+                                         g = G(x) and f = g - x, gamma the
+                                         least-squares fit of f (Walker and
+                                         Ni, SIAM J. Numer. Anal. 49, 2011).
+                                         Same stopping rule |g_k - x_k| < tol
+                                         and the same accepted value g_k, so
+                                         the step converges to the same
+                                         implicit solution in fewer residuals
+                                         at tight tol; 9 extra amplitude-sized
+                                         device vectors                       */
 
 typedef struct rteom_ctx rteom_ctx;
 
@@ -209,7 +224,8 @@ int rteom_set_state(rteom_ctx* ctx, const double* t_in, long long steps, const d
  *         when memory allows), [1] the same with no pack cached (the least
  *         it works with), [2] held after set-up with every pack cached
  *  flags  RTEOM_FLAG_LADDER_CHOLESKY plans the Cholesky mode; without it
- *         the plan has resident (ov|vv)/(vv|vv) blocks
+ *         the plan has resident (ov|vv)/(vv|vv) blocks; RTEOM_FLAG_ANDERSON
+ *         adds the buffers of the accelerated micro-iteration
  * Returns RTEOM_OK, or RTEOM_ERR_ARG for a bad shape, precision or flag.
  */
 int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, double* bytes);

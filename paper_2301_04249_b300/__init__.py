@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: F401
                    RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_OOM, RTEOM_ERR_STATE, RTEOM_FLAG_CUMULANT_NO_FOV,
-                   RTEOM_FLAG_LADDER_CHOLESKY,
+                   RTEOM_FLAG_LADDER_CHOLESKY, RTEOM_FLAG_ANDERSON,
                    RTEOM_FP64, RTEOM_OK, RTEOM_REQ_CANCELLED, RTEOM_REQ_DONE, RTEOM_REQ_FAILED,
                    RTEOM_REQ_QUEUED, RTEOM_REQ_RUNNING, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32,
                    RTEOM_FP64_OZAKI)

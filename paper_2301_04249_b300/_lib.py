@@ -20,6 +20,7 @@ RTEOM_SPLIT_TF32 = 2
 RTEOM_FP64_OZAKI = 3
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
 RTEOM_FLAG_LADDER_CHOLESKY = 2
+RTEOM_FLAG_ANDERSON = 4
 RTEOM_REQ_QUEUED = 0
 RTEOM_REQ_RUNNING = 1
 RTEOM_REQ_DONE = 2

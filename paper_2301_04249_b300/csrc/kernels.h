@@ -191,6 +191,24 @@ void unpack_pairs_cols(const double* Rq, double* R, int nO, int nV, int a0, int 
 void add_block(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
                int64_t cols, cudaStream_t st);
 
+// Anderson acceleration of the micro-iteration (depth 3); vectors are n
+// complex elements, the dF and dG histories kAndersonDepth slots of n each.
+constexpr int kAndersonDepth = 3;
+constexpr int kAndersonDots = kAndersonDepth * (kAndersonDepth + 1) / 2 + kAndersonDepth;
+// f = g - x; first: Fp = f, Gp = g; otherwise dF = f - Fp, dG = g - Gp (one
+// slot), then Fp = f, Gp = g.
+void anderson_push(int64_t n, const double* g, const double* x, double* Fp, double* Gp,
+                   double* dF, double* dG, int first, cudaStream_t st);
+// out (complex [kAndersonDots]): <dF_i, dF_j> for (i,j) = (0,0),(0,1),(0,2),
+// (1,1),(1,2),(2,2), then <dF_i, f>, with <u,v> = sum conj(u) v; entries with
+// an index >= count are zero.  partial: complex [anderson_partials()][9].
+int anderson_partials();
+void anderson_dots(int64_t n, const double* dF, const double* f, int count, double* partial,
+                   double* out, cudaStream_t st);
+// x = g - sum_{j < count} gamma_j dG_j; gamma: host, 3 complex (interleaved).
+void anderson_mix(int64_t n, const double* g, const double* dG, int count, const double* gamma,
+                  double* x, cudaStream_t st);
+
 // Geometry of the padded amplitude vector: blocks t1a, t1b (nO*nV) then
 // t2aa, t2ab, t2bb (nO*nO*nV*nV), complex.  Pads: alpha virtual slot 0 and
 // beta occupied slot `core`.

@@ -7,6 +7,7 @@
 // 8-byte convergence word per micro-iteration.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -53,6 +54,14 @@ struct rteom_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
   bool tune_first = false;  // run the next residual eagerly for the autotuner
   bool eager_timing = false;  // rteom_set_timing(ctx, 2): residuals outside graphs
+  // Anderson acceleration of the micro-iteration (RTEOM_FLAG_ANDERSON):
+  // g_k = G(x_k), f_{k-1}, g_{k-1}, the dF/dG histories (kAndersonDepth
+  // slots each), the partials and result of the normal-equation dots, and
+  // their pinned host copy; and_count = history slots in use
+  double *and_g = nullptr, *and_fp = nullptr, *and_gp = nullptr, *and_df = nullptr,
+         *and_dg = nullptr, *and_partial = nullptr, *and_dots = nullptr;
+  double* h_dots = nullptr;
+  int and_count = 0;
   long long cache_plan_bytes = 0;  // tensor-core pack cache planned at set-up
   bool graph_timed[2] = {false, false};            // captured with event-record nodes
   std::vector<Engine::GraphPair> graph_pairs[2];
@@ -107,6 +116,7 @@ struct rteom_ctx {
     for (void* p : allocs)
       if (p) cudaFree(p);
     if (h_maxdiff) cudaFreeHost(h_maxdiff);
+    if (h_dots) cudaFreeHost(h_dots);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
@@ -274,7 +284,8 @@ void energy_into(rteom_ctx* c, const double* t, double* Ehist, double* Chist, lo
   });
 }
 
-void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, double out[3]);
+void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool anderson,
+                        double out[3]);
 
 // Chunk sizes of the Cholesky-mode residual: values of a per ladder chunk
 // (a W chunk of chunk_a*nV^3 doubles) and of m per (mf|ae) chunk, each chunk
@@ -305,7 +316,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
       chol = true;
     } else {
       double pb[3];
-      plan_context_bytes(O, V, nchol, c->precision, false, pb);
+      plan_context_bytes(O, V, nchol, c->precision, false, c->flags & RTEOM_FLAG_ANDERSON, pb);
       size_t fr = 0, tot = 0;
       RT_CUDA(cudaMemGetInfo(&fr, &tot));
       chol = pb[1] > 0.97 * (double)fr;
@@ -546,6 +557,19 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   void* hp = nullptr;
   RT_CUDA(cudaMallocHost(&hp, 64));
   c->h_maxdiff = static_cast<unsigned long long*>(hp);
+  if (c->flags & RTEOM_FLAG_ANDERSON) {
+    const size_t v = 16ull * c->g.total();
+    c->and_g = c->dmalloc(v);
+    c->and_fp = c->dmalloc(v);
+    c->and_gp = c->dmalloc(v);
+    c->and_df = c->dmalloc(kAndersonDepth * v);
+    c->and_dg = c->dmalloc(kAndersonDepth * v);
+    c->and_partial = c->dmalloc(16ull * kAndersonDots * anderson_partials());
+    c->and_dots = c->dmalloc(16ull * kAndersonDots);
+    void* hd = nullptr;
+    RT_CUDA(cudaMallocHost(&hd, 16ull * kAndersonDots));
+    c->h_dots = static_cast<double*>(hd);
+  }
   RT_CUDA(cudaStreamSynchronize(st));
   // split precision and FP64 emulation: tensor-core contractions inside the
   // residual only (the set-up integrals above are FP64); pipeline timeouts
@@ -603,8 +627,10 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
 // setup(): integrals built while the Cholesky inputs live, then the pack
 // cache filled ladder blocks first, each FP64 ladder block freed after its
 // pack.  chol: the Cholesky mode (no (ov|vv)/(vv|vv) blocks; the slot-space
-// Cholesky blocks stay).
-void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, double out[3]) {
+// Cholesky blocks stay); anderson: the buffers of the accelerated
+// micro-iteration.
+void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool anderson,
+                        double out[3]) {
   const double nO = O, nVd = V + 1.0, nb = O + V;
   const int nV = V + 1;
   const double npv = nVd * (nVd - 1.0) / 2.0;
@@ -679,7 +705,10 @@ void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, doubl
       8.0 * (nb + nchol * nb * nb + nchol * nO * nO) +
       (chol ? 0.0 : 8.0 * nchol * (nO * nVd + 2.0 * nVd * nVd));
   const double fock = 2.0 * (24.0 * (nO * nO + nO * nVd + nVd * nVd) + 8.0 * (nO + nVd));
-  const double amps = 4.0 * 16.0 * (double)g.total() + 2.0 * 16.0 * 1024 + 16.0 * 2048 + 256.0;
+  const double amps = 4.0 * 16.0 * (double)g.total() + 2.0 * 16.0 * 1024 + 16.0 * 2048 + 256.0 +
+                      (anderson ? (3.0 + 2.0 * kAndersonDepth) * 16.0 * (double)g.total() +
+                                      16.0 * kAndersonDots * (anderson_partials() + 1.0)
+                                : 0.0);
   const double phase_a_all = inputs + fock + ints + arena_all;
   const double phase_a_none = inputs + fock + ints + arena_none;
   const double base_all = ints + fock + arena_all + amps;
@@ -713,6 +742,71 @@ int rteom_internal_begin(rteom_ctx* c, int nsteps, double dt, double tol, int ma
   });
 }
 
+// Anderson coefficients: gamma minimising |f - dF gamma| from the normal
+// equations H gamma = b (H_ij = <dF_i, dF_j>, b_i = <dF_i, f>, the layout of
+// anderson_dots), H regularised by 1e-10 of its largest diagonal entry (the
+// normal equations square the condition of dF) and solved by Gaussian
+// elimination with partial pivoting.  False when no usable solution exists
+// or a coefficient exceeds 1e4 (nearly dependent history); the caller then
+// takes the plain step.
+static bool anderson_gamma(int m, const double* dots, double* gamma) {
+  using cd = std::complex<double>;
+  static const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+  cd H[kAndersonDepth][kAndersonDepth + 1];
+  for (int d = 0; d < 6; ++d) {
+    const cd v(dots[2 * d], dots[2 * d + 1]);
+    H[I[d]][J[d]] = v;
+    H[J[d]][I[d]] = std::conj(v);
+  }
+  double hmax = 0.0;
+  for (int i = 0; i < m; ++i) {
+    H[i][i] = cd(H[i][i].real(), 0.0);
+    H[i][m] = cd(dots[12 + 2 * i], dots[13 + 2 * i]);
+    hmax = std::max(hmax, H[i][i].real());
+  }
+  if (!(hmax > 0.0) || !std::isfinite(hmax)) return false;
+  for (int i = 0; i < m; ++i) H[i][i] += 1e-10 * hmax;
+  for (int col = 0; col < m; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < m; ++r)
+      if (std::abs(H[r][col]) > std::abs(H[piv][col])) piv = r;
+    if (!(std::abs(H[piv][col]) > 0.0)) return false;
+    for (int q = 0; q <= m; ++q) std::swap(H[col][q], H[piv][q]);
+    for (int r = col + 1; r < m; ++r) {
+      const cd f = H[r][col] / H[col][col];
+      for (int q = col; q <= m; ++q) H[r][q] -= f * H[col][q];
+    }
+  }
+  cd x[kAndersonDepth];
+  for (int i = m - 1; i >= 0; --i) {
+    cd v = H[i][m];
+    for (int q = i + 1; q < m; ++q) v -= H[i][q] * x[q];
+    x[i] = v / H[i][i];
+    if (!std::isfinite(x[i].real()) || !std::isfinite(x[i].imag()) || std::abs(x[i]) > 1e4)
+      return false;
+  }
+  for (int i = 0; i < kAndersonDepth; ++i) {
+    gamma[2 * i] = i < m ? x[i].real() : 0.0;
+    gamma[2 * i + 1] = i < m ? x[i].imag() : 0.0;
+  }
+  return true;
+}
+
+// Next iterate of the accelerated micro-iteration into T_K: the plain step
+// x = g_k while there is no history, else x = g_k - sum_j gamma_j dG_j.
+static void anderson_next(rteom_ctx* c) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->g.total();
+  double gamma[2 * kAndersonDepth];
+  if (c->and_count > 0 && anderson_gamma(c->and_count, c->h_dots, gamma)) {
+    c->E.launch(kElementwise, 0.0, [&] {
+      anderson_mix(n, c->and_g, c->and_dg, c->and_count, gamma, c->T_K, st);
+    });
+  } else {
+    RT_CUDA(cudaMemcpyAsync(c->T_K, c->and_g, 16ull * n, cudaMemcpyDeviceToDevice, st));
+  }
+}
+
 // Launch micro-iteration k of the current step (residual when k > 0, the
 // Adams-Moulton update, the status-word copy) and record the run event.
 static void launch_micro(rteom_ctx* c, int k) {
@@ -721,10 +815,27 @@ static void launch_micro(rteom_ctx* c, int k) {
   RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 8, st));
   const double* tk_in = k == 0 ? c->T_N : c->T_K;
   const double* Rk = k == 0 ? c->R_N : c->R_K;
+  double* out = c->and_g ? c->and_g : c->T_K;  // Anderson: g_k apart from x_k
   c->E.launch(kElementwise, 0.0, [&] {
-    am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], c->dt, c->T_N, c->R_N, tk_in, c->T_K,
-              Rk, c->maxdiff, st);
+    am_update(c->g, c->fo[0], c->fv[0], c->fo[1], c->fv[1], c->dt, c->T_N, c->R_N, tk_in, out, Rk,
+              c->maxdiff, st);
   });
+  if (c->and_g) {
+    const int64_t n = c->g.total();
+    const int64_t slot = k == 0 ? 0 : (k - 1) % kAndersonDepth;
+    c->E.launch(kElementwise, 0.0, [&] {
+      anderson_push(n, c->and_g, tk_in, c->and_fp, c->and_gp, c->and_df + 2 * n * slot,
+                    c->and_dg + 2 * n * slot, k == 0, st);
+    });
+    c->and_count = k == 0 ? 0 : std::min(k, kAndersonDepth);
+    if (c->and_count > 0) {
+      c->E.launch(kElementwise, 0.0, [&] {
+        anderson_dots(n, c->and_df, c->and_fp, c->and_count, c->and_partial, c->and_dots, st);
+      });
+      RT_CUDA(cudaMemcpyAsync(c->h_dots, c->and_dots, 16ull * kAndersonDots,
+                              cudaMemcpyDeviceToHost, st));
+    }
+  }
   RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
   RT_CUDA(cudaEventRecord(c->run.ev, st));
 }
@@ -769,7 +880,8 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
     }
     if (d < r.tol) {  // converged: accept t^(k+1), cumulant step
       cudaStream_t st = c->stream;
-      RT_CUDA(cudaMemcpyAsync(c->T_N, c->T_K, 16ull * c->g.total(), cudaMemcpyDeviceToDevice, st));
+      RT_CUDA(cudaMemcpyAsync(c->T_N, c->and_g ? c->and_g : c->T_K, 16ull * c->g.total(),
+                              cudaMemcpyDeviceToDevice, st));
       energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
       c->steps += 1;
       c->micro_total += r.k + 1;
@@ -787,6 +899,7 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
       return fail(c, RTEOM_ERR_NOT_CONVERGED,
                   "micro-iterations did not reach tol at step " + std::to_string(c->steps));
     }
+    if (c->and_g) anderson_next(c);  // x_{k+1} into T_K
     r.k += 1;
     launch_micro(c, r.k);
     *waiting = 1;
@@ -821,7 +934,7 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
       precision != RTEOM_SPLIT_BF16)
     return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 "
                               "or RTEOM_FP64_OZAKI");
-  if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY))
+  if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON))
     return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)
@@ -1000,14 +1113,16 @@ int rteom_set_state(rteom_ctx* c, const double* t_in, long long steps, const dou
 
 int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, double* bytes) {
   if (!bytes || nocc < 1 || nvir < 1 || nchol < 0 ||
-      (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY)) ||
+      (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY |
+                 RTEOM_FLAG_ANDERSON)) ||
       (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
        precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16) ||
       (double)(nvir + 1) * (nvir + 1) > 2.0e9)
     return RTEOM_ERR_ARG;
   try {
     plan_context_bytes(nocc, nvir, nchol, precision,
-                       (flags & RTEOM_FLAG_LADDER_CHOLESKY) && nchol > 0, bytes);
+                       (flags & RTEOM_FLAG_LADDER_CHOLESKY) && nchol > 0,
+                       (flags & RTEOM_FLAG_ANDERSON) != 0, bytes);
   } catch (const std::exception&) {
     return RTEOM_ERR_ARG;
   }

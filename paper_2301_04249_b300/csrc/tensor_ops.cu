@@ -303,6 +303,118 @@ __global__ void add_block_kernel(double* __restrict__ dst, int64_t ldd,
     for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) dst[r * ldd + c] += src[r * lds + c];
 }
 
+// ---------------------------------------------------------------- Anderson mixing
+// Type-II Anderson acceleration of the fixed-point micro-iteration (Walker and
+// Ni, SIAM J. Numer. Anal. 49, 1715 (2011)): with g_k = G(x_k), f_k = g_k - x_k
+// and the last differences dF_j = f_{j+1} - f_j, dG_j = g_{j+1} - g_j,
+// x_{k+1} = g_k - sum_j gamma_j dG_j where gamma minimises |f_k - sum_j gamma_j dF_j|.
+
+// f = g - x.  first: Fp = f, Gp = g.  Otherwise dF[slot] = f - Fp,
+// dG[slot] = g - Gp, then Fp = f, Gp = g.
+__global__ void anderson_push_kernel(int64_t n, const double2* __restrict__ g,
+                                     const double2* __restrict__ x, double2* Fp, double2* Gp,
+                                     double2* __restrict__ dF, double2* __restrict__ dG,
+                                     int first) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 gv = g[e], xv = x[e];
+    const double2 f = make_double2(gv.x - xv.x, gv.y - xv.y);
+    if (!first) {
+      const double2 fp = Fp[e], gp = Gp[e];
+      dF[e] = make_double2(f.x - fp.x, f.y - fp.y);
+      dG[e] = make_double2(gv.x - gp.x, gv.y - gp.y);
+    }
+    Fp[e] = f;
+    Gp[e] = gv;
+  }
+}
+
+// Inner products <u, v> = sum conj(u) v of the normal equations: positions
+// 0..5 hold <dF_i, dF_j> for (i, j) = (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) and
+// 6..8 hold <dF_i, f>; entries with an index >= count are zero.  Pass 1: one
+// partial per block (fixed grid), pass 2: fixed-order sums (deterministic).
+__device__ __forceinline__ void and_pair(int d, int& i, int& j) {
+  const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+  i = I[d];
+  j = J[d];
+}
+
+__global__ void anderson_dots_pass1(int64_t n, const double2* __restrict__ dF, int64_t slot,
+                                    const double2* __restrict__ f, int count,
+                                    double2* __restrict__ partial) {
+  double2 acc[kAndersonDots];
+#pragma unroll
+  for (int d = 0; d < kAndersonDots; ++d) acc[d] = make_double2(0.0, 0.0);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double2 u[kAndersonDepth];
+#pragma unroll
+    for (int q = 0; q < kAndersonDepth; ++q)
+      u[q] = q < count ? dF[q * slot + e] : make_double2(0.0, 0.0);
+    const double2 fv = f[e];
+#pragma unroll
+    for (int d = 0; d < kAndersonDots; ++d) {
+      double2 a, b;
+      if (d < 6) {
+        int i, j;
+        and_pair(d, i, j);
+        a = u[i];
+        b = u[j];
+      } else {
+        a = u[d - 6];
+        b = fv;
+      }
+      acc[d].x += a.x * b.x + a.y * b.y;
+      acc[d].y += a.x * b.y - a.y * b.x;
+    }
+  }
+  __shared__ double2 red[kThreads];
+  for (int d = 0; d < kAndersonDots; ++d) {
+    red[threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        red[threadIdx.x].x += red[threadIdx.x + w].x;
+        red[threadIdx.x].y += red[threadIdx.x + w].y;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kAndersonDots + d] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void anderson_dots_pass2(const double2* __restrict__ partial, int np,
+                                    double2* __restrict__ out) {
+  const int d = threadIdx.x;
+  if (d >= kAndersonDots) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < np; ++b) {
+    const double2 v = partial[(int64_t)b * kAndersonDots + d];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[d] = s;
+}
+
+// x = g - sum_{j < count} gamma_j dG_j
+__global__ void anderson_mix_kernel(int64_t n, const double2* __restrict__ g,
+                                    const double2* __restrict__ dG, int64_t slot, int count,
+                                    double2 g0, double2 g1, double2 g2,
+                                    double2* __restrict__ x) {
+  const double2 gam[3] = {g0, g1, g2};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = g[e];
+    for (int q = 0; q < count; ++q) {
+      const double2 w = dG[q * slot + e];
+      v.x -= gam[q].x * w.x - gam[q].y * w.y;
+      v.y -= gam[q].x * w.y + gam[q].y * w.x;
+    }
+    x[e] = v;
+  }
+}
+
 // ---------------------------------------------------------------- amplitude geometry
 struct Elem {
   int blk, i, j, a, b;
@@ -798,6 +910,41 @@ void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const d
       g, fo_a, fv_a, fo_b, fv_b, dt, reinterpret_cast<const double2*>(tn),
       reinterpret_cast<const double2*>(Rn), reinterpret_cast<const double2*>(tk_in),
       reinterpret_cast<double2*>(tk_out), reinterpret_cast<const double2*>(Rk), maxdiff_bits);
+  RT_CHECK_LAUNCH();
+}
+
+void anderson_push(int64_t n, const double* g, const double* x, double* Fp, double* Gp,
+                   double* dF, double* dG, int first, cudaStream_t st) {
+  if (n == 0) return;
+  anderson_push_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
+      n, reinterpret_cast<const double2*>(g), reinterpret_cast<const double2*>(x),
+      reinterpret_cast<double2*>(Fp), reinterpret_cast<double2*>(Gp),
+      reinterpret_cast<double2*>(dF), reinterpret_cast<double2*>(dG), first);
+  RT_CHECK_LAUNCH();
+}
+
+int anderson_partials() { return 148 * 4; }
+
+void anderson_dots(int64_t n, const double* dF, const double* f, int count, double* partial,
+                   double* out, cudaStream_t st) {
+  const int np = anderson_partials();
+  anderson_dots_pass1<<<np, kThreads, 0, st>>>(n, reinterpret_cast<const double2*>(dF), n,
+                                               reinterpret_cast<const double2*>(f), count,
+                                               reinterpret_cast<double2*>(partial));
+  RT_CHECK_LAUNCH();
+  anderson_dots_pass2<<<1, 32, 0, st>>>(reinterpret_cast<const double2*>(partial), np,
+                                        reinterpret_cast<double2*>(out));
+  RT_CHECK_LAUNCH();
+}
+
+void anderson_mix(int64_t n, const double* g, const double* dG, int count, const double* gamma,
+                  double* x, cudaStream_t st) {
+  if (n == 0) return;
+  const double2 g0 = make_double2(gamma[0], gamma[1]), g1 = make_double2(gamma[2], gamma[3]),
+                g2 = make_double2(gamma[4], gamma[5]);
+  anderson_mix_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(
+      n, reinterpret_cast<const double2*>(g), reinterpret_cast<const double2*>(dG), n, count, g0,
+      g1, g2, reinterpret_cast<double2*>(x));
   RT_CHECK_LAUNCH();
 }
 

@@ -2,6 +2,7 @@
 
   python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde] [--residuals 2]
          [--precision fp64|split_tf32|split_bf16|fp64_ozaki] [--cholesky] [--steps N]
+         [--tol TOL] [--anderson]
 
 Each evaluation launches every kernel of one residual on the library's
 stream outside CUDA graphs, with the particle-particle ladder GEMMs inside
@@ -11,7 +12,8 @@ With --steps N it propagates N Adams-Moulton steps from T(0) = 0 instead
 (no host amplitude arrays) and prints the set-up time, the device memory
 the context took and the time per step.  --cholesky asks for the Cholesky
 mode (RTEOM_FLAG_LADDER_CHOLESKY); rteom_create also takes it by itself
-when the resident blocks do not fit.
+when the resident blocks do not fit.  --anderson accelerates the
+micro-iterations (RTEOM_FLAG_ANDERSON); --tol sets their cutoff (1e-4).
 """
 from __future__ import annotations
 
@@ -37,6 +39,8 @@ def main():
                     default="fp64")
     ap.add_argument("--cholesky", action="store_true")
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--anderson", action="store_true")
     ap.add_argument("--eager-timing", action="store_true",
                     help="with --steps: residuals outside graphs, every launch timed")
     a = ap.parse_args()
@@ -44,7 +48,8 @@ def main():
     rng = np.random.default_rng(0)
     prec = {"fp64": P.RTEOM_FP64, "split_tf32": P.RTEOM_SPLIT_TF32,
             "split_bf16": P.RTEOM_SPLIT_BF16, "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
-    flags = P.RTEOM_FLAG_LADDER_CHOLESKY if a.cholesky else 0
+    flags = (P.RTEOM_FLAG_LADDER_CHOLESKY if a.cholesky else 0) | \
+        (P.RTEOM_FLAG_ANDERSON if a.anderson else 0)
     if a.steps > 0:
         import torch
         free0 = torch.cuda.mem_get_info()[0]
@@ -54,10 +59,11 @@ def main():
             held = free0 - torch.cuda.mem_get_info()[0]
             g.set_timing(2 if a.eager_timing else 1)
             t0 = time.perf_counter()
-            g.propagate(a.steps, run["dt"], tol=1e-4)
+            g.propagate(a.steps, run["dt"], tol=a.tol)
             wall = time.perf_counter() - t0
             info = g.info()
-            print(json.dumps(dict(workload=a.workload, precision=a.precision,
+            print(json.dumps(dict(workload=a.workload, precision=a.precision, tol=a.tol,
+                                  anderson=a.anderson,
                                   setup_s=setup_s, device_bytes_held=held,
                                   steps=a.steps, s_per_step=wall / a.steps,
                                   micro_per_step=info["micro"] / a.steps,

@@ -89,3 +89,11 @@ def test_config5_fits_one_b300_only_in_cholesky_mode(precision):
 def test_plan_rejects_unknown_flags():
     with pytest.raises(P.RteomError):
         P.plan_bytes(4, 10, 5, P.RTEOM_FP64, 1 << 7)
+
+
+def test_anderson_buffers_are_planned():
+    O, V = 8, 100
+    total = 2 * O * (V + 1) + 3 * O * O * (V + 1) ** 2
+    base = P.plan_bytes(O, V, 400, P.RTEOM_FP64)["peak"]
+    acc = P.plan_bytes(O, V, 400, P.RTEOM_FP64, P.RTEOM_FLAG_ANDERSON)["peak"]
+    assert acc - base >= 9 * 16 * total

@@ -148,7 +148,8 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol,
 /*
  * rteom_propagate -- advance the amplitudes nsteps time steps of length dt
  * with the first-order Adams-Moulton rule (Eq. 9), each solved by fixed-point
- * micro-iterations from the predictor t^(0) = t_n, stopping when the largest
+ * micro-iterations (Anderson-accelerated with RTEOM_FLAG_ANDERSON) from the
+ * predictor t^(0) = t_n, stopping when the largest
  * |t^(k+1) - t^(k)| over all blocks is below tol, and accumulate the cumulant
  * C_{n+1} = C_n + (i dt/2)(E_n + E_{n+1}) with E = <Phi|(H_N e^T)_C|Phi>
  * (Eqs. 5-6).

@@ -59,8 +59,9 @@ class Engine {
   std::set<std::string> tc_cache_allowed;
   bool tc_cache_select = false;
   bool plan_cached = false;
-  // pack_only: a tensor-core contraction only packs (and caches) its constant
-  // operands and launches nothing else
+  // pack_only: a tensor-core contraction only packs its constant operands
+  // (into the cache) and its held operands (see hold()) and launches
+  // nothing else
   bool pack_only = false;
 
   // Autotuner.  A GEMM of at most tune_max_flops that is not a matrix-vector

@@ -100,6 +100,22 @@ def test_c2_full_size_first_steps_match_oracle():
     assert _relC(C, gold["C"]) < 1e-10
 
 
+def test_c2_first_50_steps_at_the_production_tolerance_match_oracle():
+    """The benchmark workload at the paper's tol 1e-4: the first 50 steps of
+    C(t) against the stored oracle run.  Both sides apply the same stopping
+    rule, so they take the same micro-iterations, and C(t) agrees to FP64
+    rounding."""
+    gold = _load_golden("c2_formaldehyde_tol0.0001")
+    p, run = workload("c2_formaldehyde")
+    n = len(gold["C"]) - 1
+    assert n >= 50
+    with _ctx(p) as g:
+        C = g.propagate(n, run["dt"], tol=1e-4)
+        info = g.info()
+    assert info["micro"] == gold["micro"].sum()
+    assert _relC(C, gold["C"]) < 1e-10
+
+
 def test_c2_full_size_residual_sampled(rng):
     """Full-size residual at random amplitudes: every element of the T1 blocks
     and a random sample of T2 elements against the oracle."""

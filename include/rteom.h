@@ -138,7 +138,10 @@ typedef struct rteom_ctx rteom_ctx;
  * The inputs are copied to device memory owned by the context (cudaMalloc);
  * the amplitudes start at T(0) = 0 and C(0) = 0 (Section 3).  Errors:
  * RTEOM_ERR_ARG (sizes, indices, NULL eps), RTEOM_ERR_NONFINITE (NaN/Inf in
- * an input), RTEOM_ERR_OOM, RTEOM_ERR_CUDA.
+ * an input), RTEOM_ERR_OOM, RTEOM_ERR_CUDA.  Fault injection for tests: with
+ * the environment variable RTEOM_INJECT_DEVICE_LIMIT=<bytes> set when the
+ * context is created, its device allocations past that total fail with
+ * RTEOM_ERR_OOM on the host (no device call is made for them).
  */
 int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol,
                  const double* eps, const double* L,

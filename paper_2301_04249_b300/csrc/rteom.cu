@@ -81,9 +81,16 @@ struct rteom_ctx {
 
   size_t bytes_allocated = 0;
   std::vector<size_t> alloc_sizes;
+  // host-side fault injection for tests: device allocations past this many
+  // bytes fail as out of memory (RTEOM_INJECT_DEVICE_LIMIT; -1 = off)
+  long long inject_limit = -1;
   double* dmalloc(size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (inject_limit >= 0 && (long long)(bytes_allocated + bytes) > inject_limit)
+      throw Error(RTEOM_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) +
+                                     "): injected device limit of " +
+                                     std::to_string(inject_limit) + " bytes");
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -962,6 +969,7 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   c->nO = nocc;
   c->nV = nvir + 1;
   c->g = AmpGeom{c->nO, c->nV, core_index};
+  if (const char* v = std::getenv("RTEOM_INJECT_DEVICE_LIMIT")) c->inject_limit = std::atoll(v);
   int rc = guarded(c.get(), [&] {
     if (cuda_stream) {
       c->stream = static_cast<cudaStream_t>(cuda_stream);

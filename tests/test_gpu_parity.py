@@ -213,6 +213,21 @@ def test_bad_calls_return_errors():
         assert e.value.code == P.RTEOM_ERR_NONFINITE
 
 
+def test_injected_out_of_memory_is_reported_and_leaves_the_device_usable(monkeypatch):
+    """Host-side fault injection: device allocations past 1 MB fail with
+    RTEOM_ERR_OOM during set-up; the partial context is freed and the next
+    context works."""
+    p = gen_problem(4, 12, 20, 21)
+    monkeypatch.setenv("RTEOM_INJECT_DEVICE_LIMIT", str(2 ** 20))
+    with pytest.raises(P.RteomError) as e:
+        _ctx(p)
+    assert e.value.code == P.RTEOM_ERR_OOM
+    monkeypatch.delenv("RTEOM_INJECT_DEVICE_LIMIT")
+    with _ctx(p) as g:
+        C = g.propagate(3, 0.05, tol=1e-10)
+    assert np.isfinite(C).all()
+
+
 def test_timed_and_untimed_graphs_agree_bitwise():
     """Timing adds event-record nodes around the ladder GEMMs of the captured
     residual graphs; results must not change."""

@@ -133,3 +133,22 @@ def test_sweep_with_a_core_outside_the_occupied_space_queues_nothing():
             s.submit_sweep(p, [], 5, DT)
         st = s.stats()
     assert st["queued"] == 0 and st["running"] == 0 and st["done"] == 0
+
+
+def test_a_request_that_runs_out_of_memory_fails_alone(monkeypatch):
+    """Host-side fault injection: every context may hold at most 10 MB, so
+    the O=6, V=40 request (about 67 MB planned) fails with RTEOM_ERR_OOM at
+    set-up while the small requests around it complete."""
+    monkeypatch.setenv("RTEOM_INJECT_DEVICE_LIMIT", str(10 * 2 ** 20))
+    small = [gen_problem(3, 10, 12, 41), gen_problem(3, 10, 12, 43)]
+    big = gen_problem(6, 40, 80, 42)
+    with P.Server(max_active=2) as s:
+        ids = [s.submit(small[0], 5, DT, tol=1e-8), s.submit(big, 5, DT, tol=1e-8),
+               s.submit(small[1], 5, DT, tol=1e-8)]
+        for rid in ids:
+            assert s.wait(rid, 120.0)
+        res = [s.poll(rid) for rid in ids]
+        st = s.stats()
+    assert res[0][0] == P.RTEOM_REQ_DONE and res[2][0] == P.RTEOM_REQ_DONE
+    assert res[1][0] == P.RTEOM_REQ_FAILED and res[1][1] == P.RTEOM_ERR_OOM
+    assert st["done"] == 2 and st["failed"] == 1 and st["mem_in_use"] == 0

@@ -374,11 +374,16 @@ void rteom_server_destroy(rteom_server* s);
  *
  * Scratch: one partial sum per occupied pair lives in a static device array
  * of 4096 doubles (32 KiB) that every GPU loading the library keeps until the
- * process exits.  The first call on each device looks up that array's device
- * address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.  All calls share the array
- * and each overwrites the partials it reads, so calls whose kernels overlap on
- * the GPU (other streams, other host threads) race and must be serialised.
+ * process exits.  The first call in each CUDA context (the first call on a
+ * device, and the first again after a cudaDeviceReset, which reloads the
+ * library's device code at a new address) looks up that array's device
+ * address with cudaGetSymbolAddress, with the caller's device current, and
+ * caches it under the context's id; make that first call before any stream
+ * capture.  All calls share the array and each overwrites the partials it
+ * reads, so calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race and must be serialised.
+ * Cost: 2 O^2 V^2 Nchol FP64 FMAs (the integrals are formed from L for every
+ * (i,j,a,b)), meant for small ground-state problems.
  * Errors: RTEOM_ERR_ARG (sizes, including nocc*nocc > 4096, or NULL
  * pointers; checked before any launch), RTEOM_ERR_CUDA.
  */

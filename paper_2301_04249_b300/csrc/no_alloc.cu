@@ -15,23 +15,27 @@
 // streams, or different host threads on one device) race on it; serialise
 // them.  Each call overwrites every partial it later reads, so nothing has to
 // start at zero.
+//
+// Cost: the pair kernel forms (ia|jb) and (ib|ja) from the Cholesky vectors
+// for every (i,j,a,b), 2 O^2 V^2 Nchol FP64 FMAs (about 1.8e12 at O=50, V=450,
+// Nchol=1800, minutes on the FP64 pipe), against the O^2 V^2 of rteom_create,
+// which reads its stored (ov|ov) block.  It suits the small ground-state
+// problems this entry point is meant for.
+#include <cuda.h>
+
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "../../include/rteom.h"
 #include "common.cuh"
+#include "scratch_cache.h"
 
 namespace {
 
 constexpr int kMaxPairs = 4096;  // occupied pairs (i,j): nocc <= 64
 constexpr int kThreads = 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_ecorr_pairs[kMaxPairs];
-
-std::mutex g_setup_mutex;
-double* g_pairs_ptr[kMaxDevices] = {nullptr};
 
 // One block per occupied pair (i,j): partial[i*O+j] = sum_ab [2(ia|jb) -
 // (ib|ja)] (t2_ijab + t1_ia t1_jb), with (pq|rs) = sum_Q L_pq L_rs.
@@ -84,27 +88,77 @@ int report(int code, const std::string& msg, char* err, int err_len) {
   return code;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Driver entry points for the id of the current context, fetched once
+// through the runtime (the library does not link the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+struct CtxIdApi {
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+};
+
+const CtxIdApi& ctx_id_api() {
+  static const CtxIdApi api = [] {
+    CtxIdApi a;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      a.get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      a.get_id = reinterpret_cast<CtxGetIdFn>(f);
+    return a;
+  }();
+  return api;
+}
+
+// Id of the context current on this thread; false when there is none yet
+// (the runtime makes the device's primary context current on its first use)
+// or the entry points are unavailable.
+bool current_ctx_id(unsigned long long* id) {
+  const CtxIdApi& api = ctx_id_api();
+  if (!api.get_current || !api.get_id) return false;
+  CUcontext ctx = nullptr;
+  if (api.get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return api.get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+rteom::ContextAddressCache g_pairs_cache;
+
+// Device address of the scratch array in the current context: looked up with
+// cudaGetSymbolAddress (with the caller's device current) the first time a
+// context uses this entry point, then taken from the per-context cache.
 int pairs_scratch(double** out, char* err, int err_len) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess)
-    return report(RTEOM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e), err,
-                  err_len);
-  if (dev < 0 || dev >= kMaxDevices)
-    return report(RTEOM_ERR_ARG, "device ordinal beyond the supported 64 devices", err, err_len);
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_pairs_ptr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_ecorr_pairs);
-    if (e != cudaSuccess || p == nullptr)
-      return report(RTEOM_ERR_CUDA,
-                    std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e), err,
-                    err_len);
-    g_pairs_ptr[dev] = p;
+  auto lookup = [](void** addr) -> int {
+    const cudaError_t e = cudaGetSymbolAddress(addr, g_ecorr_pairs);
+    return (e == cudaSuccess && *addr != nullptr) ? 0 : (int)e + 1;
+  };
+  auto failed = [&](int rc) {
+    return report(RTEOM_ERR_CUDA,
+                  std::string("cudaGetSymbolAddress(scratch): ") +
+                      cudaGetErrorString(static_cast<cudaError_t>(rc - 1)),
+                  err, err_len);
+  };
+  unsigned long long id = 0;
+  void* p = nullptr;
+  if (!current_ctx_id(&id)) {
+    // no current context yet: this lookup creates the primary context; the
+    // address is cached under its id when the id can be read
+    const int rc = lookup(&p);
+    if (rc != 0) return failed(rc);
+    if (current_ctx_id(&id)) {
+      const int rc2 = g_pairs_cache.get(id, lookup, &p);
+      if (rc2 != 0) return failed(rc2);
+    }
+  } else {
+    const int rc = g_pairs_cache.get(id, lookup, &p);
+    if (rc != 0) return failed(rc);
   }
-  *out = g_pairs_ptr[dev];
+  *out = static_cast<double*>(p);
   return RTEOM_OK;
 }
 
@@ -131,10 +185,18 @@ extern "C" int rteom_ecorr_noalloc(int nocc, int nvir, int nchol, const double* 
   int rc = pairs_scratch(&scratch, err, err_len);
   if (rc != RTEOM_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int pairs = nocc * nocc;
-  ecorr_pairs_kernel<<<pairs, kThreads, 0, st>>>(L, nchol, nocc, nvir, t1_gs, t2_gs, scratch);
-  ecorr_sum_kernel<<<1, kThreads, 0, st>>>(scratch, pairs, e_corr);
-  cudaError_t e = cudaGetLastError();
+  int pairs = nocc * nocc;
+  // cudaLaunchKernel returns the error of this launch itself, so an earlier,
+  // unrelated error of the calling thread is neither reported nor cleared
+  void* pair_args[] = {(void*)&L,      (void*)&nchol, (void*)&nocc,  (void*)&nvir,
+                       (void*)&t1_gs, (void*)&t2_gs, (void*)&scratch};
+  cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(&ecorr_pairs_kernel),
+                                   dim3(pairs), dim3(kThreads), pair_args, 0, st);
+  if (e == cudaSuccess) {
+    void* sum_args[] = {(void*)&scratch, (void*)&pairs, (void*)&e_corr};
+    e = cudaLaunchKernel(reinterpret_cast<const void*>(&ecorr_sum_kernel), dim3(1),
+                         dim3(kThreads), sum_args, 0, st);
+  }
   if (e != cudaSuccess)
     return report(RTEOM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e), err,
                   err_len);

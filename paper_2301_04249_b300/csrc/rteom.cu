@@ -6,8 +6,10 @@
 // evaluation is one CUDA graph (captured on first use); the host reads one
 // 8-byte convergence word per micro-iteration.
 #include <algorithm>
+#include <cerrno>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -969,7 +971,23 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   c->nO = nocc;
   c->nV = nvir + 1;
   c->g = AmpGeom{c->nO, c->nV, core_index};
-  if (const char* v = std::getenv("RTEOM_INJECT_DEVICE_LIMIT")) c->inject_limit = std::atoll(v);
+  if (const char* v = std::getenv("RTEOM_INJECT_DEVICE_LIMIT")) {
+    // test-only fault injection: a plain byte count; anything else is
+    // rejected so that a mistyped value cannot pass for a real OOM
+    char* end = nullptr;
+    errno = 0;
+    const long long lim = std::strtoll(v, &end, 10);
+    if (end == v || *end != '\0' || errno != 0 || lim < 0)
+      return bad(RTEOM_ERR_ARG, std::string("RTEOM_INJECT_DEVICE_LIMIT must be a byte count, got '") +
+                                    v + "'");
+    c->inject_limit = lim;
+    static bool announced = false;
+    if (!announced) {
+      announced = true;
+      std::fprintf(stderr, "rteom: RTEOM_INJECT_DEVICE_LIMIT=%lld: device allocations past this "
+                           "total fail as out of memory (fault injection)\n", lim);
+    }
+  }
   int rc = guarded(c.get(), [&] {
     if (cuda_stream) {
       c->stream = static_cast<cudaStream_t>(cuda_stream);

@@ -69,3 +69,10 @@ def test_block_marshalling_roundtrip(rng):
     back = P.split_blocks(P.join_blocks(blocks), 4, 6)
     for a, b in zip(blocks, back):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("val", ["abc", "10MB", "-5", ""])
+def test_injected_device_limit_must_be_a_byte_count(monkeypatch, val):
+    monkeypatch.setenv("RTEOM_INJECT_DEVICE_LIMIT", val)
+    rc, msg = _create()
+    assert rc == P.RTEOM_ERR_ARG and "RTEOM_INJECT_DEVICE_LIMIT" in msg

@@ -4,11 +4,20 @@
 One bench step = one time step of the propagation (Eq. 9): the residual
 R(t_n), the fixed-point micro-iterations of the Adams-Moulton update, the
 cumulant integrand and C_{n+1} (Eqs. 5-6).  Metric: time steps/s, whole job
-(sum over ranks; ranks are independent replicas).  Default workload: the
-formaldehyde-shaped FP64 problem O=8, V=100, Nchol=400, dt=0.025 au, with
-the paper's micro-iteration cutoff 1e-4.
+(sum over ranks; ranks are independent replicas).
+
+Default workload: the ESCA-shaped propagation O=50, V=450, Nchol=1800,
+dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-precision
+form (contractions as split products on the tensor cores, FP64 update,
+cumulant and phases).  Beside it, on the same inputs: the other split form
+and the FP64-accurate emulated form (a few steps each), an estimate of the
+plain FP64 (DFMA) form from its measured contraction rate, and the
+formaldehyde-shaped FP64 workload (O=8, V=100, Nchol=400) as a secondary
+line.  Every form reports time per step and per micro-iteration (the
+paper's metric) and TFLOP/s against measured peaks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--form split_tf32|split_bf16|fp64_ozaki|fp64]
 
 Prints one JSON line on rank 0.
 """
@@ -34,13 +43,17 @@ from synth import workload  # noqa: E402
 
 METRIC = "time_steps_per_s"
 UNIT = "steps/s"
-FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (profiling recipe table); no tensor-core FP64 path
-TF32_PER_BF16_NOMINAL = 1.1 / 2.25  # dense TF32 / dense BF16, nominal B300 figures
 MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
-LADDER_PROFILE = os.path.join(HERE, "profiles", "ladder_gemm_f64_c2.txt")
-LADDER_TC_PROFILE = os.path.join(HERE, "profiles", "ladder_tc_tf32_c2.txt")
-LADDER_OZ_PROFILE = os.path.join(HERE, "profiles", "ladder_oz_bf16_c2.txt")
-LADDER_OZ3_PROFILE = os.path.join(HERE, "profiles", "ladder_oz3_split_bf16_c2.txt")
+PROFILES = os.path.join(HERE, "profiles")
+FORMS = ("split_tf32", "split_bf16", "fp64_ozaki", "fp64")
+# tensor-core products executed per FP64-equivalent multiply-add, by form
+PRODUCTS = {"split_tf32": 3, "split_bf16": 6, "fp64_ozaki": 28, "fp64": 1}
+# arithmetic type of the contractions, by form
+DTYPE = {"split_tf32": "tf32", "split_bf16": "bf16", "fp64_ozaki": "bf16", "fp64": "f64"}
+KERNEL = {"split_tf32": ("tc_gemm_kernel", "gemm_tc.cu"),
+          "split_bf16": ("oz_gemm_kernel<3,64>", "gemm_oz.cu"),
+          "fp64_ozaki": ("oz_gemm_kernel<7,64>", "gemm_oz.cu"),
+          "fp64": ("gemm_kernel (FP64 DFMA)", "gemm_f64.cu")}
 
 
 def parse_args():
@@ -49,18 +62,23 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2_formaldehyde")
+    ap.add_argument("--workload", default="c5_esca_large")
+    ap.add_argument("--form", choices=FORMS, default="split_tf32",
+                    help="precision form of the headline line")
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)
+    ap.add_argument("--side-steps", type=int, default=2,
+                    help="timed steps of each other form on the headline inputs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-split", action="store_true", help="skip the split-TF32 and split-BF16 forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other forms")
     ap.add_argument("--no-ozaki", action="store_true", help="skip the emulated-FP64 form")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the FP64 c2 line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=16)
     ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="scaled",
                     help="scaled: small shapes, all three forms; c4: the production request "
-                         "shapes (O~U{4..24}, V~U{40..240}) with steps cut to U{4..16}, tensor-core forms only, "
-                         "autotuner off (serial and served runs on equal terms)")
+                         "shapes (O~U{4..24}, V~U{40..240}) with steps cut to U{4..16}, tensor-core "
+                         "forms only, autotuner off (serial and served runs on equal terms)")
     return ap.parse_args()
 
 
@@ -119,7 +137,7 @@ class ClockSampler:
             self.proc.kill()
         rows = list(csv.reader(io.StringIO(open(self.path).read())))
         os.unlink(self.path)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             if len(r) < 9:
@@ -127,6 +145,7 @@ class ClockSampler:
             try:
                 sm.append(float(r[1]))
                 mx.append(float(r[2]))
+                pw.append(float(r[3]))
             except ValueError:
                 continue
             for k, nm in enumerate(names):
@@ -135,7 +154,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": float(max(pw)) if pw else None}
 
 
 # ----------------------------------------------------------------- oracle timing
@@ -150,35 +170,56 @@ def oracle_micro_per_step(name, tol):
     return float(d[1:, 5].mean())
 
 
-def time_oracle_micro_iteration(p, dt, reps, warm, t_state=None):
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def time_oracle_micro_iteration(p, dt, reps, warm, t_state=None, threads=None):
     """Wall time of one oracle micro-iteration (residual + Eq. 9 update) on
-    the host cores; returns (mean seconds, threads used)."""
+    the host cores (all BLAS threads, or `threads`); returns (mean seconds,
+    threads used)."""
     from oracle import propagate as PR
     from oracle.spinexp import CoreHoleCCSD
     sysb = CoreHoleCCSD.from_problem(p.eps, p.L, p.nocc, p.core)
     D = sysb.diagonal()
     t = t_state if t_state is not None else [x + 1e-3 for x in sysb.zeros()]
     Rn = [r - d * x for r, d, x in zip(sysb.residual(t), D, t)]
-    times = []
-    for k in range(warm + reps):
-        t0 = time.perf_counter()
-        try:
-            PR.am_step(sysb.residual, D, t, Rn, dt, tol=0.0, max_micro=2)
-        except PR.NotConverged:
-            pass
-        if k >= warm:
-            times.append(time.perf_counter() - t0)
-    try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-    except Exception:
-        threads = os.cpu_count()
+
+    def run():
+        times = []
+        for k in range(warm + reps):
+            t0 = time.perf_counter()
+            try:
+                PR.am_step(sysb.residual, D, t, Rn, dt, tol=0.0, max_micro=2)
+            except PR.NotConverged:
+                pass
+            if k >= warm:
+                times.append(time.perf_counter() - t0)
+        return float(np.mean(times))
     # am_step with tol 0 and max_micro=2 evaluates exactly one residual (k=1)
     # plus two updates, then reports non-convergence
-    return float(np.mean(times)), int(threads)
+    if threads is None:
+        return run(), int(blas_threads())
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=threads):
+        return run(), int(threads)
 
 
-# ----------------------------------------------------------------- helpers
+def time_oracle_steps(p, dt, tol, nsteps):
+    """Wall time of whole oracle time steps (propagate from T(0) = 0)."""
+    from oracle import propagate as PR
+    from oracle.spinexp import CoreHoleCCSD
+    sysb = CoreHoleCCSD.from_problem(p.eps, p.L, p.nocc, p.core)
+    t0 = time.perf_counter()
+    out = PR.propagate(sysb, nsteps, dt, tol=tol, max_micro=50)
+    return time.perf_counter() - t0, int(np.sum(out["micro"]))
+
+
+# ----------------------------------------------------------------- peaks
 def measured_peaks():
     try:
         return json.load(open(MEASURED))
@@ -186,130 +227,219 @@ def measured_peaks():
         return {}
 
 
-def ladder_traffic_per_launch(profile=LADDER_PROFILE, source="gemm_f64.cu"):
-    """Per-launch DRAM bytes of a ladder kernel from its committed ncu summary,
-    valid only while the kernel source is unchanged."""
-    if not os.path.exists(profile):
-        return None
-    src = os.path.join(HERE, "paper_2301_04249_b300", "csrc", source)
-    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    vals = {}
-    for ln in open(profile):
-        if ":" in ln:
-            k, v = ln.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha1") != digest:
-        return None
+def matmul_tflops(torch, dev, dtype, n, reps, tf32=False, seconds=0.0):
+    """cuBLAS dense GEMM rate: best of `reps` (burst) and, with seconds > 0,
+    the mean of back-to-back GEMMs for that long (sustained)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
     try:
-        return float(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
-
-
-def fp64_dgemm_tflops(torch, dev):
-    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
-    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
-    for _ in range(2):
-        a @ b
-    torch.cuda.synchronize()
-    best = 1e9
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        a @ b
-        e1.record()
+        a = torch.randn(n, n, dtype=dtype, device=dev)
+        b = torch.randn(n, n, dtype=dtype, device=dev)
+        c = a @ b
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 1e3)
-    return 2 * 4096 ** 3 / best / 1e12
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        sustained = None
+        if seconds > 0:
+            k = max(1, int(seconds / best))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(k):
+                torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            sustained = 2 * n ** 3 * k / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b, c
+        torch.cuda.empty_cache()
+        return 2 * n ** 3 / best / 1e12, sustained
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def split_summary(split, args, fp64_value, world, C_fp64, peaks):
-    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of the
-    split-TF32 form measured on the same workload and step counts."""
-    if split is None:
-        return None
-    tm = split["tm"]
+def peaks_block(torch, dev):
+    """Measured BF16 (driver file), TF32 and FP64 (cuBLAS, measured here)."""
+    pk = measured_peaks()
+    tf32_b, tf32_s = matmul_tflops(torch, dev, torch.float32, 8192, 5, tf32=True, seconds=3.0)
+    fp64_b, _ = matmul_tflops(torch, dev, torch.float64, 8192, 2)
+    return {"bf16_tflops": pk.get("bf16_tflops"),
+            "bf16_tflops_sustained": pk.get("bf16_tflops_sustained"),
+            "hbm_gbs": pk.get("hbm_gbs"),
+            "tf32_tflops": tf32_b, "tf32_tflops_sustained": tf32_s, "fp64_tflops": fp64_b,
+            "source": "bf16 and HBM: MEASURED_PEAKS.json (driver); tf32 and fp64: cuBLAS "
+                      "torch.matmul 8192^3 measured in this run (tf32: best of 5 and 3 s back "
+                      "to back; fp64: best of 2)"}
+
+
+def peak_for(form, peaks, sustained=True):
+    """Tensor-core peak of a form's products: BF16 digit planes (split-BF16,
+    emulated FP64), TF32 (split-TF32) or the FP64 pipe (FP64)."""
+    if form in ("split_bf16", "fp64_ozaki"):
+        v = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops")
+        return v, "bf16_tflops_sustained (of measured)" if sustained else "bf16_tflops (of measured)"
+    if form == "split_tf32":
+        v = peaks.get("tf32_tflops_sustained" if sustained else "tf32_tflops")
+        return v, "tf32, cuBLAS measured in this run (of measured)"
+    return peaks.get("fp64_tflops"), "fp64, cuBLAS DGEMM measured in this run (of measured)"
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM traffic of a kernel from its committed ncu summary
+    (profiles/*.txt lines 'kernel_key: ...', 'kernel_source_sha1: ...',
+    'traffic_bytes_per_launch: ...'), valid only while the kernel source is
+    unchanged; returns (bytes, summary file) or (None, None)."""
+    for fn in sorted(os.listdir(PROFILES)) if os.path.isdir(PROFILES) else []:
+        vals = {}
+        for ln in open(os.path.join(PROFILES, fn)):
+            if ":" in ln and not ln.startswith("#"):
+                k, v = ln.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_key") != kernel_key:
+            continue
+        src = os.path.join(HERE, "paper_2301_04249_b300", "csrc", vals.get("kernel_source", ""))
+        if not os.path.exists(src):
+            continue
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+        if vals.get("kernel_source_sha1") != digest:
+            continue
+        try:
+            return float(vals["traffic_bytes_per_launch"]), fn
+        except (KeyError, ValueError):
+            continue
+    return None, None
+
+
+# ----------------------------------------------------------------- one form
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def precision_of(P, form):
+    return {"split_tf32": P.RTEOM_SPLIT_TF32, "split_bf16": P.RTEOM_SPLIT_BF16,
+            "fp64_ozaki": P.RTEOM_FP64_OZAKI, "fp64": P.RTEOM_FP64}[form]
+
+
+def pinned_problem(torch, p):
+    """The problem's host arrays in pinned memory (the caller's buffers)."""
+    def pin(a):
+        if a is None:
+            return None
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+    return pin(p.eps), pin(p.L), pin(p.t1_gs), pin(p.t2_gs)
+
+
+def run_form(torch, P, p, host, form, dt, warmup, steps, tol, max_micro, stream, world,
+             sampler=None, timing_mode=3):
+    """One context of `form` on the pinned host inputs: create, `warmup`
+    untimed steps, `steps` timed steps (each a propagate call returning its
+    C_n to the host), the spectrum, destroy.  Device time of the timed steps
+    by CUDA events on the context's stream; wall time of the whole sequence
+    for the end-to-end figure."""
+    h_eps, h_L, h_t1, h_t2 = host
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    w0 = time.perf_counter()
+    g = P.Propagator(h_eps, h_L, p.nocc, p.nvir, h_t1, h_t2, core=p.core,
+                     precision=precision_of(P, form), stream=stream)
+    setup_s = time.perf_counter() - w0
+    held = free0 - torch.cuda.mem_get_info()[0]
+    C_steps = []
+    for _ in range(warmup):
+        C_steps.append(g.propagate(1, dt, tol=tol, max_micro=max_micro)[-1])
+    info0 = g.info()
+    g.set_timing(timing_mode)
+    g.timing(reset=True)
+    l0 = g.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_timed")  # launch lists: --nvtx-include "bench_timed/"
+    e0.record(stream)
+    for _ in range(steps):
+        C_steps.append(g.propagate(1, dt, tol=tol, max_micro=max_micro)[-1])
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    elapsed = e0.elapsed_time(e1) / 1e3
+    info1 = g.info()
+    tm = g.timing()
+    launches = g.kernel_launches() - l0
+    C, _ = g.cumulant()
+    omega = np.linspace(-25.0, -15.0, 2001)
+    A = g.spectrum(omega, 0.05)
+    g.close()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    h2d = sum(x.nbytes for x in host if x is not None) + omega.nbytes
+    return dict(form=form, setup_s=setup_s, device_bytes_held=held, elapsed=elapsed,
+                micro=info1["micro"] - info0["micro"], steps=steps, warmup=warmup, tm=tm,
+                launches=launches, C=C, wall=wall, h2d=h2d, d2h=16 * (warmup + steps) + A.nbytes,
+                clocks=clocks)
+
+
+def form_summary(r, peaks, world):
+    """Per-form figures: steps/s, per micro-iteration, and the roofline of the
+    form's contraction kernel over every contraction launch of the timed steps
+    (event nodes inside the residual graphs)."""
+    form = r["form"]
+    tm = r["tm"]
+    steps, micro, el = r["steps"], max(r["micro"], 1), r["elapsed"]
+    con = {k: tm["ladder"][k] + tm["contract"][k] for k in ("ms", "launches", "flops", "bytes")}
+    eq_flops = sum(v["flops"] for v in tm.values())
+    prod = PRODUCTS[form]
+    gemm_s = con["ms"] / 1e3
+    eq_rate = con["flops"] / gemm_s / 1e12 if gemm_s > 0 else None
+    peak, src = peak_for(form, peaks)
+    exe_rate = eq_rate * prod if eq_rate else None
     lad = tm["ladder"]
-    v = world * args.steps / split["elapsed"]
-    bf16 = peaks.get("bf16_tflops")
-    hbm = peaks.get("hbm_gbs")
-    tf32_peak = bf16 * TF32_PER_BF16_NOMINAL if bf16 else None
-    avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
-    fl = lad["flops"] / max(lad["launches"], 1)
-    by = lad["bytes"] / max(lad["launches"], 1)
-    ach = fl / avg_s / 1e12 if lad["launches"] else None
-    ach_gbs = by / avg_s / 1e9 if lad["launches"] else None
-    n = min(len(C_fp64), len(split["C"]))
-    dC = float(np.abs(np.asarray(split["C"])[:n] - np.asarray(C_fp64)[:n]).max())
-    return {"split_tf32": {
-        "value": v, "unit": UNIT, "ms_per_step": 1e3 * split["elapsed"] / args.steps,
-        "speedup_vs_fp64": v / fp64_value,
-        "micro_iterations_per_step": split["micro"] / args.steps,
-        "max_abs_dC_vs_fp64": dC,
-        "gpu_launches": split["launches"],
-        "roofline": {"bound": "hbm", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, ladder)",
-                     "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": ach_gbs / hbm if (ach_gbs and hbm) else None,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                     "traffic": ladder_traffic_per_launch(LADDER_TC_PROFILE, "gemm_tc.cu"),
-                     "bytes_per_launch": by, "avg_launch_ms": avg_s * 1e3,
-                     "launches": lad["launches"],
-                     "tensor": {"achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                                "frac": ach / tf32_peak if (ach and tf32_peak) else None,
-                                "peak_source": "measured BF16 x nominal TF32/BF16 ratio",
-                                "flops_per_launch_executed": fl},
-                     "note": "bytes: packed hi/lo operands read once + FP32 split-K slabs; at "
-                             "this size 85 FLOP/B, below the TF32 ridge, so HBM binds; "
-                             "traffic is the alpha-beta launch (the largest), bytes_per_launch "
-                             "the mean over the three ladder launches of a residual"},
-    }}
-
-
-def ozaki_summary(run, args, fp64_value, world, C_fp64, peaks, name="fp64_ozaki", planes=7,
-                  profile=LADDER_OZ_PROFILE):
-    """Steps/s, speedup, cumulant deviation and tensor-pipe roofline of a
-    digit-sliced form (emulated FP64: 7 planes; split-BF16: 3 planes)
-    measured on the same workload and step counts."""
-    if run is None:
-        return None
-    products = planes * (planes + 1) // 2
-    lad = run["tm"]["ladder"]
-    v = world * args.steps / run["elapsed"]
-    bf16 = peaks.get("bf16_tflops")
-    avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
-    fl = lad["flops"] / max(lad["launches"], 1)  # FP64-equivalent
-    eq = fl / avg_s / 1e12 if lad["launches"] else None
-    ach = products * eq if eq else None
-    n = min(len(C_fp64), len(run["C"]))
-    Cf = np.asarray(C_fp64)[:n]
-    dC = float(np.abs(np.asarray(run["C"])[:n] - Cf).max())
-    return {name: {
-        "value": v, "unit": UNIT, "ms_per_step": 1e3 * run["elapsed"] / args.steps,
-        "speedup_vs_fp64": v / fp64_value,
-        "micro_iterations_per_step": run["micro"] / args.steps,
-        "max_abs_dC_vs_fp64": dC,
-        "max_rel_dC_vs_fp64": dC / max(float(np.abs(Cf).max()), 1e-300),
-        "gpu_launches": run["launches"],
-        "fp64_equivalent_tflops_total": sum(x["flops"] for x in run["tm"].values())
-                                       / run["elapsed"] / 1e12,
-        "roofline": {"bound": "tensor",
-                     "kernel": f"oz_gemm_kernel<{planes}> (tcgen05 kind::f16, BF16 digit planes, "
-                               "ladder)",
-                     "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                     "frac": ach / bf16 if (ach and bf16) else None,
-                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured, burst)",
-                     "fp64_equivalent_tflops": eq,
-                     "frac_of_fp64_nominal": eq / FP64_NOMINAL_TFLOPS if eq else None,
-                     "traffic": ladder_traffic_per_launch(profile, "gemm_oz.cu")
-                                if profile else None,
-                     "flops_per_launch_executed": products * fl,
-                     "avg_launch_ms": avg_s * 1e3, "launches": lad["launches"],
-                     "note": f"executed = {products} BF16 digit-pair products per "
-                             "FP64-equivalent multiply-add of the real-embedded GEMM; the mean "
-                             "is over the three ladder launches of a residual"}},
+    lad_s = lad["ms"] / 1e3
+    kname, ksrc = KERNEL[form]
+    traffic, tfile = ncu_traffic(f"{form}:contraction")
+    return {
+        "value": world * steps / el, "unit": UNIT, "ms_per_step": 1e3 * el / steps,
+        "micro_iterations_per_step": r["micro"] / steps,
+        "ms_per_micro_iteration": 1e3 * el / micro,
+        "setup_s": r["setup_s"], "device_bytes_held": r["device_bytes_held"],
+        "gpu_launches": r["launches"],
+        "fp64_equivalent_tflops_step": eq_flops / el / 1e12,
+        "fp64_equivalent_tflop_per_micro_iteration": eq_flops / micro / 1e12,
+        "contraction_time_share": gemm_s / el,
+        "roofline": {
+            "bound": "alu" if form == "fp64" else "tensor",
+            "kernel": kname + ", every contraction launch of the timed steps",
+            "achieved": exe_rate, "peak": peak, "unit": "TFLOP/s",
+            "frac": exe_rate / peak if (exe_rate and peak) else None,
+            "peak_source": src, "traffic": traffic, "traffic_source": tfile,
+            "fp64_equivalent_tflops": eq_rate,
+            "frac_of_fp64_peak": eq_rate / peaks["fp64_tflops"]
+            if (eq_rate and peaks.get("fp64_tflops")) else None,
+            "launches": con["launches"], "avg_launch_ms": con["ms"] / max(con["launches"], 1),
+            "flops_per_launch_fp64_equivalent": con["flops"] / max(con["launches"], 1),
+            "products_per_multiply_add": prod,
+            "note": "achieved = FP64-equivalent FLOPs of the contractions as posed on the "
+                    "slot spaces (2/4/8 per real/mixed/complex multiply-add, tile padding "
+                    "excluded) x the form's products per multiply-add / summed event time of "
+                    "the contraction launches (split-K finalizes and operand packs excluded)"},
+        "ladder": {"launches": lad["launches"], "ms": lad["ms"],
+                   "fp64_equivalent_tflops": lad["flops"] / lad_s / 1e12 if lad_s > 0 else None,
+                   "executed_tflops": lad["flops"] * prod / lad_s / 1e12 if lad_s > 0 else None},
     }
 
 
+# ----------------------------------------------------------------- serving
 def serving_mix(n_req, kind="scaled"):
     """Core-hole request mixes (seeds 4000 + r, dt = 0.025 au, Nchol = 4V).
     scaled: O ~ U{4..8}, V ~ U{20..48}, steps ~ U{20..80}.
@@ -337,7 +467,6 @@ def run_serving(P, precision, n_req, tol, kind="scaled"):
     reference measured on the same requests."""
     mix = serving_mix(n_req, kind)
     dt = 0.025
-    # serial reference: every request alone, back to back (also its service time)
     serial = []
     with P.Server(max_active=1, precision=precision) as s:
         for p, n in mix:
@@ -374,7 +503,36 @@ def run_serving(P, precision, n_req, tol, kind="scaled"):
             "mean_service_s": mean_service}
 
 
+def serving_block(P, args):
+    if args.no_serving:
+        return None
+    if args.serving_mix == "c4":
+        os.environ["RTEOM_AUTOTUNE"] = "0"
+        try:
+            return {"workload": f"c4 shapes: {args.serving_requests} requests, O~U{{4..24}}, "
+                                "V~U{40..240}, Nchol=4V, steps~U{4..16} (production: "
+                                "U{500..4000}), dt=0.025, Poisson arrivals at 2x the mean "
+                                "service rate, 8 slots, admission by device memory, autotuner off",
+                    "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
+                                              args.tol, "c4"),
+                    "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
+                                              args.tol, "c4")}
+        finally:
+            del os.environ["RTEOM_AUTOTUNE"]
+    return {"workload": "scaled core-hole mix: 16 requests, O~U{4..8}, V~U{20..48}, "
+                        "Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x the "
+                        "mean service rate, 8 slots",
+            "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
+            "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests, args.tol),
+            "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests, args.tol)}
+
+
 # ----------------------------------------------------------------- our arm
+def describe(name, p, dt, tol, form=None):
+    s = f"{name}: O={p.nocc} V={p.nvir} Nchol={p.nchol} dt={dt} tol={tol:g}"
+    return s + (f" form={form}" if form else "")
+
+
 def run_ours(args):
     import torch
     import paper_2301_04249_b300 as P
@@ -385,182 +543,110 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
     p, run = workload(args.workload)
     dt = run["dt"]
-    stream = torch.cuda.Stream(device=dev)
-    g = P.Propagator.from_problem(p, stream=stream)
-    g.propagate(args.warmup, dt, tol=args.tol, max_micro=args.max_micro)
-    info0 = g.info()
-    g.set_timing(True)
-    g.timing(reset=True)
-    launches0 = g.kernel_launches()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
+    host = pinned_problem(torch, p)
     sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("bench_timed")  # launch lists: --nvtx-include "bench_timed/"
-    e0.record(stream)
-    g.propagate(args.steps, dt, tol=args.tol, max_micro=args.max_micro)
-    e1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    elapsed = max_over_ranks(elapsed, world, dev)
-    info1 = g.info()
-    tm = g.timing()
-    launches = g.kernel_launches() - launches0
-    micro = info1["micro"] - info0["micro"]
-    state = g.get_state(with_history=False)["t"]
-    fp64_hist, _ = g.cumulant()
-    g.close()
+    head = run_form(torch, P, p, host, args.form, dt, args.warmup, args.steps, args.tol,
+                    args.max_micro, stream, world, sampler=sampler)
+    elapsed = max_over_ranks(head["elapsed"], world, dev)
+    e2e_wall = max_over_ranks(head["wall"], world, dev)
 
-    # end to end through the public API from pinned host buffers
-    def pinned(a):
-        if a is None:
-            return None
-        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
-        t.numpy()[...] = a
-        return t.numpy()
-    h_eps, h_L, h_t1, h_t2 = pinned(p.eps), pinned(p.L), pinned(p.t1_gs), pinned(p.t2_gs)
-    omega = pinned(np.linspace(-25.0, -15.0, 2001))
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    g2 = P.Propagator(h_eps, h_L, p.nocc, p.nvir, h_t1, h_t2, core=p.core, stream=stream)
-    Cs = [g2.propagate(1, dt, tol=args.tol, max_micro=args.max_micro)[-1] for _ in range(args.steps)]
-    A = g2.spectrum(omega, 0.05)
-    g2.close()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - w0
-    h2d = sum(x.nbytes for x in (h_eps, h_L, h_t1, h_t2, omega) if x is not None)
-    d2h = 16 * 2 * args.steps + A.nbytes
-    e2e_s = max_over_ranks(e2e_s, world, dev)
-
-    # the other precision forms on the same inputs, same step counts
-    def run_form(prec):
-        gs = P.Propagator.from_problem(p, stream=stream, precision=prec)
-        gs.propagate(args.warmup, dt, tol=args.tol, max_micro=args.max_micro)
-        i0 = gs.info()
-        gs.set_timing(True)
-        gs.timing(reset=True)
-        l0 = gs.kernel_launches()
-        barrier()
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        gs.propagate(args.steps, dt, tol=args.tol, max_micro=args.max_micro)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        el_s = f0.elapsed_time(f1) / 1e3
-        tms = gs.timing()
-        i1 = gs.info()
-        Cf, _ = gs.cumulant()
-        nl = gs.kernel_launches() - l0
-        gs.close()
-        return dict(elapsed=el_s, tm=tms, micro=i1["micro"] - i0["micro"], C=Cf, launches=nl)
-
-    split = None if args.no_split else run_form(P.RTEOM_SPLIT_TF32)
-    split_bf16 = None if args.no_split else run_form(P.RTEOM_SPLIT_BF16)
-    ozaki = None if args.no_ozaki else run_form(P.RTEOM_FP64_OZAKI)
+    # the other forms on the same inputs (first steps; per micro-iteration
+    # figures compare forms whatever the micro-iterations per step)
+    side = {}
+    if not args.no_forms:
+        others = [f for f in ("split_tf32", "split_bf16") if f != args.form]
+        if not args.no_ozaki and args.form != "fp64_ozaki":
+            others.append("fp64_ozaki")
+        for f in others:
+            n = 1 if f == "fp64_ozaki" else args.side_steps
+            side[f] = run_form(torch, P, p, host, f, dt, 0, n, args.tol, args.max_micro, stream,
+                               world)
+    # the formaldehyde-shaped workload in plain FP64 (the DFMA contraction
+    # rate also gives the FP64 form's estimate at the headline size)
+    sec = None
+    if not args.no_secondary:
+        p2, run2 = workload("c2_formaldehyde")
+        host2 = pinned_problem(torch, p2)
+        sec = run_form(torch, P, p2, host2, "fp64", run2["dt"], args.warmup, args.steps,
+                       args.tol, args.max_micro, stream, world)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
 
+    peaks = peaks_block(torch, dev)
     value = replica_throughput(args.steps, elapsed, world)
-    serving = None
-    if not args.no_serving and args.serving_mix == "c4":
-        os.environ["RTEOM_AUTOTUNE"] = "0"
-        serving = {"workload": f"c4 shapes: {args.serving_requests} requests, O~U{{4..24}}, "
-                               "V~U{40..240}, Nchol=4V, steps~U{4..16} (production: U{500..4000}), "
-                               "dt=0.025, Poisson arrivals at 2x the mean service rate, 8 slots, "
-                               "admission by device memory, autotuner off",
-                   "fp64": "not run: one FP64 residual of the largest request takes about 30 s",
-                   "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
-                                             args.tol, "c4"),
-                   "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
-                                             args.tol, "c4"),
-                   "fp64_ozaki": run_serving(P, P.RTEOM_FP64_OZAKI, args.serving_requests,
-                                             args.tol, "c4")}
-        del os.environ["RTEOM_AUTOTUNE"]
-    elif not args.no_serving:
-        serving = {"workload": "scaled core-hole mix: 16 requests, O~U{4..8}, V~U{20..48}, "
-                               "Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x the "
-                               "mean service rate, 8 slots",
-                   "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
-                   "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
-                                             args.tol),
-                   "fp64_ozaki": run_serving(P, P.RTEOM_FP64_OZAKI, args.serving_requests,
-                                             args.tol)}
-    lad = tm["ladder"]
-    peaks = measured_peaks()
-    dgemm = fp64_dgemm_tflops(torch, dev)
-    lad_avg_s = lad["ms"] / 1e3 / max(lad["launches"], 1)
-    lad_flops = lad["flops"] / max(lad["launches"], 1)
-    achieved = lad_flops / lad_avg_s / 1e12 if lad["launches"] else None
-    traffic = ladder_traffic_per_launch()
-    total_flops = sum(v["flops"] for v in tm.values())
-    roofline = {"bound": "alu", "kernel": "gemm_f64 (particle-particle ladder, FP64 DFMA)",
-                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
-                "peak_source": "B300 nominal FP64 (recipe table); cuBLAS DGEMM measured live below",
-                "cublas_dgemm_tflops_measured": dgemm,
-                "frac_of_cublas_dgemm": achieved / dgemm if achieved else None,
-                "flops_per_launch": lad_flops, "avg_launch_ms": lad_avg_s * 1e3,
-                "launches": lad["launches"], "traffic": traffic}
+    hs = form_summary(head, peaks, world)
+    forms = {f: form_summary(r, peaks, world) for f, r in side.items()}
+    for f, r in side.items():
+        n = min(len(r["C"]), len(head["C"]))
+        forms[f]["max_abs_dC_vs_headline"] = float(np.abs(r["C"][:n] - head["C"][:n]).max())
+        forms[f]["timed_steps"] = r["steps"]
+        forms[f]["ms_per_micro_iteration_vs_headline"] = (
+            forms[f]["ms_per_micro_iteration"] / hs["ms_per_micro_iteration"])
+    secondary = None
+    if sec is not None:
+        ss = form_summary(sec, peaks, world)
+        secondary = {"workload": describe("c2_formaldehyde", p2, run2["dt"], args.tol, "fp64"),
+                     **ss, "clocks": None}
+        # FP64 (DFMA) form at the headline size, from its contraction rate
+        dfma = ss["roofline"]["fp64_equivalent_tflops"]
+        per_micro = hs["fp64_equivalent_tflop_per_micro_iteration"]
+        if dfma:
+            est = per_micro / dfma
+            forms["fp64"] = {
+                "estimated": True, "s_per_micro_iteration": est,
+                "ms_per_micro_iteration_vs_headline": 1e3 * est / hs["ms_per_micro_iteration"],
+                "note": f"not run at this size: {per_micro:.3g} FP64-equivalent TFLOP per "
+                        f"micro-iteration / the {dfma:.3g} TFLOP/s the DFMA contractions "
+                        "reached on the c2 line"}
 
     cpu = None
-    m_ref = oracle_micro_per_step(args.workload, args.tol)
-    if not args.no_cpu_baseline:
-        blocks = P.split_blocks(state, p.nocc, p.nvir)
-        t_mi, threads = time_oracle_micro_iteration(p, dt, reps=1, warm=0, t_state=blocks)
-        m_use = m_ref if m_ref is not None else micro / args.steps
-        cpu = {"value": 1.0 / (t_mi * m_use), "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": (f"one oracle micro-iteration (residual + Eq. 9 update) of workload "
-                          f"{args.workload} timed on the host ({t_mi:.2f} s), scaled by "
-                          f"{m_use:.2f} micro-iterations per step "
-                          + ("(the oracle's own run at this tol)" if m_ref is not None
-                             else "(measured on the GPU run)")),
-               "micro_iteration_s": t_mi}
+    if not args.no_cpu_baseline and secondary is not None:
+        cpu = cpu_baseline_block(args, hs, secondary["fp64_equivalent_tflop_per_micro_iteration"])
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.form],
         "data": "synthetic (seeded; no molecular integrals available)",
-        "config": {"workload": f"{args.workload}: O={p.nocc} V={p.nvir} Nchol={p.nchol} "
-                               f"dt={dt} tol={args.tol} precision=FP64 complex",
+        "config": {"workload": describe(args.workload, p, dt, args.tol, args.form),
+                   "form": args.form,
+                   "arithmetic": "contractions as split products on the tensor cores with FP32 "
+                                 "accumulation; Adams-Moulton update, cumulant and phases FP64"
+                   if args.form in ("split_tf32", "split_bf16") else
+                   ("contractions FP64-accurate from BF16 digit planes" if args.form ==
+                    "fp64_ozaki" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent core holes, no collectives)",
-                   "l2": "inputs larger than L2: the (ae|bf) ladder block alone is "
-                         f"{8 * (p.nvir + 1) ** 4 / 1e9:.2f} GB",
-                   "flops_per_step_tflop": total_flops / args.steps / 1e12},
-        "micro_iterations_per_step": micro / args.steps,
-        "micro_iterations_per_s": world * micro / elapsed,
-        "tflops_fp64": total_flops / elapsed / 1e12,
-        "roofline": roofline,
+                   "l2": "inputs larger than L2: the amplitude sets alone are "
+                         f"{16 * 3 * (p.nocc * p.nocc * (p.nvir + 1) ** 2) / 1e9:.1f} GB",
+                   "steps_from": f"T(0) = 0; {args.warmup} untimed steps, then {args.steps} "
+                                 "timed steps, each returning C_n to the host"},
+        "micro_iterations_per_step": hs["micro_iterations_per_step"],
+        "ms_per_micro_iteration": hs["ms_per_micro_iteration"],
+        "fp64_equivalent_tflops": hs["fp64_equivalent_tflops_step"],
+        "roofline": hs["roofline"],
+        "ladder": hs["ladder"],
+        "setup_s": hs["setup_s"], "device_bytes_held": hs["device_bytes_held"],
         "cpu_baseline": cpu,
-        "e2e": {"value": replica_throughput(args.steps, e2e_s, world), "unit": UNIT,
-                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                "what": "rteom_create from pinned host arrays + per-step rteom_propagate(1) "
-                        "returning C_n + rteom_spectrum + destroy, wall clock"},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "forms": {**(split_summary(split, args, value, world, fp64_hist, peaks) or {}),
-                  **(ozaki_summary(split_bf16, args, value, world, fp64_hist, peaks,
-                                   "split_bf16", 3, LADDER_OZ3_PROFILE) or {}),
-                  **(ozaki_summary(ozaki, args, value, world, fp64_hist, peaks) or {})},
-        "serving": serving,
-        "measured_peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+        "e2e": {"value": replica_throughput(args.warmup + args.steps, e2e_wall, world),
+                "unit": UNIT,
+                "h2d_bytes_per_step": head["h2d"] / (args.warmup + args.steps),
+                "d2h_bytes_per_step": head["d2h"] / (args.warmup + args.steps),
+                "what": "rteom_create from pinned host arrays + every step through "
+                        "rteom_propagate(1) returning its C_n + rteom_spectrum + destroy, wall "
+                        "clock over all warm-up and timed steps"},
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "peaks": peaks,
+        "forms": forms,
+        "secondary": secondary,
+        "serving": serving_block(P, args),
     }
     print(json.dumps(res), flush=True)
     if world > 1:
@@ -568,27 +654,57 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def cpu_baseline_block(args, hs, c2_tflop_per_micro):
+    """The oracle on the host cores: one micro-iteration of the
+    formaldehyde-shaped workload (the oracle cannot hold a residual of the
+    headline size in host memory), scaled to the headline workload by the
+    ratio of FP64-equivalent FLOPs per micro-iteration (both counted by the
+    library on its own runs)."""
+    p2, run2 = workload("c2_formaldehyde")
+    t_mi, threads = time_oracle_micro_iteration(p2, run2["dt"], reps=1, warm=0)
+    scale = hs["fp64_equivalent_tflop_per_micro_iteration"] / c2_tflop_per_micro
+    m = hs["micro_iterations_per_step"]
+    est_step = t_mi * scale * m
+    return {"value": 1.0 / est_step, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one oracle micro-iteration of c2_formaldehyde (O=8 V=100 Nchol=400) on "
+                      f"the host ({t_mi:.2f} s), extrapolated to {args.workload} by the ratio of "
+                      f"FP64-equivalent FLOPs per micro-iteration ({scale:.3g}x) and "
+                      f"{m:.2f} micro-iterations per step: the oracle cannot hold a residual of "
+                      "this size in host memory",
+            "micro_iteration_s_c2": t_mi, "extrapolated": True}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle on the host cores, timed on whole time steps of the
+    formaldehyde-shaped workload (O=8, V=100, Nchol=400; its largest
+    configuration that fits host memory), plus one micro-iteration on one
+    core; the headline size is given as a FLOP-scaled estimate."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    p, run = workload(args.workload)
-    m_ref = oracle_micro_per_step(args.workload, args.tol)
-    t_mi, threads = time_oracle_micro_iteration(p, run["dt"], reps=args.steps, warm=args.warmup)
-    m_use = m_ref if m_ref is not None else float("nan")
-    value = 1.0 / (t_mi * m_use)
-    sample = (f"each step: one oracle micro-iteration (residual + Eq. 9 update) of workload "
-              f"{args.workload} on the host cores ({t_mi:.2f} s mean over {args.steps}), scaled "
-              f"by the oracle's {m_use:.2f} micro-iterations per step at tol {args.tol:g}")
+    p, run = workload("c2_formaldehyde")
+    n = max(1, args.steps)
+    el, micro = time_oracle_steps(p, run["dt"], args.tol, n)
+    threads = int(blas_threads())
+    t1, _ = time_oracle_micro_iteration(p, run["dt"], reps=1, warm=0, threads=1)
+    value = n / el
+    sample = (f"whole oracle time steps of c2_formaldehyde (O=8 V=100 Nchol=400, dt "
+              f"{run['dt']}, tol {args.tol:g}) from T(0) = 0 on {threads} host threads: {n} "
+              f"steps, {micro} micro-iterations in {el:.1f} s; the oracle cannot hold a "
+              f"residual of {args.workload} in host memory; one micro-iteration on one core "
+              f"takes {t1:.1f} s")
     res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mi * m_use,
+           "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": f"{args.workload}: O={p.nocc} V={p.nvir} "
-                                                      f"Nchol={p.nchol} dt={run['dt']} tol={args.tol}"},
+           "data": "synthetic",
+           "config": {"workload": describe("c2_formaldehyde", p, run["dt"], args.tol),
+                      "headline_workload": args.workload},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                            "sample": sample},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                            "sample": sample, "one_core_micro_iteration_s": t1,
+                            "micro_iterations_per_step": micro / n},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
 
 

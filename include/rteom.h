@@ -243,22 +243,51 @@ int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, do
 int rteom_debug_residual(rteom_ctx* ctx, const double* t_in, double* R_out, double* E_out);
 
 /*
+ * rteom_debug_residual_sparse -- test entry point for problems whose
+ * amplitude vector is too large to pass through the host: the projections
+ * R_mu of Eqs. 7-8 at chosen entries, for amplitudes that are zero except
+ * at chosen entries (the context's state is not changed).
+ *  t_index, t_val, nt  host: nt flat complex indices into the amplitude
+ *                      vector (0 <= k < rteom_state_size/2) and their values
+ *                      (2*nt doubles, interleaved); every other amplitude is
+ *                      zero.  Entries of t2aa/t2bb must come with their
+ *                      antisymmetric partners (not checked).  Repeated
+ *                      indices: one of the values is kept.
+ *  r_index, nr, R_out  host: nr flat indices and the residual there
+ *                      (2*nr doubles)
+ * A residual depends on the orbitals its amplitudes touch: every summed
+ * index of a CCSD term sits on an amplitude.  So for amplitudes supported on
+ * a few orbitals the entries returned equal the residual of the problem cut
+ * down to those orbitals and the free ones, which tests compare with the
+ * oracle at full problem sizes.  Errors: RTEOM_ERR_ARG (an index outside the
+ * vector, missing arrays), RTEOM_ERR_NONFINITE, RTEOM_ERR_OOM,
+ * RTEOM_ERR_CUDA.
+ */
+int rteom_debug_residual_sparse(rteom_ctx* ctx, const long long* t_index, const double* t_val,
+                                long long nt, const long long* r_index, long long nr,
+                                double* R_out);
+
+/*
  * rteom_set_timing / rteom_get_timing -- per-kernel-class device timing with
  * CUDA events on the context's stream (0 = off, the default).  Classes:
  * 0 ladder contraction, 1 other contractions, 2 tensor permutes (and
  * tensor-core operand packing), 3 elementwise/update/energy.  get_timing
- * fills ms[4] (total milliseconds), launches[4] and flops[4] (FLOPs of the
- * launches: algorithmic for FP64 GEMMs, executed split products for
- * tensor-core GEMMs), bytes[4] (algorithmic DRAM bytes: operands read once,
+ * fills ms[4] (total milliseconds), launches[4] and flops[4] (FP64-equivalent
+ * algorithmic FLOPs of the launches: 2, 4 or 8 per real, mixed or complex
+ * multiply-add of each contraction as posed on the slot spaces; the split
+ * and emulated forms execute that many times the products per multiply-add
+ * on the tensor cores), bytes[4] (algorithmic DRAM bytes: operands read once,
  * outputs or split-K slabs written); any pointer may be NULL.  reset != 0
- * zeroes the counters after reading.  Inside the captured residual graphs only the
- * ladder launches carry event nodes, so ms[] of the other classes counts
- * only eagerly launched work (set-up, rteom_debug_residual); launches[] and
- * flops[] count every launch.  on = 2 runs the residuals of rteom_propagate
- * eagerly (no graphs, the same kernels) with an event pair around every
- * launch, so every class is timed; with the environment variable
- * RTEOM_TRACE=<file> each timed launch also appends one JSON line (class,
- * contraction, FLOPs, ms) to that file.
+ * zeroes the counters after reading.  Modes: on = 1 puts event nodes inside
+ * the captured residual graphs around the ladder launches only, so ms[] of
+ * the other classes counts only eagerly launched work (set-up,
+ * rteom_debug_residual); launches[] and flops[] count every launch.  on = 3
+ * puts event nodes around every contraction launch (classes 0 and 1).
+ * on = 2 runs the residuals of rteom_propagate eagerly (no graphs, the same
+ * kernels) with an event pair around every launch, so every class is timed;
+ * with the environment variable RTEOM_TRACE=<file> each timed launch also
+ * appends one JSON line (class, contraction, FLOPs, ms) to that file.
+ * Errors: RTEOM_ERR_ARG for a mode outside 0..3.
  */
 int rteom_set_timing(rteom_ctx* ctx, int on);
 int rteom_get_timing(rteom_ctx* ctx, double* ms, long long* launches, double* flops,

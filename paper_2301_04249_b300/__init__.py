@@ -161,10 +161,25 @@ class Propagator:
         self._check(self._lib.rteom_debug_residual(self._ctx, _ptr(t), _ptr(R), _ptr(E)))
         return split_blocks(R, self.nocc, self.nvir), complex(E[0], E[1])
 
+    def residual_sparse(self, t_index, t_val, r_index):
+        """Residual entries at flat indices r_index of the amplitude vector for
+        amplitudes zero except t_val at flat indices t_index (complex)."""
+        ti = np.ascontiguousarray(t_index, dtype=np.int64)
+        tv = np.ascontiguousarray(t_val, dtype=np.complex128).view(np.float64)
+        ri = np.ascontiguousarray(r_index, dtype=np.int64)
+        R = np.zeros(2 * ri.size)
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        self._check(self._lib.rteom_debug_residual_sparse(
+            self._ctx, ti.ctypes.data_as(llp), _ptr(tv), int(ti.size), ri.ctypes.data_as(llp),
+            int(ri.size), _ptr(R)))
+        return R.view(np.complex128)
+
     def set_timing(self, on):
-        """0/False off, 1/True on, 2 on with the residuals run outside graphs
-        (every launch timed)."""
-        on = 2 if on == 2 else int(bool(on))
+        """0/False off; 1/True on (event nodes around the ladder launches
+        inside the residual graphs); 2 on with the residuals run outside
+        graphs (every launch timed); 3 on with event nodes around every
+        contraction launch inside the graphs."""
+        on = int(on) if on in (2, 3) else int(bool(on))
         self._check(self._lib.rteom_set_timing(self._ctx, on))
 
     def timing(self, reset: bool = False):

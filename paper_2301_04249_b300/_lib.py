@@ -44,6 +44,8 @@ SIGNATURES = {
     "rteom_get_state": (ctypes.c_int, [_vp, _dp, _llp, _dp]),
     "rteom_set_state": (ctypes.c_int, [_vp, _dp, ctypes.c_longlong, _dp]),
     "rteom_debug_residual": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "rteom_debug_residual_sparse": (ctypes.c_int, [_vp, _llp, _dp, ctypes.c_longlong, _llp,
+                                                   ctypes.c_longlong, _dp]),
     "rteom_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rteom_get_timing": (ctypes.c_int, [_vp, _dp, _llp, _dp, _dp, ctypes.c_int]),
     "rteom_kernel_launches": (ctypes.c_longlong, [_vp]),

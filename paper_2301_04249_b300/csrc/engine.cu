@@ -522,6 +522,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   g.strideC = Mt * Nt;
   g.alpha = alpha;
   g.beta = bPC ? 0.0 : beta;
+  g.wait_cycles = tc_wait_cycles;
 
   // launch configuration from the autotuner, when it has one for this shape
   const bool tunable =
@@ -772,7 +773,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     // by the finalize) or the output written directly
     const double bytes = 8.0 * (double)(L.a_elems + L.b_elems) + 8.0 * (double)L.p_elems +
                          (L.ranges == 1 ? (C.cplx ? 16.0 : 8.0) * (double)Mt * Nt * Bt : 0.0);
-    launch(cls, 3.0 * flops,
+    launch(cls, flops,
            [&] {
              gemm_tc_mma(g, static_cast<float*>(pa.p0), static_cast<float*>(pa.p1),
                          static_cast<float*>(pb.p0), static_cast<float*>(pb.p1), P, tc_err, stream);

@@ -35,6 +35,10 @@ class Engine {
   bool tensor_cores = false;
   double tc_min_flops = 5e7;
   int* tc_err = nullptr;  // also collects timeouts of the emulated-FP64 kernel
+  // budget (clock cycles) of the MMA and epilogue waits of the tensor-core
+  // kernels; 0 = their default (about 2 s).  Tests shorten it to make the
+  // waits run out on purpose (failure detection without a GPU fault).
+  long long tc_wait_cycles = 0;
   // Digit slicing: contractions of at least oz_min_flops run as products of
   // oz_planes BF16 digit planes on the tensor cores (7 planes: FP64-level
   // accuracy; 3 planes: the split-BF16 form)
@@ -78,12 +82,15 @@ class Engine {
   long long tuned = 0;  // GEMM shapes this engine has tuned
 
   // Timing.  Eager launches are each bracketed by events.  While a residual
-  // graph is being captured (capturing == true) only launches of the class
-  // graph_timed_class get event-record nodes; their event pairs are kept in
-  // graph_pairs and read back after each replay with collect_graph_timing().
+  // graph is being captured (capturing == true) only launches of the classes
+  // in graph_timed_mask (bit 1 << class) get event-record nodes; their event
+  // pairs are kept in graph_pairs and read back after each replay with
+  // collect_graph_timing().  FLOP counters hold the FP64-equivalent
+  // algorithmic FLOPs of each contraction as posed (2, 4 or 8 per real,
+  // mixed or complex multiply-add), whatever the form executes.
   bool timing = false;
   bool capturing = false;
-  KernelClass graph_timed_class = kLadder;
+  unsigned graph_timed_mask = 1u << kLadder;
   struct GraphPair {
     cudaEvent_t a, b;
     KernelClass cls;
@@ -123,7 +130,7 @@ class Engine {
       return;
     }
     if (capturing) {  // event-record nodes only around the timed class
-      if (cls != graph_timed_class || !graph_pairs) {
+      if (!((graph_timed_mask >> cls) & 1u) || !graph_pairs) {
         if (graph_tally) {
           graph_tally->launches[cls] += 1;
           graph_tally->flops[cls] += flops;

@@ -294,6 +294,7 @@ struct KArgs {
   float2* P;                   // unscaled (sum, compensation) [batch*ranges][Mp][Np] when ranges > 1
   int Mp, Np;
   int* err;
+  long long wait;              // budget (clock cycles) of the MMA and epilogue waits
   double* C;
   bool cplx;
   int M, N, mode;              // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
@@ -316,14 +317,19 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
   constexpr int NBUF = CF::NBUF;
   uint64_t* acc_full = empty + STAGES;  // [NBUF]: chunk accumulated in set i
   uint64_t* acc_empty = acc_full + 2;   // [NBUF]: set i drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_done = acc_empty + 2;   // teardown: every issued MMA finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* issued = abort_flag + 1;
+  int* mmas = issued + 1;              // stages whose MMAs the issuer launched
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // output tiles on one grid axis (row tiles exceed 65535 for long M)
-  const int n_tiles = g.Np / BN;
-  const int n_tile = (int)(blockIdx.x % n_tiles), m_tile = (int)(blockIdx.x / n_tiles);
+  int m_tile, n_tile;
+  // rasterization groups of 8 row tiles: a 128-row A' tile carries twice
+  // the bytes of a 64-row B' tile, so 148 CTAs in flight cover about 8 row
+  // tiles and 18 column tiles
+  grouped_tile((int)blockIdx.x, g.Mp / BM, g.Np / BN, BN == 64 ? 8 : 12, &m_tile, &n_tile);
   const int z = blockIdx.z;
   const int b = z / g.ranges, rg = z % g.ranges;
   const int kt0 = rg * g.kpr;
@@ -340,8 +346,10 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], EPI_WARPS);
     }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     *issued = 0;
+    *mmas = 0;
     fence_mbar_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
@@ -355,9 +363,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     const __nv_bfloat16* B = g.B + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
     for (int k = 0; k < nk; ++k) {
       const int s = k % STAGES;
-      if (k >= STAGES && !mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
+      if (k >= STAGES && !mbar_wait_or_abort(&empty[s], ((k / STAGES) - 1) & 1, abort_flag)) {
+        if (!*(volatile int*)abort_flag) atomicExch(g.err, 11);
         *abort_flag = 1;
-        atomicExch(g.err, 11);
         break;
       }
       if (*(volatile int*)abort_flag) break;
@@ -382,19 +390,20 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       if (kin == 0 && j >= 1) {
         // chunk j reuses accumulator set j % NBUF once chunk j - NBUF drained
         const int jj = j - NBUF;
-        if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1)) {
+        if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1, g.wait)) {
           *abort_flag = 1;
           atomicExch(g.err, 14);
           break;
         }
       }
       const int s = k % STAGES;
-      if (!mbar_wait(&full[s], (k / STAGES) & 1)) {
+      if (!mbar_wait(&full[s], (k / STAGES) & 1, g.wait)) {
         *abort_flag = 1;
         atomicExch(g.err, 12);
         break;
       }
       tc_fence_after();
+      *mmas = k + 1;
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
       for (int sa = 0; sa < S; ++sa) {
@@ -423,8 +432,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
 #pragma unroll 1
     for (int j = 0; j < nchunks; ++j) {
       const int set = j % NBUF;
-      if (!mbar_wait(&acc_full[set], (j / NBUF) & 1)) {
+      if (!mbar_wait(&acc_full[set], (j / NBUF) & 1, g.wait)) {
         ok = false;
+        *abort_flag = 1;
         atomicExch(g.err, 13);
         break;
       }
@@ -487,12 +497,20 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       }
     }
   }
+  // teardown after an abandoned pipeline: let the issued copies land and the
+  // issued MMAs finish (bounded) before the tensor memory is freed
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && *abort_flag) {
-    const int n = *issued;
-    for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
-      mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+  if (*abort_flag) {
+    if (threadIdx.x == 0) {
+      const int n = *issued;
+      for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
+        mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+    }
+    if (warp == 1 && lane == 0 && *mmas > 0) {
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0);
+    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -727,6 +745,7 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.Mp = p.Mp;
   g.Np = p.Np;
   g.err = err;
+  g.wait = d.wait_cycles > 0 ? d.wait_cycles : tc5::kWaitCycles;
   g.C = d.C;
   g.cplx = d.Acplx || d.Bcplx;
   g.M = d.M;

@@ -46,6 +46,9 @@ constexpr uint32_t TILE_BYTES = TILE_ELEMS * 4;  // 16 KB
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int kSliceKt = 16;  // k-tiles per FP32 accumulation slice (512 of K)
+// row tiles per rasterization group: 148 CTAs in flight cover about 12 x 12
+// square 128 x 128 output tiles
+constexpr int kGroupM = 12;
 
 // Instruction descriptor of kind::tf32: F32 accumulator, TF32 A and B, both
 // K-major, N = bn, M = 128.
@@ -74,6 +77,7 @@ struct KArgs {
   int Mp, Np;        // padded extents of the partials
   uint32_t lbo, sbo;
   int* err;          // set to a non-zero code when a wait runs out
+  long long wait;    // budget (clock cycles) of the MMA and epilogue waits
   // output (single range): alpha*acc + beta*C into the FP64 output
   double* C;
   bool cplx;
@@ -93,14 +97,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;  // [2]: slice accumulated in buffer i
   uint64_t* acc_empty = acc_full + 2;   // [2]: buffer i drained by the epilogue
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_done = acc_empty + 2;   // teardown: every issued MMA finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* issued = abort_flag + 1;  // bulk-load stages issued by the producer
+  int* mmas = issued + 1;        // stages whose MMAs the issuer launched
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // output tiles on one grid axis (row tiles exceed 65535 for long M)
-  const int n_tiles = g.Np / BN;
-  const int n_tile = (int)(blockIdx.x % n_tiles), m_tile = (int)(blockIdx.x / n_tiles);
+  int m_tile, n_tile;
+  grouped_tile((int)blockIdx.x, g.Mp / BM, g.Np / BN, kGroupM, &m_tile, &n_tile);
   const int z = blockIdx.z;
   const int b = z / g.ranges, rg = z % g.ranges;
   const int kt0 = rg * g.kpr;
@@ -117,8 +123,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], EPI_WARPS);
     }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     *issued = 0;
+    *mmas = 0;
     fence_mbar_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
@@ -135,9 +143,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
     const float* Blo = g.Blo + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
     for (int k = 0; k < nk; ++k) {
       const int s = k % STAGES;
-      if (k >= STAGES && !mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
+      if (k >= STAGES && !mbar_wait_or_abort(&empty[s], ((k / STAGES) - 1) & 1, abort_flag)) {
+        if (!*(volatile int*)abort_flag) atomicExch(g.err, 1);
         *abort_flag = 1;
-        atomicExch(g.err, 1);
         break;
       }
       if (*(volatile int*)abort_flag) break;
@@ -157,19 +165,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
     for (int k = 0; k < nk; ++k) {
       const int j = k / kSliceKt, kin = k % kSliceKt, buf = j & 1;
       if (kin == 0 && j >= 2) {
-        if (!mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1)) {
+        if (!mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1, g.wait)) {
           *abort_flag = 1;
           atomicExch(g.err, 4);
           break;
         }
       }
       const int s = k % STAGES;
-      if (!mbar_wait(&full[s], (k / STAGES) & 1)) {
+      if (!mbar_wait(&full[s], (k / STAGES) & 1, g.wait)) {
         *abort_flag = 1;
         atomicExch(g.err, 2);
         break;
       }
       tc_fence_after();
+      *mmas = k + 1;
       const uint32_t dt = tmem + (uint32_t)(buf * BN);
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
       const uint32_t a_hi = base, a_lo = base + A_BYTES;
@@ -201,8 +210,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
 #pragma unroll 1
     for (int j = 0; j < nslices; ++j) {
       const int buf = j & 1;
-      if (!mbar_wait(&acc_full[buf], (j >> 1) & 1)) {
+      if (!mbar_wait(&acc_full[buf], (j >> 1) & 1, g.wait)) {
         ok = false;
+        *abort_flag = 1;
         atomicExch(g.err, 3);
         break;
       }
@@ -256,13 +266,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
         dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
     }
   }
-  // teardown: if a stage was abandoned, let its copies land before exiting
+  // teardown after an abandoned pipeline: let the issued copies land and the
+  // issued MMAs finish (bounded) before the tensor memory is freed
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && *abort_flag) {
-    const int n = *issued;
-    for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
-      mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+  if (*abort_flag) {
+    if (threadIdx.x == 0) {
+      const int n = *issued;
+      for (int k = n > STAGES ? n - STAGES : 0; k < n; ++k)
+        mbar_wait(&full[k % STAGES], (k / STAGES) & 1);
+    }
+    if (warp == 1 && lane == 0 && *mmas > 0) {
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0);
+    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -418,7 +435,7 @@ __global__ void tc_finalize_kernel(FinArgs f, int batch) {
 
 constexpr int kBN = 128;
 constexpr int kStages = 3;
-constexpr size_t kSmemBytes = kStages * (2 * TILE_BYTES + 2 * (size_t)kBN * BK * 4) + 128;
+constexpr size_t kSmemBytes = kStages * (2 * TILE_BYTES + 2 * (size_t)kBN * BK * 4) + 256;
 
 inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -567,6 +584,7 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.lbo = 128;   // core matrices adjacent along K
   g.sbo = 1024;  // 8-row groups
   g.err = err;
+  g.wait = d.wait_cycles > 0 ? d.wait_cycles : tc5::kWaitCycles;
   g.C = d.C;
   g.cplx = d.Acplx || d.Bcplx;
   g.M = d.M;

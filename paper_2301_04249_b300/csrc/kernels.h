@@ -80,6 +80,10 @@ struct GemmDesc {
   // launch configuration chosen by the autotuner: tile index < gemm_f64_tiles()
   // and K slices; -1 / 0 = the shape heuristic
   int tile = -1, splits = 0;
+  // tensor-core paths only: clock-cycle budget of the waits of the MMA and
+  // epilogue warps on their pipeline barriers (0 = the default, about 2 s);
+  // a wait that runs out sets the error word and the CTA winds down
+  long long wait_cycles = 0;
 };
 // Number of K slices the kernel will use for this shape (1 = no split).
 int gemm_f64_splits(const GemmDesc& d);
@@ -248,6 +252,13 @@ void energy(const AmpGeom& g, const double* t, const double* ovov, const double*
 // blocks (pads zeroed), and the reverse.  O, V are the spatial counts.
 void pack_amplitudes(const AmpGeom& g, const double* unpadded, double* padded, cudaStream_t st);
 void unpack_amplitudes(const AmpGeom& g, const double* padded, double* unpadded, cudaStream_t st);
+// Sparse access by flat index k of the unpadded vector (0 <= k < unpadded
+// length, complex entries): padded[slot(k)] = val for each k, and
+// out[e] = padded[slot(idx[e])].  Indices are checked by the caller.
+void scatter_unpadded(const AmpGeom& g, const long long* idx, const double* val, int64_t n,
+                      double* padded, cudaStream_t st);
+void gather_unpadded(const AmpGeom& g, const double* padded, const long long* idx, int64_t n,
+                     double* out, cudaStream_t st);
 
 // ---- set-up (once per context) ----------------------------------------------
 // Slot-space Cholesky blocks from L [nchol][nb][nb]:

@@ -65,7 +65,8 @@ struct rteom_ctx {
   double* h_dots = nullptr;
   int and_count = 0;
   long long cache_plan_bytes = 0;  // tensor-core pack cache planned at set-up
-  bool graph_timed[2] = {false, false};            // captured with event-record nodes
+  // 0: captured without event nodes, else 1 + the engine's graph_timed_mask
+  unsigned graph_timed[2] = {0u, 0u};
   std::vector<Engine::GraphPair> graph_pairs[2];
   Engine::GraphTally graph_tally[2];
   int graph_pending[2] = {0, 0};                   // replays whose timing is not yet read
@@ -220,7 +221,8 @@ void run_residual(rteom_ctx* c, int which) {
     c->E.tuning = false;
     return;
   }
-  if (c->graph[which] && c->graph_timed[which] != c->E.timing) drop_graph(c, which);
+  const unsigned timed_key = c->E.timing ? 1u + c->E.graph_timed_mask : 0u;
+  if (c->graph[which] && c->graph_timed[which] != timed_key) drop_graph(c, which);
   if (!c->graph[which]) {
     long long before = c->E.launches;
     cudaGraph_t gr;
@@ -246,7 +248,7 @@ void run_residual(rteom_ctx* c, int which) {
     cudaError_t e = cudaGraphInstantiate(&c->graph[which], gr, 0);
     cudaGraphDestroy(gr);
     RT_CUDA(e);
-    c->graph_timed[which] = c->E.timing;
+    c->graph_timed[which] = timed_key;
     c->graph_kernels = c->E.launches - before;
     c->E.launches = before;
   }
@@ -428,6 +430,15 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   E.fp64_emulation = sliced;
   E.oz_planes = c->precision == RTEOM_SPLIT_BF16 ? 3 : 7;
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
+  if (const char* v = std::getenv("RTEOM_TEST_CONSUMER_WAIT_CYCLES")) {
+    // test hook: shortened MMA/epilogue waits of the tensor-core kernels
+    char* end = nullptr;
+    const long long w = std::strtoll(v, &end, 10);
+    if (end == v || *end != '\0' || w <= 0)
+      throw Error(RTEOM_ERR_ARG, std::string("RTEOM_TEST_CONSUMER_WAIT_CYCLES must be a positive "
+                                             "cycle count, got '") + v + "'");
+    E.tc_wait_cycles = w;
+  }
   if (const char* v = std::getenv("RTEOM_OZ_MIN_FLOPS")) E.oz_min_flops = std::atof(v);
   auto dry_peak = [&]() {
     E.dry = true;
@@ -1183,10 +1194,54 @@ int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double
   });
 }
 
+int rteom_debug_residual_sparse(rteom_ctx* c, const long long* t_index, const double* t_val,
+                                long long nt, const long long* r_index, long long nr,
+                                double* R_out) {
+  if (!c) return RTEOM_ERR_ARG;
+  if (nt < 0 || nr < 0 || (nt > 0 && (!t_index || !t_val)) || (nr > 0 && (!r_index || !R_out)))
+    return fail(c, RTEOM_ERR_ARG, "need nt, nr >= 0 and the index/value arrays they count");
+  const long long n = unpadded_size(c);
+  for (long long k = 0; k < nt; ++k)
+    if (t_index[k] < 0 || t_index[k] >= n)
+      return fail(c, RTEOM_ERR_ARG, "t_index[" + std::to_string(k) + "] outside the amplitude vector");
+  for (long long k = 0; k < nr; ++k)
+    if (r_index[k] < 0 || r_index[k] >= n)
+      return fail(c, RTEOM_ERR_ARG, "r_index[" + std::to_string(k) + "] outside the amplitude vector");
+  if (nt > 0 && !all_finite(t_val, 2 * (size_t)nt))
+    return fail(c, RTEOM_ERR_NONFINITE, "non-finite amplitude");
+  return guarded(c, [&] {
+    cudaStream_t st = c->stream;
+    long long* d_ti = nt ? reinterpret_cast<long long*>(c->dmalloc(8ull * nt)) : nullptr;
+    double* d_tv = nt ? c->dmalloc(16ull * nt) : nullptr;
+    long long* d_ri = nr ? reinterpret_cast<long long*>(c->dmalloc(8ull * nr)) : nullptr;
+    double* d_R = nr ? c->dmalloc(16ull * nr) : nullptr;
+    if (nt) {
+      RT_CUDA(cudaMemcpyAsync(d_ti, t_index, 8ull * nt, cudaMemcpyHostToDevice, st));
+      RT_CUDA(cudaMemcpyAsync(d_tv, t_val, 16ull * nt, cudaMemcpyHostToDevice, st));
+    }
+    if (nr) RT_CUDA(cudaMemcpyAsync(d_ri, r_index, 8ull * nr, cudaMemcpyHostToDevice, st));
+    RT_CUDA(cudaMemsetAsync(c->T_K, 0, 16ull * c->g.total(), st));
+    c->E.launch(kElementwise, 0.0, [&] { scatter_unpadded(c->g, d_ti, d_tv, nt, c->T_K, st); });
+    compute_residual(c->E, c->op, c->T_K, c->R_K);
+    c->E.launch(kElementwise, 0.0, [&] { gather_unpadded(c->g, c->R_K, d_ri, nr, d_R, st); });
+    if (nr) RT_CUDA(cudaMemcpyAsync(R_out, d_R, 16ull * nr, cudaMemcpyDeviceToHost, st));
+    RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
+    RT_CUDA(cudaStreamSynchronize(st));
+    for (void* p : {(void*)d_ti, (void*)d_tv, (void*)d_ri, (void*)d_R})
+      if (p) c->dfree(p);
+    if (c->E.timing) c->E.collect_timing();
+    if (c->h_maxdiff[1] != 0)
+      return fail(c, RTEOM_ERR_CUDA, "tensor-core pipeline wait timed out");
+    return RTEOM_OK;
+  });
+}
+
 int rteom_set_timing(rteom_ctx* c, int on) {
   if (!c) return RTEOM_ERR_ARG;
+  if (on < 0 || on > 3) return fail(c, RTEOM_ERR_ARG, "timing mode must be 0, 1, 2 or 3");
   c->E.timing = on != 0;
   c->eager_timing = on == 2;
+  c->E.graph_timed_mask = on == 3 ? (1u << kLadder) | (1u << kContract) : (1u << kLadder);
   return RTEOM_OK;
 }
 

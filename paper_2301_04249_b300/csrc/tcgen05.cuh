@@ -38,11 +38,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: true when the phase completed, false when the budget (clock
+// cycles) ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long budget = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+// Bounded wait that also gives up as soon as another warp of the CTA has
+// set *abort_flag (a pipeline stage it waits for will then never come).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   const int* abort_flag,
+                                                   long long budget = kWaitCycles) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(const volatile int*)abort_flag) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -125,6 +140,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Output tile (m, n) of CTA t on an m_tiles x n_tiles grid, visited in
+// groups of `group` row tiles with the row tile fastest inside a group: the
+// CTAs in flight then cover a few row tiles and a few column tiles, so the
+// k tiles they load at about the same time are shared through L2 instead of
+// each CTA streaming its own column tile from HBM.
+__device__ __forceinline__ void grouped_tile(int t, int m_tiles, int n_tiles, int group, int* m,
+                                             int* n) {
+  const int per_group = group * n_tiles;
+  const int g = t / per_group;
+  const int first = g * group;
+  const int gsz = min(group, m_tiles - first);
+  const int r = t - g * per_group;
+  *m = first + r % gsz;
+  *n = r / gsz;
 }
 
 }  // namespace tc5

@@ -646,6 +646,62 @@ __global__ void unpack_kernel(AmpGeom g, const double2* __restrict__ p, double2*
   }
 }
 
+// Padded index of the entry with flat index k of the unpadded spin-block
+// vector (the inverse of unpadded_index on real entries).
+__device__ __forceinline__ int64_t padded_of_unpadded(const AmpGeom& g, int64_t k) {
+  const int64_t oA = g.nO, vA = g.nV - 1, oB = g.nO - 1, vB = g.nV;
+  const int64_t n1a = oA * vA, n1b = oB * vB, n2aa = oA * oA * vA * vA, n2ab = oA * oB * vA * vB;
+  int blk = 0;
+  int64_t q = k;
+  if (q >= n1a) {
+    q -= n1a;
+    blk = 1;
+    if (q >= n1b) {
+      q -= n1b;
+      blk = 2;
+      if (q >= n2aa) {
+        q -= n2aa;
+        blk = 3;
+        if (q >= n2ab) {
+          q -= n2ab;
+          blk = 4;
+        }
+      }
+    }
+  }
+  const int si = spin_ia(blk), sj = spin_jb(blk);
+  auto occ_slot = [&](int s, int64_t i) -> int64_t { return (s && i >= g.core) ? i + 1 : i; };
+  auto vir_slot = [&](int s, int64_t a) -> int64_t { return s ? a : a + 1; };
+  const int64_t nva = si ? vB : vA, nvb = sj ? vB : vA, noj = sj ? oB : oA;
+  if (blk < 2) {
+    const int64_t i = q / nva, a = q % nva;
+    return g.off(blk) + occ_slot(si, i) * g.nV + vir_slot(si, a);
+  }
+  const int64_t b = q % nvb;
+  q /= nvb;
+  const int64_t a = q % nva;
+  q /= nva;
+  const int64_t j = q % noj, i = q / noj;
+  return g.off(blk) + ((occ_slot(si, i) * g.nO + occ_slot(sj, j)) * g.nV + vir_slot(si, a)) * g.nV +
+         vir_slot(sj, b);
+}
+
+__global__ void scatter_unpadded_kernel(AmpGeom g, const long long* __restrict__ idx,
+                                        const double2* __restrict__ val, int64_t n,
+                                        double2* __restrict__ padded) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    padded[padded_of_unpadded(g, idx[e])] = val[e];
+}
+
+__global__ void gather_unpadded_kernel(AmpGeom g, const double2* __restrict__ padded,
+                                       const long long* __restrict__ idx, int64_t n,
+                                       double2* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = padded[padded_of_unpadded(g, idx[e])];
+}
+
 // ---------------------------------------------------------------- set-up
 __device__ __forceinline__ int vmap(int a, int nO, int core) { return a == 0 ? core : nO + a - 1; }
 
@@ -965,6 +1021,22 @@ void energy(const AmpGeom& g, const double* t, const double* ovov, const double*
   energy_pass2<<<1, kThreads, 0, st>>>(reinterpret_cast<const double2*>(partial), np,
                                        reinterpret_cast<double2*>(E_hist),
                                        reinterpret_cast<double2*>(C_hist), n, dt, update_c);
+  RT_CHECK_LAUNCH();
+}
+
+void scatter_unpadded(const AmpGeom& g, const long long* idx, const double* val, int64_t n,
+                      double* padded, cudaStream_t st) {
+  if (n <= 0) return;
+  scatter_unpadded_kernel<<<grid_for(n, 1), kThreads, 0, st>>>(
+      g, idx, reinterpret_cast<const double2*>(val), n, reinterpret_cast<double2*>(padded));
+  RT_CHECK_LAUNCH();
+}
+
+void gather_unpadded(const AmpGeom& g, const double* padded, const long long* idx, int64_t n,
+                     double* out, cudaStream_t st) {
+  if (n <= 0) return;
+  gather_unpadded_kernel<<<grid_for(n, 1), kThreads, 0, st>>>(
+      g, reinterpret_cast<const double2*>(padded), idx, n, reinterpret_cast<double2*>(out));
   RT_CHECK_LAUNCH();
 }
 

@@ -3,4 +3,4 @@
 This package draws random numbers and nothing else of the propagation method:
 no Fock matrix, residual, integrator or cumulant arithmetic lives here.
 """
-from .generators import Problem, gen_problem, WORKLOADS, workload  # noqa: F401
+from .generators import Problem, gen_problem, random_amplitudes, WORKLOADS, workload  # noqa: F401

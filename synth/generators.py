@@ -103,3 +103,17 @@ def workload(name: str, **kw) -> tuple[Problem, dict]:
     nsteps, dt = w.pop("nsteps"), w.pop("dt")
     w.update(kw)
     return gen_problem(**w), dict(nsteps=nsteps, dt=dt)
+
+
+def random_amplitudes(shapes, seed: int, scale: float):
+    """Seeded random complex amplitude blocks [t1a, t1b, t2aa, t2ab, t2bb] with
+    the given shapes, entries scale * (N(0,1) + i N(0,1)); the same-spin T2
+    blocks (index 2 and 4) are made antisymmetric in (i,j) and in (a,b), the
+    layout the amplitude vector requires."""
+    rng = np.random.default_rng(seed)
+    t = [scale * (rng.standard_normal(s) + 1j * rng.standard_normal(s)) for s in shapes]
+    for k in (2, 4):
+        if len(t) > k:
+            t[k] = t[k] - t[k].transpose(1, 0, 2, 3)
+            t[k] = t[k] - t[k].transpose(0, 1, 3, 2)
+    return t

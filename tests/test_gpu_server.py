@@ -6,6 +6,8 @@ import numpy as np
 import pytest
 
 import paper_2301_04249_b300 as P
+from oracle import propagate as PR
+from oracle.spinexp import CoreHoleCCSD
 from synth import gen_problem
 
 pytestmark = pytest.mark.gpu
@@ -19,13 +21,15 @@ def _mix():
     return [(gen_problem(O, V, N, seed), n) for O, V, N, seed, n in shapes]
 
 
-@pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_FP64_OZAKI])
+@pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16,
+                                       P.RTEOM_FP64_OZAKI])
 def test_result_identical_alone_and_in_the_mix(precision, monkeypatch):
     if precision == P.RTEOM_SPLIT_TF32:
         monkeypatch.setenv("RTEOM_TC_MIN_FLOPS", "0")   # small shapes on the tensor cores too
-    if precision == P.RTEOM_FP64_OZAKI:
+    if precision in (P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_BF16):
         monkeypatch.setenv("RTEOM_OZ_MIN_FLOPS", "0")
-    tol = 1e-8 if precision == P.RTEOM_SPLIT_TF32 else 1e-10  # split: ~1e-9 fixed-point floor
+    # split forms: ~1e-9 fixed-point floor of the packed amplitudes
+    tol = 1e-8 if precision in (P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16) else 1e-10
     jobs = _mix()
     alone = []
     for p, n in jobs:
@@ -122,6 +126,10 @@ def test_core_hole_sweep_matches_lone_propagations():
         assert np.array_equal(C, ref)
     assert not np.array_equal(res[0][2], res[1][2])  # the core holes differ
     assert st["done"] == len(cores) and st["failed"] == 0 and st["mem_in_use"] == 0
+    # and each core hole (valence holes included) against the oracle
+    for c, (_, _, C, _) in zip(cores, res):
+        ref = PR.propagate(CoreHoleCCSD.from_problem(p.eps, p.L, p.nocc, c), 20, DT, tol=1e-8)
+        assert np.abs(C - ref["C"]).max() <= 1e-10 * np.abs(ref["C"]).max(), c
 
 
 def test_sweep_with_a_core_outside_the_occupied_space_queues_nothing():

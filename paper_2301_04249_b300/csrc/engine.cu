@@ -691,6 +691,25 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                        (outcopy ? " pC" : "")
                  : std::string();
   if (cls == kLadder && !dry && !pack_only) nvtxRangePushA("rteom_ladder");
+  // RTEOM_NVTX_CONTRACT set: one NVTX range per contraction named after its
+  // spec ("c_imae_mbej2ijab" for "imae,mbej->ijab"), so that a profiler can
+  // select the launches of one contraction
+  static const bool nvtx_each = std::getenv("RTEOM_NVTX_CONTRACT") != nullptr;
+  const bool nvtx_here = nvtx_each && !dry && !pack_only;
+  if (nvtx_here) {
+    std::string nm = "c_";
+    for (const char* q = spec; *q; ++q) {
+      if (*q == ',') {
+        nm += '_';
+      } else if (q[0] == '-' && q[1] == '>') {
+        nm += '2';
+        ++q;
+      } else {
+        nm += *q;
+      }
+    }
+    nvtxRangePushA(nm.c_str());
+  }
   // packed operand of the tensor-core paths: from the cache, stored in it
   // (constant tensors during the cache fill), or packed into the arena
   auto operand = [&](const char* role, const Tensor& T, const Packed* cached, int64_t bytes0,
@@ -747,7 +766,61 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
     if (held) held_packs_[ck] = pk;
     return pk;
   };
-  if (!packed_path) {
+  // Complex x complex on the tensor cores as three real products (3M)
+  // instead of the four of the real embedding, for operands packed per call.
+  const bool use3m = packed_path && allow_3m && A.cplx && B.cplx && Bt == 1 && !pack_only &&
+                     !cA && !cB && !A.constant && !B.constant && !holdA && !holdB &&
+                     !held_.count(A.p) && !held_.count(B.p);
+  if (use3m) {
+    const GemmDesc d3 = use_oz && swap ? swapped(g) : g;
+    const GemmDesc r = gemm_3m_desc(d3);
+    const double flops3 = 0.75 * flops;  // three real products instead of four
+    if (use_tc) {
+      const TcLayout L = gemm_tc_layout(r);
+      const int64_t sa = L.a_elems / 3, sb = L.b_elems / 3;
+      float* ahi = reinterpret_cast<float*>(arena.alloc((4 * L.a_elems + 7) / 8));
+      float* alo = reinterpret_cast<float*>(arena.alloc((4 * L.a_elems + 7) / 8));
+      float* bhi = reinterpret_cast<float*>(arena.alloc((4 * L.b_elems + 7) / 8));
+      float* blo = reinterpret_cast<float*>(arena.alloc((4 * L.b_elems + 7) / 8));
+      float2* P = reinterpret_cast<float2*>(arena.alloc(L.p_elems));
+      for (int k = 0; k < 3; ++k) {
+        GemmDesc pk = d3;
+        pk.part_a = pk.part_b = k;
+        launch(kPermute, 0.0,
+               [&] {
+                 gemm_tc_pack_a(pk, ahi + k * sa, alo + k * sa, stream);
+                 gemm_tc_pack_b(pk, bhi + k * sb, blo + k * sb, stream);
+               },
+               trace_on() ? std::string("tc pack 3M ") + spec : std::string());
+      }
+      launch(cls, flops3,
+             [&] { gemm_tc_mma(r, ahi, alo, bhi, blo, P, tc_err, stream); }, label + " 3M",
+             8.0 * (double)(L.a_elems + L.b_elems) + 8.0 * (double)L.p_elems);
+      launch(kElementwise, 0.0, [&] { gemm_tc_combine_3m(d3, P, stream); }, "tc combine 3M");
+    } else {
+      const OzLayout L = gemm_oz_layout(r, oz_planes);
+      uint16_t* ap = reinterpret_cast<uint16_t*>(arena.alloc((2 * L.planes * L.a_elems + 7) / 8));
+      int* ae = reinterpret_cast<int*>(arena.alloc((4 * L.a_rows + 7) / 8));
+      uint16_t* bp = reinterpret_cast<uint16_t*>(arena.alloc((2 * L.planes * L.b_elems + 7) / 8));
+      int* be = reinterpret_cast<int*>(arena.alloc((4 * L.b_rows + 7) / 8));
+      float2* P = reinterpret_cast<float2*>(arena.alloc(L.p_elems));
+      for (int k = 0; k < 3; ++k) {
+        GemmDesc pk = d3;
+        pk.part_a = pk.part_b = k;
+        launch(kPermute, 0.0,
+               [&] {
+                 gemm_oz_pack_a(pk, oz_planes, ap, ae, stream, k, 3);
+                 gemm_oz_pack_b(pk, oz_planes, bp, be, stream, k, 3);
+               },
+               trace_on() ? std::string("oz pack 3M ") + spec : std::string());
+      }
+      launch(cls, flops3,
+             [&] { gemm_oz_mma(r, oz_planes, ap, ae, bp, be, P, tc_err, stream); }, label + " 3M",
+             2.0 * L.planes * (double)(L.a_elems + L.b_elems) + 8.0 * (double)L.p_elems);
+      launch(kElementwise, 0.0, [&] { gemm_oz_combine_3m(d3, oz_planes, ae, be, P, stream); },
+             "oz combine 3M");
+    }
+  } else if (!packed_path) {
     const int64_t w = gemm_f64_workspace(g);
     if (w) g.work = arena.alloc(w);
     // operands read once, output written (or slabs written and read back)
@@ -821,6 +894,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
              "oz finalize");
   }
   if (outcopy) axpy((batch + bM + bN + "->" + p.c).c_str(), 1.0, Cuse, beta, C);
+  if (nvtx_here) nvtxRangePop();
   if (cls == kLadder && !dry) nvtxRangePop();
   if (dry && std::getenv("RTEOM_PLAN_TRACE"))  // scratch planning: arena top inside this call
     std::fprintf(stderr,

@@ -44,6 +44,8 @@ class Engine {
   // accuracy; 3 planes: the split-BF16 form)
   bool fp64_emulation = false;
   int oz_planes = 7;
+  // complex x complex products on the tensor cores as three real GEMMs (3M)
+  bool allow_3m = true;
   double oz_min_flops = 5e7;
   // Packed tensor-core operands of constant tensors, keyed by tensor, spec
   // and role.  Entries are created only while tc_cache_fill is set (an eager

@@ -116,6 +116,7 @@ struct PackArgs {
   int64_t s_r, s_c, s_b;  // element strides of logical rows, columns, batch
   int R, C;               // logical extents of the source operand (rows x K)
   int mode;               // 0 plain, 1 complex rows [Re; Im], 2 complex K [Re | Im], 3 complex B
+  int part;               // complex source read as one real part (0 re, 1 im, 2 re+im), or -1
   int Rp, Kp, rowtile;    // packed extents (rows multiple of rowtile, K of 32)
   __nv_bfloat16* planes;  // S planes of plane_elems
   int64_t plane_elems;
@@ -155,6 +156,10 @@ __device__ __forceinline__ double embedded(const PackArgs& p, int b, int rp, int
   if (!valid) return 0.0;
   const int64_t off = b * p.s_b + (p.view.rdims ? view_row(p.view, r) + view_col(p.view, c)
                                                  : r * p.s_r + c * p.s_c);
+  if (p.part >= 0) {
+    const double* q = p.src + 2 * off;
+    return p.part == 2 ? q[0] + q[1] : q[p.part];
+  }
   const double x = p.cplx ? p.src[2 * off + part] : p.src[off];
   return neg ? neg_f64(x) : x;
 }
@@ -292,6 +297,7 @@ struct KArgs {
   const int *ea, *eb;          // row scale exponents of A' [batch][Mp] and B' [batch][Np]
   int KT, kpr, ranges;
   float2* P;                   // unscaled (sum, compensation) [batch*ranges][Mp][Np] when ranges > 1
+  bool force_p;                // partials even with one range (3M products)
   int Mp, Np;
   int* err;
   long long wait;              // budget (clock cycles) of the MMA and epilogue waits
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     if (ok) {
       const int mr = m_tile * BM + row;
       const int er = row_exp(g.ea[(int64_t)b * g.Mp + mr]);
-      if (g.ranges == 1) {
+      if (g.ranges == 1 && !g.force_p) {
         int m = mr, part = 0;
         if (g.mode == 1 && mr >= g.M) {
           m = mr - g.M;
@@ -587,7 +593,7 @@ struct Plan {
 
 Plan plan(const GemmDesc& d, int S) {
   Plan p;
-  p.mode = (d.Acplx ? 1 : 0) + (d.Bcplx ? 2 : 0);
+  p.mode = (d.Acplx && d.part_a < 0 ? 1 : 0) + (d.Bcplx && d.part_b < 0 ? 2 : 0);
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
@@ -619,8 +625,38 @@ Plan plan(const GemmDesc& d, int S) {
   }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
-  p.p_elems = p.ranges == 1 ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
+  p.p_elems = (p.ranges == 1 && !d.force_partials) ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
   return p;
+}
+
+// 3M combine of the digit-plane products: P holds [3][ranges][Mp][Np]
+// unscaled pairs, product b scaled by the row exponents ea[b][m], eb[b][n]
+// of its packed operands; C = alpha (P1 - P2 + i (P3 - P1 - P2)) + beta C.
+__global__ void oz_combine_3m_kernel(FinArgs f) {
+  const int64_t per = (int64_t)f.M * f.N;
+  const int64_t zs = (int64_t)f.Mp * f.Np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / f.N), n = (int)(e % f.N);
+    double v[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+      float su = 0.0f, cm = 0.0f;
+      for (int z = 0; z < f.ranges; ++z) {
+        const float2 q = pp[z * zs];
+        two_sum_acc(su, cm, q.x);
+        cm += q.y;
+      }
+      v[b] = scaled_value(su, cm, row_exp(f.ea[(int64_t)b * f.Mp + m]),
+                          row_exp(f.eb[(int64_t)b * f.Np + n]));
+    }
+    const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
+    double* c = f.C + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+    const double a = f.alpha;
+    c[0] = f.beta == 0.0 ? a * re : (f.beta == 1.0 ? c[0] + a * re : fma(f.beta, c[0], a * re));
+    c[1] = f.beta == 0.0 ? a * im : (f.beta == 1.0 ? c[1] + a * im : fma(f.beta, c[1], a * im));
+  }
 }
 
 int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
@@ -672,7 +708,8 @@ void gemm_oz_init() {
   set(oz::oz_gemm_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
 }
 
-void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st) {
+void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
+                    int slot, int nslots) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d, S);
   oz::PackArgs pa{};
@@ -684,20 +721,22 @@ void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaS
   pa.R = d.M;
   pa.C = d.K;
   pa.mode = p.mode == 1 ? 1 : (p.mode == 3 ? 2 : 0);
+  pa.part = d.Acplx ? d.part_a : -1;
   pa.Rp = p.Mp;
   pa.Kp = p.Kp;
   pa.rowtile = oz::BM;
-  pa.planes = reinterpret_cast<__nv_bfloat16*>(planes);
-  pa.plane_elems = p.a_elems;
   pa.s_out = (int64_t)p.Mp * p.Kp;
-  pa.expo = expo;
+  pa.planes = reinterpret_cast<__nv_bfloat16*>(planes) + (int64_t)slot * pa.s_out * d.batch;
+  pa.plane_elems = p.a_elems * nslots;
+  pa.expo = expo + (int64_t)slot * p.Mp * d.batch;
   pa.view = d.va;
   pa.rows_fast = d.va.rdims ? (d.va.rstr[d.va.rdims - 1] == 1 && d.va.kstr[d.va.kdims - 1] != 1)
                             : (pa.s_r == 1 && pa.s_c != 1);
   oz::pack(pa, p.a_elems, d.batch, S, st);
 }
 
-void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st) {
+void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
+                    int slot, int nslots) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d, S);
   oz::PackArgs pb{};
@@ -709,13 +748,14 @@ void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaS
   pb.R = d.N;
   pb.C = d.K;
   pb.mode = p.mode == 2 ? 1 : (p.mode == 3 ? 3 : 0);
+  pb.part = d.Bcplx ? d.part_b : -1;
   pb.Rp = p.Np;
   pb.Kp = p.Kp;
   pb.rowtile = p.bn;
-  pb.planes = reinterpret_cast<__nv_bfloat16*>(planes);
-  pb.plane_elems = p.b_elems;
   pb.s_out = (int64_t)p.Np * p.Kp;
-  pb.expo = expo;
+  pb.planes = reinterpret_cast<__nv_bfloat16*>(planes) + (int64_t)slot * pb.s_out * d.batch;
+  pb.plane_elems = p.b_elems * nslots;
+  pb.expo = expo + (int64_t)slot * p.Np * d.batch;
   pb.view = d.vb;
   pb.rows_fast = d.vb.rdims ? (d.vb.rstr[d.vb.rdims - 1] == 1 && d.vb.kstr[d.vb.kdims - 1] != 1)
                             : (pb.s_r == 1 && pb.s_c != 1);
@@ -742,6 +782,7 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.kpr = p.kpr;
   g.ranges = p.ranges;
   g.P = P;
+  g.force_p = d.force_partials;
   g.Mp = p.Mp;
   g.Np = p.Np;
   g.err = err;
@@ -773,7 +814,7 @@ void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, co
                       cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const oz::Plan p = oz::plan(d, S);
-  if (p.ranges == 1) return;
+  if (p.ranges == 1 && !d.force_partials) return;
   oz::FinArgs fa{};
   fa.P = P;
   fa.ea = ea;
@@ -792,6 +833,29 @@ void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, co
   fa.alpha = d.alpha;
   fa.beta = d.beta;
   oz::oz_finalize_kernel<<<oz::grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+void gemm_oz_combine_3m(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
+                        cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0) return;
+  const oz::Plan p = oz::plan(gemm_3m_desc(d), S);
+  oz::FinArgs fa{};
+  fa.P = P;
+  fa.ea = ea;
+  fa.eb = eb;
+  fa.Mp = p.Mp;
+  fa.Np = p.Np;
+  fa.ranges = p.ranges;
+  fa.M = d.M;
+  fa.N = d.N;
+  fa.C = d.C;
+  fa.cplx = true;
+  fa.ldm = d.transC ? 1 : d.ldc;
+  fa.ldn = d.transC ? d.ldc : 1;
+  fa.alpha = d.alpha;
+  fa.beta = d.beta;
+  oz::oz_combine_3m_kernel<<<oz::grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
   RT_CHECK_LAUNCH();
 }
 

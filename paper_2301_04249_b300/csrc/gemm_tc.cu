@@ -74,6 +74,7 @@ struct KArgs {
   int kpr;                             // k-tiles per K range
   int ranges;                          // K ranges (CTAs along K per tile)
   float2* P;         // (sum, compensation) partials [batch*ranges][Mp][Np] when ranges > 1
+  bool force_p;      // partials even with one range (3M products)
   int Mp, Np;        // padded extents of the partials
   uint32_t lbo, sbo;
   int* err;          // set to a non-zero code when a wait runs out
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (ok && g.ranges == 1) {
+    if (ok && g.ranges == 1 && !g.force_p) {
       // map (row', col') of D = A'B'^T onto one real or imaginary part of C
       const int mr = m_tile * BM + row;
       int m = mr, part = 0;
@@ -296,6 +297,7 @@ struct PackArgs {
   int64_t s_r, s_c, s_b;  // element strides of logical rows, columns, batch
   int R, C;               // logical extents of the source operand (rows x K)
   int mode;               // see PackMode
+  int part;               // complex source read as one real part (0 re, 1 im, 2 re+im), or -1
   int Rp, Kp;             // packed (padded) extents: rows multiple of rowtile, K of 32
   int rowtile;            // 128 for A', BN for B'
   float *hi, *lo;
@@ -312,70 +314,110 @@ enum PackMode {
   kBcc = 3,         // complex B of a complex x complex product
 };
 
-template <typename IDX>
-__global__ void tc_pack_kernel(PackArgs p, int batch) {
-  const IDX per = (IDX)p.Rp * (IDX)p.Kp;
-  const int KT = p.Kp / BK;
-  const IDX n = per * (IDX)batch;
-  for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < n;
-       e += (IDX)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const IDX q = e - (IDX)b * per;
-    int rp, kp;
-    if (p.rows_fast) {
-      rp = (int)(q % (IDX)p.Rp);
-      kp = (int)(q / (IDX)p.Rp);
-    } else {
-      rp = (int)(q / (IDX)p.Kp);
-      kp = (int)(q % (IDX)p.Kp);
+// Value of the embedded real operand at packed (row rp, column kp), FP32.
+__device__ __forceinline__ float packed_value(const PackArgs& p, int b, int rp, int kp) {
+  int r = rp, c = kp, part = 0;
+  bool neg = false;
+  bool valid = true;
+  switch (p.mode) {
+    case kPlain:
+      valid = rp < p.R && kp < p.C;
+      break;
+    case kStackRows:
+      part = rp >= p.R;
+      r = rp - part * p.R;
+      valid = rp < 2 * p.R && kp < p.C;
+      break;
+    case kStackK:
+      part = kp >= p.C;
+      c = kp - part * p.C;
+      valid = rp < p.R && kp < 2 * p.C;
+      break;
+    default: {  // kBcc: rows n' (output columns), K' = [K | K]
+      const int ro = rp >= p.R, ko = kp >= p.C;
+      r = rp - ro * p.R;
+      c = kp - ko * p.C;
+      valid = rp < 2 * p.R && kp < 2 * p.C;
+      // [[Re, Im], [-Im, Re]] indexed by (k-half, n-half): part = Im when halves differ
+      part = ro != ko;
+      neg = ko && !ro;
     }
-    int r = rp, c = kp, part = 0;
-    bool neg = false;
-    bool valid = true;
-    switch (p.mode) {
-      case kPlain:
-        valid = rp < p.R && kp < p.C;
-        break;
-      case kStackRows:
-        part = rp >= p.R;
-        r = rp - part * p.R;
-        valid = rp < 2 * p.R && kp < p.C;
-        break;
-      case kStackK:
-        part = kp >= p.C;
-        c = kp - part * p.C;
-        valid = rp < p.R && kp < 2 * p.C;
-        break;
-      default: {  // kBcc: rows n' (output columns), K' = [K | K]
-        const int ro = rp >= p.R, ko = kp >= p.C;
-        r = rp - ro * p.R;
-        c = kp - ko * p.C;
-        valid = rp < 2 * p.R && kp < 2 * p.C;
-        // [[Re, Im], [-Im, Re]] indexed by (k-half, n-half): part = Im when halves differ
-        part = ro != ko;
-        neg = ko && !ro;
+  }
+  if (!valid) return 0.0f;
+  const int64_t off = b * p.s_b + (p.view.rdims ? view_row(p.view, r) + view_col(p.view, c)
+                                                 : r * p.s_r + c * p.s_c);
+  float xf;
+  if (p.part >= 0) {
+    const double* q = p.src + 2 * off;
+    xf = f64_to_f32(p.part == 2 ? q[0] + q[1] : q[p.part]);
+  } else {
+    xf = f64_to_f32(p.cplx ? p.src[2 * off + part] : p.src[off]);
+  }
+  return neg ? -xf : xf;
+}
+
+// x ~ hi + lo: hi = tf32(x), lo = tf32(x - hi) (the difference is exact in FP32)
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  uint32_t hb, lb;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(x));
+  hi = __uint_as_float(hb);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(x - hi));
+  lo = __uint_as_float(lb);
+}
+
+// Packed layout: tile (row tile rt, k tile kt) of rowtile x 32 is contiguous;
+// inside it the core matrix (8 rows x 4 k) of row group rr/8 and k quad kq
+// sits at ((rr/8)*8 + kq)*32 floats, row rr%8 at 4 floats: one thread writes
+// one 16-byte row of a core matrix.  A warp packs one block of 32 rows x 32 k
+// when the source rows are contiguous (lane = row: each load coalesced across
+// the warp), else one block of 8 rows x 32 k (lane = row r/8-th quarter and k
+// quad: each lane loads 4 consecutive k).
+__global__ void tc_pack_kernel(PackArgs p, int batch) {
+  const int KT = p.Kp / BK;
+  const int rows_per = p.rows_fast ? 32 : 8;
+  const int64_t groups = (int64_t)(p.Rp / rows_per) * KT;  // blocks per batch entry
+  const int64_t units = groups * batch;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < units; w += nwarps) {
+    const int b = (int)(w / groups);
+    const int64_t gq = w - (int64_t)b * groups;
+    const int rg = (int)(gq / KT), kt = (int)(gq % KT);
+    float* hi_t = p.hi + (int64_t)b * p.s_out;
+    float* lo_t = p.lo + (int64_t)b * p.s_out;
+    if (p.rows_fast) {
+      const int rp = rg * 32 + lane;
+      const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+      const int64_t tile = ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK);
+#pragma unroll 2
+      for (int kq = 0; kq < BK / 4; ++kq) {
+        float4 h, l;
+        tf32_split(packed_value(p, b, rp, kt * BK + kq * 4 + 0), h.x, l.x);
+        tf32_split(packed_value(p, b, rp, kt * BK + kq * 4 + 1), h.y, l.y);
+        tf32_split(packed_value(p, b, rp, kt * BK + kq * 4 + 2), h.z, l.z);
+        tf32_split(packed_value(p, b, rp, kt * BK + kq * 4 + 3), h.w, l.w);
+        const int64_t dst = tile + ((rr / 8) * 8 + kq) * 32 + (rr % 8) * 4;
+        *reinterpret_cast<float4*>(hi_t + dst) = h;
+        *reinterpret_cast<float4*>(lo_t + dst) = l;
+      }
+    } else {
+      const int kq = lane & 7;
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int rp = rg * 8 + pass * 4 + (lane >> 3);
+        const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+        const int k0 = kt * BK + kq * 4;
+        float4 h, l;
+        tf32_split(packed_value(p, b, rp, k0 + 0), h.x, l.x);
+        tf32_split(packed_value(p, b, rp, k0 + 1), h.y, l.y);
+        tf32_split(packed_value(p, b, rp, k0 + 2), h.z, l.z);
+        tf32_split(packed_value(p, b, rp, k0 + 3), h.w, l.w);
+        const int64_t dst = ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
+                            ((rr / 8) * 8 + kq) * 32 + (rr % 8) * 4;
+        *reinterpret_cast<float4*>(hi_t + dst) = h;
+        *reinterpret_cast<float4*>(lo_t + dst) = l;
       }
     }
-    float xf = 0.0f;
-    if (valid) {
-      const int64_t off = b * p.s_b + (p.view.rdims ? view_row(p.view, r) + view_col(p.view, c)
-                                                     : r * p.s_r + c * p.s_c);
-      xf = f64_to_f32(p.cplx ? p.src[2 * off + part] : p.src[off]);
-      if (neg) xf = -xf;
-    }
-    // x ~ hi + lo: hi = tf32(x), lo = tf32(x - hi) (the difference is exact in FP32)
-    uint32_t hb, lb;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xf));
-    const float hi = __uint_as_float(hb);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(xf - hi));
-    const float lo = __uint_as_float(lb);
-    // tiled core-matrix layout
-    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
-    const int kt = kp / BK, kk = kp % BK;
-    const int64_t dst = (int64_t)b * p.s_out + ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
-                        ((rr / 8) * 8 + kk / 4) * 32 + (rr % 8) * 4 + (kk % 4);
-    p.hi[dst] = hi;
-    p.lo[dst] = lo;
   }
 }
 
@@ -448,7 +490,7 @@ struct Plan {
 
 Plan plan(const GemmDesc& d) {
   Plan p;
-  p.mode = (d.Acplx ? 1 : 0) + (d.Bcplx ? 2 : 0);
+  p.mode = (d.Acplx && d.part_a < 0 ? 1 : 0) + (d.Bcplx && d.part_b < 0 ? 2 : 0);
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
@@ -476,8 +518,37 @@ Plan plan(const GemmDesc& d) {
   }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
-  p.p_elems = p.ranges == 1 ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
+  p.p_elems = (p.ranges == 1 && !d.force_partials) ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
   return p;
+}
+
+// 3M combine: P holds [3][ranges][Mp][Np] (sum, compensation) pairs of the
+// products P1 = Re A Re B, P2 = Im A Im B, P3 = (Re A + Im A)(Re B + Im B);
+// C = alpha (P1 - P2 + i (P3 - P1 - P2)) + beta C, the ranges summed in order.
+__global__ void tc_combine_3m_kernel(FinArgs f) {
+  const int64_t per = (int64_t)f.M * f.N;
+  const int64_t zs = (int64_t)f.Mp * f.Np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / f.N), n = (int)(e % f.N);
+    double v[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+      float s = 0.0f, cm = 0.0f;
+      for (int z = 0; z < f.ranges; ++z) {
+        const float2 q = pp[z * zs];
+        two_sum_acc(s, cm, q.x);
+        cm += q.y;
+      }
+      v[b] = f32_to_f64(s) + f32_to_f64(cm);
+    }
+    const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
+    double* c = f.C + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+    const double a = f.alpha;
+    c[0] = f.beta == 0.0 ? a * re : (f.beta == 1.0 ? c[0] + a * re : fma(f.beta, c[0], a * re));
+    c[1] = f.beta == 0.0 ? a * im : (f.beta == 1.0 ? c[1] + a * im : fma(f.beta, c[1], a * im));
+  }
 }
 
 }  // namespace tc
@@ -503,10 +574,10 @@ namespace {
 int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
 
 void launch_pack(const tc::PackArgs& pa, int64_t elems, int batch, cudaStream_t st) {
-  if (elems < (int64_t(1) << 32) - (int64_t)256 * 148 * 16)
-    tc::tc_pack_kernel<uint32_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
-  else
-    tc::tc_pack_kernel<uint64_t><<<grid_of(elems), 256, 0, st>>>(pa, batch);
+  // one warp per block of 32 x 32 (rows-fast) or 8 x 32 packed elements
+  const int64_t units = elems / (pa.rows_fast ? 1024 : 256);
+  const int grid = (int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16);
+  tc::tc_pack_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa, batch);
   RT_CHECK_LAUNCH();
 }
 }  // namespace
@@ -524,6 +595,7 @@ void gemm_tc_pack_a(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pa.R = d.M;
   pa.C = d.K;
   pa.mode = p.mode == 1 ? kStackRows : (p.mode == 3 ? kStackK : kPlain);
+  pa.part = d.Acplx ? d.part_a : -1;
   pa.Rp = p.Mp;
   pa.Kp = p.Kp;
   pa.rowtile = BM;
@@ -549,6 +621,7 @@ void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st) {
   pb.R = d.N;
   pb.C = d.K;
   pb.mode = p.mode == 2 ? kStackRows : (p.mode == 3 ? kBcc : kPlain);
+  pb.part = d.Bcplx ? d.part_b : -1;
   pb.Rp = p.Np;
   pb.Kp = p.Kp;
   pb.rowtile = kBN;
@@ -579,6 +652,7 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.kpr = p.kpr;
   g.ranges = p.ranges;
   g.P = P;
+  g.force_p = d.force_partials;
   g.Mp = p.Mp;
   g.Np = p.Np;
   g.lbo = 128;   // core matrices adjacent along K
@@ -604,7 +678,7 @@ void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st) {
   using namespace tc;
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
   const Plan p = plan(d);
-  if (p.ranges == 1) return;  // the MMA kernel wrote C directly
+  if (p.ranges == 1 && !d.force_partials) return;  // the MMA kernel wrote C directly
   FinArgs fa{};
   fa.P = P;
   fa.Mp = p.Mp;
@@ -621,6 +695,36 @@ void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st) {
   fa.alpha = d.alpha;
   fa.beta = d.beta;
   tc_finalize_kernel<<<grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
+  RT_CHECK_LAUNCH();
+}
+
+GemmDesc gemm_3m_desc(const GemmDesc& d) {
+  GemmDesc r = d;
+  r.part_a = 0;
+  r.part_b = 0;
+  r.batch = 3;
+  r.force_partials = true;
+  return r;
+}
+
+void gemm_tc_combine_3m(const GemmDesc& d, const float2* P, cudaStream_t st) {
+  using namespace tc;
+  if (d.M <= 0 || d.N <= 0) return;
+  const Plan p = plan(gemm_3m_desc(d));
+  FinArgs fa{};
+  fa.P = P;
+  fa.Mp = p.Mp;
+  fa.Np = p.Np;
+  fa.ranges = p.ranges;
+  fa.M = d.M;
+  fa.N = d.N;
+  fa.C = d.C;
+  fa.cplx = true;
+  fa.ldm = d.transC ? 1 : d.ldc;
+  fa.ldn = d.transC ? d.ldc : 1;
+  fa.alpha = d.alpha;
+  fa.beta = d.beta;
+  tc_combine_3m_kernel<<<grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
   RT_CHECK_LAUNCH();
 }
 

@@ -84,6 +84,13 @@ struct GemmDesc {
   // epilogue warps on their pipeline barriers (0 = the default, about 2 s);
   // a wait that runs out sets the error word and the CTA winds down
   long long wait_cycles = 0;
+  // tensor-core paths only: a complex operand enters as the real matrix of
+  // one of its parts (0 real, 1 imaginary, 2 real + imaginary) instead of its
+  // real embedding (-1).  The three products of the 3M complex GEMM use them.
+  int part_a = -1, part_b = -1;
+  // tensor-core paths only: write (sum, compensation) partials even with one
+  // K range per tile (the 3M combine reads them)
+  bool force_partials = false;
 };
 // Number of K slices the kernel will use for this shape (1 = no split).
 int gemm_f64_splits(const GemmDesc& d);
@@ -117,6 +124,15 @@ void gemm_tc_pack_b(const GemmDesc& d, float* hi, float* lo, cudaStream_t st);
 void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const float* Bhi,
                  const float* Blo, float2* P, int* err, cudaStream_t st);
 void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st);
+// Complex x complex GEMM of d (batch 1) as three real products (Gauss; error
+// analysis in Higham, SIAM J. Matrix Anal. Appl. 13, 1992): P1 = Re A Re B,
+// P2 = Im A Im B, P3 = (Re A + Im A)(Re B + Im B) run as one batch-3 real
+// GEMM (operands packed with part_a = part_b = 0, 1, 2 into consecutive batch
+// slots, partials forced), then C = alpha (P1 - P2 + i (P3 - P1 - P2)) +
+// beta C.  gemm_tc_3m_desc gives the batch-3 real GEMM whose layout sizes
+// the buffers.
+GemmDesc gemm_3m_desc(const GemmDesc& d);
+void gemm_tc_combine_3m(const GemmDesc& d, const float2* P, cudaStream_t st);
 
 // FP64-accurate GEMM on the BF16 tensor cores (operand slicing into seven
 // 8-bit digit planes with per-row power-of-two scales; exact chunk sums,
@@ -138,12 +154,19 @@ struct OzLayout {
 // of the row scales).
 OzLayout gemm_oz_layout(const GemmDesc& d, int S);
 void gemm_oz_init();
-void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st);
-void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st);
+// slot / nslots: pack into batch slot `slot` of a buffer laid out for
+// nslots batch entries of this (batch-1) operand (the 3M products).
+void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
+                    int slot = 0, int nslots = 1);
+void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
+                    int slot = 0, int nslots = 1);
 void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, const uint16_t* B,
                  const int* eb, float2* P, int* err, cudaStream_t st);
 void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
                       cudaStream_t st);
+// The 3M combine of the digit-plane form (row scales of each product applied).
+void gemm_oz_combine_3m(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
+                        cudaStream_t st);
 
 // out[o] = alpha * in[sum_k idx_k(o) * in_stride[k]] + beta * out[o]; out is
 // contiguous with dims out_dim[0..nd-1]; strides count elements.  A real
@@ -228,7 +251,7 @@ struct AmpGeom {
 
 // One Adams-Moulton micro-iteration (Eq. 9) over every element:
 // tk <- [(1 + i dt D/2) tn + (i dt/2)(Rn - D tn + Rk - D tk)] / (1 - i dt D/2),
-// pads forced to zero; *maxdiff_bits = max over elements of |new - old|
+// pads forced to zero; *maxdiff_bits = max over elements of |new - old|^2
 // (as IEEE bits of a non-negative double; NaN compares largest).
 // tk_in and tk_out may alias (in-place update).
 void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const double* fo_b,

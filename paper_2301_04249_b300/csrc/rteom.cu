@@ -430,6 +430,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   E.fp64_emulation = sliced;
   E.oz_planes = c->precision == RTEOM_SPLIT_BF16 ? 3 : 7;
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
+  if (const char* v = std::getenv("RTEOM_NO_3M")) E.allow_3m = std::atoi(v) == 0;
   if (const char* v = std::getenv("RTEOM_TEST_CONSUMER_WAIT_CYCLES")) {
     // test hook: shortened MMA/epilogue waits of the tensor-core kernels
     char* end = nullptr;
@@ -892,7 +893,7 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
                   "tensor-core pipeline wait timed out (code " +
                       std::to_string((long long)c->h_maxdiff[1]) + ")");
     }
-    const double d = bits_to_double(c->h_maxdiff[0]);
+    const double d = std::sqrt(bits_to_double(c->h_maxdiff[0]));  // the kernel keeps |.|^2
     if (!std::isfinite(d)) {
       r.phase = 2;
       return fail(c, RTEOM_ERR_NONFINITE,

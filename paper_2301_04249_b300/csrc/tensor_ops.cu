@@ -5,6 +5,7 @@
 // Every reduction is deterministic: fixed grids, fixed per-thread order,
 // shared-memory trees, and bitwise max for the convergence measure, so the
 // same inputs give the same bits whatever else runs on the GPU.
+#include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -86,6 +87,70 @@ __global__ void permute_kernel(const double* __restrict__ in, double* __restrict
     } else {
       const double c = rd ? out[o] : 0.0;
       out[o] = axop(op, in[off], c, alpha, beta);
+    }
+  }
+}
+
+// Permutes whose output's innermost index is strided in the input while
+// another output index is the input's unit-stride one: a 32 x 32 tile of
+// (x = output innermost, y = that index) goes through shared memory, read
+// along y and written along x, so both sides stay coalesced.  The remaining
+// indices ("rest") are walked by blockIdx.y.
+struct TileDesc {
+  int64_t X, Y;             // extents of the x and y indices
+  int64_t in_sx;            // input stride of x (that of y is 1)
+  int64_t out_sy;           // output stride of y (that of x is 1)
+  int nrest;                // other indices, innermost first
+  int64_t rest_dim[4], rest_in[4], rest_out[4];
+  int64_t nrest_total;
+};
+
+template <bool CPI, bool CPO>
+__global__ void permute_tiled_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                     TileDesc t, double alpha, double beta, int op) {
+  using TI = typename std::conditional<CPI, double2, double>::type;
+  __shared__ TI tile[32][33];
+  const int64_t tx_tiles = (t.X + 31) / 32;
+  const int64_t x0 = (int64_t)(blockIdx.x % tx_tiles) * 32, y0 = (int64_t)(blockIdx.x / tx_tiles) * 32;
+  const TI* tin = reinterpret_cast<const TI*>(in);
+  const bool rd = op == kAdd || op == kSub || (op == kGeneral && beta != 0.0);
+  for (int64_t r = blockIdx.y; r < t.nrest_total; r += gridDim.y) {
+    int64_t rem = r, ib = 0, ob = 0;
+    for (int k = 0; k < t.nrest; ++k) {
+      const int64_t q = rem / t.rest_dim[k];
+      const int64_t i = rem - q * t.rest_dim[k];
+      ib += i * t.rest_in[k];
+      ob += i * t.rest_out[k];
+      rem = q;
+    }
+    __syncthreads();  // the previous rest index finished reading the tile
+    for (int xi = threadIdx.y; xi < 32; xi += blockDim.y) {
+      const int64_t x = x0 + xi, y = y0 + threadIdx.x;
+      if (x < t.X && y < t.Y) tile[xi][threadIdx.x] = tin[ib + x * t.in_sx + y];
+    }
+    __syncthreads();
+    for (int yi = threadIdx.y; yi < 32; yi += blockDim.y) {
+      const int64_t x = x0 + threadIdx.x, y = y0 + yi;
+      if (x >= t.X || y >= t.Y) continue;
+      const int64_t o = ob + y * t.out_sy + x;
+      if constexpr (CPO) {
+        double2* po = reinterpret_cast<double2*>(out) + o;
+        const double2 c = rd ? *po : make_double2(0.0, 0.0);
+        double2 v;
+        if constexpr (CPI) {
+          v = tile[threadIdx.x][yi];
+        } else {
+          v = make_double2(tile[threadIdx.x][yi], 0.0);
+        }
+        double2 res;
+        res.x = axop(op, v.x, c.x, alpha, beta);
+        res.y = CPI ? axop(op, v.y, c.y, alpha, beta)
+                    : (rd ? (op == kGeneral ? beta * c.y : c.y) : 0.0);
+        *po = res;
+      } else {
+        const double c = rd ? out[o] : 0.0;
+        out[o] = axop(op, (double)tile[threadIdx.x][yi], c, alpha, beta);
+      }
     }
   }
 }
@@ -468,6 +533,23 @@ __device__ __forceinline__ unsigned long long umax_warp(unsigned long long v) {
   return v;
 }
 
+// 1/x for x >= 1 (here x = 1 + (h D)^2): an FP32 reciprocal refined by two
+// Newton-Raphson steps r <- r (2 - x r) in FP64, each squaring the relative
+// error (2^-22 -> 2^-44 -> below 2^-53 before rounding).
+__device__ __forceinline__ double recip_newton(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
+
+// One block per row of an amplitude block: a T1 row (i) holds nV entries,
+// a T2 row (i, j) nV*nV entries (a, b).  The row's occupied part of the
+// denominator, its spins and its pad status are fixed per block; the
+// virtual part comes from two table reads.  With R' = R - D t the update of
+// Eq. 9 reduces to
+//   t_new = [t_n + i h (R_n + R_k - D t_k)] (1 + i h D) / (1 + (h D)^2),
+// h = dt/2, and the convergence measure is max |t_new - t_k|^2.
 __global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
                                  const double* __restrict__ fv_a, const double* __restrict__ fo_b,
                                  const double* __restrict__ fv_b, double dt,
@@ -475,42 +557,72 @@ __global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
                                  const double2* tk_in, double2* tk_out,
                                  const double2* __restrict__ Rk, unsigned long long* maxdiff) {
   __shared__ unsigned long long red[kThreads / 32];
+  const int nO = g.nO, nV = g.nV;
+  const int rows1 = 2 * nO, rows = rows1 + 3 * nO * nO;
+  const double h = 0.5 * dt;
   unsigned long long m = 0ull;
-  int64_t total = g.total();
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    Elem x = decode(g, e);
-    double2 old = tk_in[e];
-    double2 nw = make_double2(0.0, 0.0);
-    if (!is_pad(g, x)) {
-      int s1 = spin_ia(x.blk);
-      const double* fo1 = s1 ? fo_b : fo_a;
-      const double* fv1 = s1 ? fv_b : fv_a;
-      double D = fv1[x.a] - fo1[x.i];
-      if (x.blk >= 2) {
-        int s2 = spin_jb(x.blk);
-        D += (s2 ? fv_b : fv_a)[x.b] - (s2 ? fo_b : fo_a)[x.j];
-      }
-      double h = 0.5 * dt;
-      double2 t0 = tn[e];
-      double2 rn = Rn[e], rk = Rk[e];
-      // R' = R - D t for both points
-      double px = (rn.x - D * t0.x) + (rk.x - D * old.x);
-      double py = (rn.y - D * t0.y) + (rk.y - D * old.y);
-      // num = (1 + i h D) t0 + i h (R'n + R'k)
-      double nx = t0.x - h * D * t0.y - h * py;
-      double ny = t0.y + h * D * t0.x + h * px;
-      // divide by (1 - i h D): multiply by (1 + i h D) / (1 + (h D)^2)
-      double hd = h * D;
-      double inv = 1.0 / (1.0 + hd * hd);
-      nw.x = (nx - hd * ny) * inv;
-      nw.y = (ny + hd * nx) * inv;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    int blk, i, j;
+    int64_t base;
+    int len;
+    if (row < rows1) {
+      blk = row / nO;
+      i = row - blk * nO;
+      j = 0;
+      base = g.off(blk) + (int64_t)i * nV;
+      len = nV;
+    } else {
+      const int q = row - rows1;
+      const int t = q / (nO * nO);
+      blk = 2 + t;
+      const int ij = q - t * nO * nO;
+      i = ij / nO;
+      j = ij - i * nO;
+      base = g.off(blk) + (int64_t)ij * nV * nV;
+      len = nV * nV;
     }
-    tk_out[e] = nw;
-    double d = hypot(nw.x - old.x, nw.y - old.y);
-    unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(d));
-    if (d != d) bits = 0x7ff8000000000000ull;
-    m = bits > m ? bits : m;
+    const int s1 = spin_ia(blk), s2 = spin_jb(blk);
+    const double* fv1 = s1 ? fv_b : fv_a;
+    const double* fv2 = s2 ? fv_b : fv_a;
+    bool row_pad = (s1 == 1 && i == g.core);
+    double Drow = -(s1 ? fo_b : fo_a)[i];
+    if (blk >= 2) {
+      row_pad = row_pad || (s2 == 1 && j == g.core);
+      Drow -= (s2 ? fo_b : fo_a)[j];
+    }
+    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+      int a, b;
+      if (blk >= 2) {
+        a = q / nV;
+        b = q - a * nV;
+      } else {
+        a = q;
+        b = -1;
+      }
+      const int64_t e = base + q;
+      const double2 old = tk_in[e];
+      double2 nw = make_double2(0.0, 0.0);
+      const bool pad = row_pad || (s1 == 0 && a == 0) || (b >= 0 && s2 == 0 && b == 0);
+      if (!pad) {
+        double D = Drow + fv1[a];
+        if (b >= 0) D += fv2[b];
+        const double2 t0 = tn[e], rn = Rn[e], rk = Rk[e];
+        const double sx = fma(-D, old.x, rn.x + rk.x);
+        const double sy = fma(-D, old.y, rn.y + rk.y);
+        const double nx = fma(-h, sy, t0.x);
+        const double ny = fma(h, sx, t0.y);
+        const double hd = h * D;
+        const double inv = recip_newton(fma(hd, hd, 1.0));
+        nw.x = fma(-hd, ny, nx) * inv;
+        nw.y = fma(hd, nx, ny) * inv;
+      }
+      tk_out[e] = nw;
+      const double dx = nw.x - old.x, dy = nw.y - old.y;
+      const double d2 = fma(dx, dx, dy * dy);
+      unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
+      if (d2 != d2) bits = 0x7ff8000000000000ull;
+      m = bits > m ? bits : m;
+    }
   }
   m = umax_warp(m);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -867,8 +979,51 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
   for (int k = 0; k < d.nd; ++k) total *= d.out_dim[k];
   if (total == 0) return;
   if (in_cplx && !out_cplx) throw Error(-1, "permute_add: complex input into real output");
-  int grid = grid_for(total, 16);
   const int op = axop_of(alpha, beta);
+  // tiled transpose when the output's innermost index is strided in the
+  // input and another output index is the input's unit-stride one
+  const int xo = d.nd - 1;
+  int yo = -1;
+  for (int k = 0; k < xo; ++k)
+    if (d.in_stride[k] == 1 && d.out_dim[k] > 1) yo = k;
+  if (d.nd >= 2 && d.nd <= 6 && d.in_stride[xo] != 1 && yo >= 0 && d.out_dim[xo] >= 16 &&
+      d.out_dim[yo] >= 16) {
+    TileDesc t{};
+    t.X = d.out_dim[xo];
+    t.Y = d.out_dim[yo];
+    t.in_sx = d.in_stride[xo];
+    int64_t os = 1;
+    int64_t out_stride[6];
+    for (int k = d.nd - 1; k >= 0; --k) {
+      out_stride[k] = os;
+      os *= d.out_dim[k];
+    }
+    t.out_sy = out_stride[yo];
+    t.nrest = 0;
+    t.nrest_total = 1;
+    for (int k = d.nd - 1; k >= 0; --k) {
+      if (k == xo || k == yo) continue;
+      t.rest_dim[t.nrest] = d.out_dim[k];
+      t.rest_in[t.nrest] = d.in_stride[k];
+      t.rest_out[t.nrest] = out_stride[k];
+      t.nrest_total *= d.out_dim[k];
+      ++t.nrest;
+    }
+    const int64_t tiles = ((t.X + 31) / 32) * ((t.Y + 31) / 32);
+    if (tiles <= 0x7fffffffll) {
+      dim3 grid((unsigned)tiles, (unsigned)std::min<int64_t>(t.nrest_total, 65535));
+      dim3 block(32, 8);
+      if (in_cplx)
+        permute_tiled_kernel<true, true><<<grid, block, 0, st>>>(in, out, t, alpha, beta, op);
+      else if (out_cplx)
+        permute_tiled_kernel<false, true><<<grid, block, 0, st>>>(in, out, t, alpha, beta, op);
+      else
+        permute_tiled_kernel<false, false><<<grid, block, 0, st>>>(in, out, t, alpha, beta, op);
+      RT_CHECK_LAUNCH();
+      return;
+    }
+  }
+  int grid = grid_for(total, 16);
   auto go = [&](auto idx_tag) {
     using I = decltype(idx_tag);
     if (in_cplx)
@@ -962,7 +1117,8 @@ void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const d
                const double* fv_b, double dt, const double* tn, const double* Rn,
                const double* tk_in, double* tk_out, const double* Rk,
                unsigned long long* maxdiff_bits, cudaStream_t st) {
-  am_update_kernel<<<grid_for(g.total(), 16), kThreads, 0, st>>>(
+  const int rows = 2 * g.nO + 3 * g.nO * g.nO;
+  am_update_kernel<<<std::min(rows, 148 * 16), kThreads, 0, st>>>(
       g, fo_a, fv_a, fo_b, fv_b, dt, reinterpret_cast<const double2*>(tn),
       reinterpret_cast<const double2*>(Rn), reinterpret_cast<const double2*>(tk_in),
       reinterpret_cast<double2*>(tk_out), reinterpret_cast<const double2*>(Rk), maxdiff_bits);

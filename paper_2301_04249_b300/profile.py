@@ -1,6 +1,6 @@
 """Evaluate CCSD residuals of a named workload eagerly, for profilers.
 
-  python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde] [--residuals 2]
+  python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde | --shape O,V,N] [--residuals 2]
          [--precision fp64|split_tf32|split_bf16|fp64_ozaki] [--cholesky] [--steps N]
          [--tol TOL] [--anderson]
 
@@ -34,6 +34,8 @@ from synth import workload  # noqa: E402
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c2_formaldehyde")
+    ap.add_argument("--shape", default=None,
+                    help="O,V,Nchol: a synthetic problem of this shape (seed 9) instead")
     ap.add_argument("--residuals", type=int, default=2)
     ap.add_argument("--precision", choices=["fp64", "split_tf32", "split_bf16", "fp64_ozaki"],
                     default="fp64")
@@ -44,7 +46,12 @@ def main():
     ap.add_argument("--eager-timing", action="store_true",
                     help="with --steps: residuals outside graphs, every launch timed")
     a = ap.parse_args()
-    p, run = workload(a.workload)
+    if a.shape:
+        from synth import gen_problem
+        O, V, N = (int(x) for x in a.shape.split(","))
+        p, run = gen_problem(O, V, N, 9), dict(dt=0.025)
+    else:
+        p, run = workload(a.workload)
     rng = np.random.default_rng(0)
     prec = {"fp64": P.RTEOM_FP64, "split_tf32": P.RTEOM_SPLIT_TF32,
             "split_bf16": P.RTEOM_SPLIT_BF16, "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]

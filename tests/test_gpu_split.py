@@ -119,12 +119,32 @@ def test_split_tracks_fp64_path_over_40_steps(form):
     assert np.abs(C32 - C64).max() < 1e-6
 
 
+# Steps of the 200-step config-1 stress run over which C(t) stays within
+# 1e-6 absolute of the oracle with every contraction on the tensor cores.
+# Split-BF16 (exact digit-pair chunk sums) holds it over the whole run
+# (measured 2.5e-7).  Split-TF32 (FP32 sums over slices of 512 of K) leaves
+# it after about 60 steps (3 au; 3.3e-6 absolute, 2.9e-7 relative, after
+# 200 steps with |C| up to 11); its default configuration, where only
+# contractions of at least 5e7 FLOP (and the autotuner's picks) take the
+# tensor cores, stays within 2.5e-7 over all 200 steps.
+STRESS_HORIZON = {P.RTEOM_SPLIT_TF32: 50, P.RTEOM_SPLIT_BF16: 200}
+
+
+def test_split_c1_default_configuration_full_run_absolute(form):
+    """Config 1 in full (200 steps, 10 au) in the form's default
+    configuration: C(t) within 1e-6 absolute of the oracle at every step."""
+    C_ref, _, _ = _golden("c1_fp64_small")
+    p, run = workload("c1_fp64_small")
+    with _split(p, form) as g:
+        C = g.propagate(run["nsteps"], run["dt"], tol=1e-8)
+    assert np.abs(C - C_ref).max() < 1e-6, np.abs(C - C_ref).max()
+
+
 def test_split_everything_on_tensor_cores_c1_qp_peak(monkeypatch, form):
     """Stress case: every contraction on the tensor cores (threshold 0), 200
-    steps of c1 (10 au, |C| up to 11).  The 22-bit hi/lo split leaves a drift
-    of a few 1e-6 absolute in the phase of C over this horizon (measured
-    2.6e-6, i.e. 2.3e-7 relative); the bound here is 1e-6 relative, and the
-    quasiparticle peak must stay within 0.005 eV."""
+    steps of config 1 (10 au, |C| up to 11): C(t) within 1e-6 absolute up to
+    the form's horizon (STRESS_HORIZON), within 1e-6 relative over the whole
+    run, and the quasiparticle peak within 0.005 eV."""
     monkeypatch.setenv(form[1], "0")
     C_ref, eps_c, e_corr = _golden("c1_fp64_small")
     p, run = workload("c1_fp64_small")
@@ -134,15 +154,12 @@ def test_split_everything_on_tensor_cores_c1_qp_peak(monkeypatch, form):
         # the quasiparticle peak sits above eps_c + E_corr by the relaxation shift
         omega = np.linspace(shift - 1.0, shift + 3.0, 4001)
         A = g.spectrum(omega, 0.1)
-    assert np.abs(C - C_ref).max() < 1e-6 * np.abs(C_ref).max()
+    h = STRESS_HORIZON[form[0]]
+    err = np.abs(C - C_ref)
+    assert err[:h + 1].max() < 1e-6, (h, err[:h + 1].max())
+    assert err.max() < 1e-6 * np.abs(C_ref).max()
     Ao = PR.spectrum(PR.green_function(C_ref, run["dt"], eps_c, e_corr), run["dt"], omega, 0.1)
-
-    def peak(a):
-        k = int(np.argmax(a))
-        assert 0 < k < len(a) - 1, "peak must lie inside the frequency window"
-        y0, y1, y2 = a[k - 1], a[k], a[k + 1]
-        return omega[k] + 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2) * (omega[1] - omega[0])
-    assert abs(peak(A) - peak(Ao)) < QP_TOL_HA
+    assert abs(_qp_peak(omega, A) - _qp_peak(omega, Ao)) < QP_TOL_HA
     assert np.abs(A - Ao).max() < 1e-5 * np.abs(Ao).max()
 
 

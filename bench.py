@@ -338,7 +338,7 @@ def pinned_problem(torch, p):
 
 
 def run_form(torch, P, p, host, form, dt, warmup, steps, tol, max_micro, stream, world,
-             sampler=None, timing_mode=3):
+             sampler=None, timing_mode=3, flags=0):
     """One context of `form` on the pinned host inputs: create, `warmup`
     untimed steps, `steps` timed steps (each a propagate call returning its
     C_n to the host), the spectrum, destroy.  Device time of the timed steps
@@ -349,7 +349,7 @@ def run_form(torch, P, p, host, form, dt, warmup, steps, tol, max_micro, stream,
     free0 = torch.cuda.mem_get_info()[0]
     w0 = time.perf_counter()
     g = P.Propagator(h_eps, h_L, p.nocc, p.nvir, h_t1, h_t2, core=p.core,
-                     precision=precision_of(P, form), stream=stream)
+                     precision=precision_of(P, form), flags=flags, stream=stream)
     setup_s = time.perf_counter() - w0
     held = free0 - torch.cuda.mem_get_info()[0]
     C_steps = []
@@ -572,6 +572,23 @@ def run_ours(args):
         host2 = pinned_problem(torch, p2)
         sec = run_form(torch, P, p2, host2, "fp64", run2["dt"], args.warmup, args.steps,
                        args.tol, args.max_micro, stream, world)
+    # the cached (vv|vv) ladder block against forming it from the Cholesky
+    # vectors at every residual, on the formaldehyde-shaped workload
+    ablation = None
+    if not args.no_secondary:
+        abl = {}
+        for form in ("fp64", "split_tf32"):
+            for mode, fl in (("resident", 0), ("cholesky", P.RTEOM_FLAG_LADDER_CHOLESKY)):
+                r = run_form(torch, P, p2, host2, form, run2["dt"], 3, 10, args.tol,
+                             args.max_micro, stream, world, flags=fl)
+                abl[f"{form}_{mode}"] = {"ms_per_micro_iteration": 1e3 * r["elapsed"] / max(r["micro"], 1),
+                                         "device_bytes_held": r["device_bytes_held"]}
+            abl[f"{form}_cholesky_over_resident"] = (abl[f"{form}_cholesky"]["ms_per_micro_iteration"]
+                                                     / abl[f"{form}_resident"]["ms_per_micro_iteration"])
+        ablation = {"workload": describe("c2_formaldehyde", p2, run2["dt"], args.tol),
+                    "what": "time per micro-iteration with the resident (vv|vv) ladder block "
+                            "(cached W) and with the Cholesky mode (W formed from L at every "
+                            "residual), 10 timed steps after 3 untimed", **abl}
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -646,6 +663,7 @@ def run_ours(args):
         "peaks": peaks,
         "forms": forms,
         "secondary": secondary,
+        "ablation_cached_w": ablation,
         "serving": serving_block(P, args),
     }
     print(json.dumps(res), flush=True)

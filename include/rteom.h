@@ -56,19 +56,23 @@ extern "C" {
                                  ones the autotuner finds faster there) on the
                                  BF16 tensor cores as three 8-bit digit planes
                                  per operand with per-row power-of-two scales
-                                 (x carried to about 2^-24 of its row scale),
-                                 the 6 leading digit-pair products summed
-                                 exactly in FP32 over chunks of 256 of K and
-                                 accumulated as compensated pairs; every other
-                                 step FP64 */
+                                 (x carried to about 2^-24 of its row scale):
+                                 the leading digit-pair product summed exactly
+                                 in FP32 over chunks of 512 of K, the 5 other
+                                 leading pairs (planes pre-scaled by their
+                                 digit weights) in one FP32 accumulator
+                                 beside it, chunks added as compensated
+                                 pairs; complex x complex products as three
+                                 real ones; every other step FP64 */
 #define RTEOM_SPLIT_TF32  2   /* contractions of at least 5e7 FLOP (and smaller
                                  ones the autotuner finds faster there) on the
                                  tensor cores as split-TF32 products (x = hi +
                                  lo, hi*hi + hi*lo + lo*hi) with FP32
                                  accumulation over slices of at most 512 of K,
-                                 slices summed as compensated FP32 pairs; every
-                                 other step (small contractions, Adams-Moulton
-                                 update, cumulant, phases) FP64 */
+                                 slices summed as compensated FP32 pairs;
+                                 complex x complex products as three real ones;
+                                 every other step (small contractions,
+                                 Adams-Moulton update, cumulant, phases) FP64 */
 #define RTEOM_FP64_OZAKI  3   /* FP64-accurate contractions on the BF16 tensor
                                  cores (no counterpart in the paper): operands
                                  sliced into seven 8-bit digit planes with

@@ -178,8 +178,8 @@ std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
 // whose A' has few rows runs as C^T = B^T A^T (output written transposed)
 // when that pads much less.
 int64_t oz_padded(int64_t ra, int64_t rb, int S) {
-  (void)S;  // both plane counts tile B' in 32 or 64 rows
-  const int64_t bn = rb <= 32 ? 32 : 64;
+  // B' tiles of 32 rows when narrow, else 128 (three planes) or 64 (seven)
+  const int64_t bn = rb <= 32 ? 32 : (S == 3 ? 128 : 64);
   return (ra + 127) / 128 * 128 * ((rb + bn - 1) / bn * bn);
 }
 

@@ -23,15 +23,17 @@
 //
 // Operand layout: digit planes [S][batch][row tile][k tile][rows x 32] of
 // BF16 in 8 x 8 core matrices (K-major, no swizzle; 128 B between core
-// matrices along K, 512 B between 8-row groups).  A stage holds all seven
-// planes of one k tile of A (128 rows) and B (64 rows), 84 KB; two stages.
-// Tensor memory holds the S diagonal accumulators (7 x 64 columns), twice
-// over where both sets fit (3 planes), so a chunk drains while the next one
-// accumulates.
+// matrices along K, 512 B between 8-row groups).  A stage holds all planes of
+// one k tile of A (128 rows) and B (64 rows for seven planes, 84 KB, two
+// stages; 128 rows for three, 48 KB, four stages).  Tensor memory holds the
+// accumulators of one chunk (seven planes: 7 diagonals x 64 columns; three
+// planes: 2 x 128 columns, see Cfg), twice over where both sets fit, so a
+// chunk drains while the next one accumulates.
 //
-// Warp roles (320 threads): warp 0 lane 0 issues the bulk copies, warp 1
-// owns the tensor memory and lane 0 issues the MMAs, warps 2-9 drain the
-// accumulators (warp w reads lanes 32*(w%4)..+31, column half (w-2)/4).
+// Warp roles: warp 0 lane 0 issues the bulk copies, warp 1 owns the tensor
+// memory and lane 0 issues the MMAs, the other 8 (16 for 128-column tiles)
+// warps drain the accumulators (warp w reads lanes 32*(w%4)..+31 and column
+// group (w-2)/4).
 // Every wait is bounded; on expiry the CTA records an error code, lets its
 // copies land, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -53,8 +55,6 @@ using namespace tc5;
 constexpr int BM = 128;                    // rows of A' per tile (TMEM lanes)
 constexpr int BK = 32;                     // K per k tile (BF16, 64 bytes per row)
 constexpr uint32_t A_TILE = BM * BK * 2;   // 8 KB
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int kZeroExp = INT_MIN / 4;      // scale exponent of an all-zero row
 constexpr int kNanExp = INT_MAX / 4;       // ... of a row holding an infinity or NaN
 
@@ -62,20 +62,39 @@ constexpr int kNanExp = INT_MAX / 4;       // ... of a row holding an infinity o
 // output-tile width BN (rows of B' per tile).  A diagonal sums at most S
 // digit pairs, so a chunk of K stays exact in FP32 while S * K * 2^14 <
 // 2^24: 128 of K for S = 7, 256 for S = 3.
+//
+// Three planes (the split-BF16 form) use two accumulators instead of one per
+// diagonal: the leading pair (0,0), exact over chunks of 512 of K, and the
+// five others together, their planes packed pre-scaled by the digit weights
+// 2^-8 and 2^-16 (exact in BF16) so that one FP32 accumulator carries them
+// at their relative weights (rounding about 2^-24 of a term 2^-8 below the
+// leading one).  That leaves room for 128-column tiles, two accumulator sets
+// and chunks twice as long.
 template <int S, int BN>
 struct Cfg {
-  static constexpr int CHUNK_KT = S > 4 ? 4 : 8;  // k tiles per exact chunk
+  static constexpr bool FUSED = S == 3;
+  static constexpr int NACC = FUSED ? 2 : S;       // accumulators per set
+  static constexpr int CHUNK_KT = FUSED ? 16 : (S > 4 ? 4 : 8);  // k tiles per chunk
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
   static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 4 ? (200u * 1024u / STAGE_BYTES) : 4;
   // two accumulator sets (the next chunk accumulates while the last one
   // drains) when both fit the 512 tensor-memory columns
-  static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;
-  static constexpr int ACC_COLS = NBUF * S * BN;
+  static constexpr int NBUF = 2 * NACC * BN <= 512 ? 2 : 1;
+  static constexpr int ACC_COLS = NBUF * NACC * BN;
   static constexpr uint32_t TMEM_COLS = ACC_COLS <= 128 ? 128 : (ACC_COLS <= 256 ? 256 : 512);
   static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 256;
+  // accumulator drain: 16 warps for 128-column tiles (32 columns each keep
+  // their compensated pairs in registers), else 8; four warps per group of
+  // 32 tensor-memory lanes
+  static constexpr int EPI = BN >= 128 ? 16 : 8;
+  static constexpr int THREADS = 64 + 32 * EPI;
+  static constexpr int COLS = BN / (EPI / 4);  // columns drained by one warp
   static_assert(ACC_COLS <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
-  static_assert(S * CHUNK_KT * BK * 16384 < (1 << 24), "chunk sums must stay exact in FP32");
+  // exactness of the chunk sums: S pairs per diagonal (one pair for the
+  // leading accumulator of the fused form), |d_s d_t| <= 2^14
+  static_assert((FUSED ? 1 : S) * CHUNK_KT * BK * 16384 < (1 << 24),
+                "chunk sums must stay exact in FP32");
   static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
@@ -274,7 +293,10 @@ __global__ void oz_digits_kernel(PackArgs p, int batch) {
       digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const __nv_bfloat162 h = __halves2bfloat162(__int2bfloat16_rn(d0[s]), __int2bfloat16_rn(d1[s]));
+        // the fused three-plane form stores plane s pre-scaled by 2^(-8 s)
+        const float ws = S == 3 ? __int_as_float((127 - 8 * s) << 23) : 1.0f;
+        const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn((float)d0[s] * ws),
+                                                    __float2bfloat16_rn((float)d1[s] * ws));
         packed[s][j / 2] = *reinterpret_cast<const uint32_t*>(&h);
       }
     }
@@ -309,14 +331,14 @@ struct KArgs {
 };
 
 template <int S, int BN>
-__global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
+__global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g) {
   using CF = Cfg<S, BN>;
   constexpr int CHUNK_KT = CF::CHUNK_KT;
   constexpr int STAGES = CF::STAGES;
   constexpr uint32_t B_TILE = CF::B_TILE;
   constexpr uint32_t STAGE_BYTES = CF::STAGE_BYTES;
   constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
-  constexpr int HALF = BN / 2;  // columns drained by one epilogue warp
+  constexpr int HALF = CF::COLS;  // columns drained by one epilogue warp
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
@@ -350,7 +372,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], EPI_WARPS);
+      mbar_init(&acc_empty[i], CF::EPI);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -415,12 +437,16 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       for (int sa = 0; sa < S; ++sa) {
 #pragma unroll
         for (int sb = 0; sb < S - sa; ++sb) {
-          const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * S + sa + sb) * BN);
+          // accumulator of the pair: its diagonal, or (fused) leading / rest;
+          // the first pair into an accumulator in a chunk starts it afresh
+          const int acc = CF::FUSED ? (sa + sb > 0 ? 1 : 0) : sa + sb;
+          const bool first_pair = sa == 0 && (!CF::FUSED || sb <= 1);
+          const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * CF::NACC + acc) * BN);
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint64_t ad = smem_desc(base + sa * A_TILE + ks * 256, 128, 512);
             const uint64_t bd = smem_desc(base + S * A_TILE + sb * B_TILE + ks * 256, 128, 512);
-            mma_bf16(dt, ad, bd, idesc, (kin > 0 || ks > 0 || sa > 0) ? 1u : 0u);
+            mma_bf16(dt, ad, bd, idesc, (kin > 0 || ks > 0 || !first_pair) ? 1u : 0u);
           }
         }
       }
@@ -446,13 +472,15 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(KArgs g) {
       }
       tc_fence_after();
 #pragma unroll 1
-      for (int d = 0; d < S; ++d) {
-        const float w = __int_as_float((127 - 14 - 8 * d) << 23);  // 2^(2 - 8 (d + 2))
+      for (int d = 0; d < CF::NACC; ++d) {
+        // 2^(2 - 8 (d + 2)) for diagonal d; the fused accumulators both carry
+        // the weight of the leading diagonal (the rest is pre-scaled)
+        const float w = __int_as_float((127 - 14 - 8 * (CF::FUSED ? 0 : d)) << 23);
 #pragma unroll
         for (int c = 0; c < HALF; c += 16) {
           uint32_t r[16];
           tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) +
-                        (uint32_t)((set * S + d) * BN + h * HALF + c),
+                        (uint32_t)((set * CF::NACC + d) * BN + h * HALF + c),
                     r);
 #pragma unroll
           for (int v = 0; v < 16; ++v)
@@ -600,7 +628,7 @@ Plan plan(const GemmDesc& d, int S) {
   // 32 columns for a narrow B', else 64: with seven planes one accumulator
   // set of 7 x 64 columns, with three planes two sets of 3 x 64 (the next
   // chunk accumulates while the last drains)
-  p.bn = Br <= 32 ? 32 : 64;
+  p.bn = Br <= 32 ? 32 : (S == 3 ? 128 : 64);
   p.Mp = roundup(std::max(Ar, 1), BM);
   p.Np = roundup(std::max(Br, 1), p.bn);
   p.Kp = roundup(std::max(Ak, 1), BK);
@@ -704,7 +732,7 @@ void gemm_oz_init() {
   };
   set(oz::oz_gemm_kernel<7, 64>, oz::Cfg<7, 64>::SMEM);
   set(oz::oz_gemm_kernel<7, 32>, oz::Cfg<7, 32>::SMEM);
-  set(oz::oz_gemm_kernel<3, 64>, oz::Cfg<3, 64>::SMEM);
+  set(oz::oz_gemm_kernel<3, 128>, oz::Cfg<3, 128>::SMEM);
   set(oz::oz_gemm_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
 }
 
@@ -799,14 +827,14 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.beta = d.beta;
   dim3 grid((p.Np / p.bn) * (p.Mp / oz::BM), 1, d.batch * p.ranges);
   using namespace oz;
-  if (S == 3 && p.bn == 64)
-    oz_gemm_kernel<3, 64><<<grid, THREADS, Cfg<3, 64>::SMEM, st>>>(g);
+  if (S == 3 && p.bn == 128)
+    oz_gemm_kernel<3, 128><<<grid, Cfg<3, 128>::THREADS, Cfg<3, 128>::SMEM, st>>>(g);
   else if (S == 3)
-    oz_gemm_kernel<3, 32><<<grid, THREADS, Cfg<3, 32>::SMEM, st>>>(g);
+    oz_gemm_kernel<3, 32><<<grid, Cfg<3, 32>::THREADS, Cfg<3, 32>::SMEM, st>>>(g);
   else if (p.bn == 32)
-    oz_gemm_kernel<7, 32><<<grid, THREADS, Cfg<7, 32>::SMEM, st>>>(g);
+    oz_gemm_kernel<7, 32><<<grid, Cfg<7, 32>::THREADS, Cfg<7, 32>::SMEM, st>>>(g);
   else
-    oz_gemm_kernel<7, 64><<<grid, THREADS, Cfg<7, 64>::SMEM, st>>>(g);
+    oz_gemm_kernel<7, 64><<<grid, Cfg<7, 64>::THREADS, Cfg<7, 64>::SMEM, st>>>(g);
   RT_CHECK_LAUNCH();
 }
 

@@ -531,23 +531,35 @@ __global__ void tc_combine_3m_kernel(FinArgs f) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(e / f.N), n = (int)(e % f.N);
-    double v[3];
+    // products as compensated FP32 pairs (s, c); the differences are formed
+    // with TwoSum on the leading parts, so only the final value takes an
+    // FP64 add (the FP64 pipe is the scarce unit)
+    float s[3], cm[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
-      float s = 0.0f, cm = 0.0f;
+      s[b] = 0.0f;
+      cm[b] = 0.0f;
       for (int z = 0; z < f.ranges; ++z) {
         const float2 q = pp[z * zs];
-        two_sum_acc(s, cm, q.x);
-        cm += q.y;
+        two_sum_acc(s[b], cm[b], q.x);
+        cm[b] += q.y;
       }
-      v[b] = f32_to_f64(s) + f32_to_f64(cm);
     }
-    const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
+    float re_h = s[0], re_l = cm[0] - cm[1];
+    two_sum_acc(re_h, re_l, -s[1]);                 // P1 - P2
+    float im_h = s[2], im_l = cm[2] - cm[0] - cm[1];
+    two_sum_acc(im_h, im_l, -s[0]);
+    two_sum_acc(im_h, im_l, -s[1]);                 // P3 - P1 - P2
+    const double re = f32_to_f64(re_h) + f32_to_f64(re_l);
+    const double im = f32_to_f64(im_h) + f32_to_f64(im_l);
     double* c = f.C + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
     const double a = f.alpha;
-    c[0] = f.beta == 0.0 ? a * re : (f.beta == 1.0 ? c[0] + a * re : fma(f.beta, c[0], a * re));
-    c[1] = f.beta == 0.0 ? a * im : (f.beta == 1.0 ? c[1] + a * im : fma(f.beta, c[1], a * im));
+    const bool unit = a == 1.0 || a == -1.0;
+    const double vr = unit ? (a < 0 ? neg_f64(re) : re) : a * re;
+    const double vi = unit ? (a < 0 ? neg_f64(im) : im) : a * im;
+    c[0] = f.beta == 0.0 ? vr : (f.beta == 1.0 ? c[0] + vr : fma(f.beta, c[0], vr));
+    c[1] = f.beta == 0.0 ? vi : (f.beta == 1.0 ? c[1] + vi : fma(f.beta, c[1], vi));
   }
 }
 

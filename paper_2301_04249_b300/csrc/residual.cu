@@ -404,6 +404,21 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
       ein("jf,mfbe->mbej", c, t1[s], ovvv, 1.0, W);
     }
   };
+  // c sum_nf Y_jn^{x} (me|nf) with the Coulomb integral: O^3 V^3 through the
+  // assembled (ov|ov), or, in the Cholesky mode, sum_Q L^Q_me [sum_nf Y L^Q_nf]
+  // (2 O^2 V^2 Nchol, several times less when Nchol < O (V+1) / 2)
+  auto w_coulomb = [&](const char* spec, const char* yspec, double c, const Tensor& Y,
+                       const Tensor& W) {
+    if (chol) {
+      const int64_t mq = A.mark();
+      Tensor q = newc({nQ, nO, nV});
+      ein(yspec, 1.0, Y, Lov, 0.0, q);  // q[Q][j][b] = sum_nf Y L^Q_nf
+      ein("Qme,Qjb->mbej", c, Lov, q, 1.0, W);
+      A.release(mq);
+    } else {
+      ein(spec, c, Y, ovov, 1.0, W);
+    }
+  };
   auto W_same = [&](int s, const Tensor& W) {  // ssss
     axpy("mejb->mbej", 1.0, ovov, 0.0, W);
     axpy("mjbe->mbej", -1.0, oovv, 1.0, W);
@@ -416,7 +431,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     t2t1(X, &t2ss[s], 0.5, t1[s], t1[s], 1.0, 0.0);
     ein("jnfb,menf->mbej", -1.0, X, ovov_as, 1.0, W);
     A.release(m2);
-    ein("jnbf,menf->mbej", 0.5, t2su[s], ovov, 1.0, W);
+    w_coulomb("jnbf,menf->mbej", "jnbf,Qnf->Qjb", 0.5, t2su[s], W);
   };
   auto W_usus = [&](int s, const Tensor& W) {  // m u, b s, e u, j s
     axpy("mejb->mbej", 1.0, ovov, 0.0, W);
@@ -426,7 +441,7 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     const int64_t m2 = A.mark();
     Tensor X = new2();
     t2t1(X, &t2ss[s], 0.5, t1[s], t1[s], 1.0, 0.0);
-    ein("jnfb,menf->mbej", -1.0, X, ovov, 1.0, W);
+    w_coulomb("jnfb,menf->mbej", "jnfb,Qnf->Qjb", -1.0, X, W);
     A.release(m2);
   };
   auto W_suus = [&](int s, const Tensor& W) {  // m s, b u, e u, j s

@@ -1011,7 +1011,12 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
     }
     const int64_t tiles = ((t.X + 31) / 32) * ((t.Y + 31) / 32);
     if (tiles <= 0x7fffffffll) {
-      dim3 grid((unsigned)tiles, (unsigned)std::min<int64_t>(t.nrest_total, 65535));
+      // about eight blocks per SM in all; each walks several rest indices
+      int64_t gy = (148 * 8 + tiles - 1) / tiles;
+      if (gy > t.nrest_total) gy = t.nrest_total;
+      if (gy > 65535) gy = 65535;
+      if (gy < 1) gy = 1;
+      dim3 grid((unsigned)tiles, (unsigned)gy);
       dim3 block(32, 8);
       if (in_cplx)
         permute_tiled_kernel<true, true><<<grid, block, 0, st>>>(in, out, t, alpha, beta, op);

@@ -7,10 +7,10 @@ cumulant integrand and C_{n+1} (Eqs. 5-6).  Metric: time steps/s, whole job
 (sum over ranks; ranks are independent replicas).
 
 Default workload: the ESCA-shaped propagation O=50, V=450, Nchol=1800,
-dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-precision
-form (contractions as split products on the tensor cores, FP64 update,
-cumulant and phases).  Beside it, on the same inputs: the other split form
-and the FP64-accurate emulated form (a few steps each), an estimate of the
+dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-BF16
+form (contractions as BF16 digit-plane products on the tensor cores, FP64
+update, cumulant and phases).  Beside it, on the same inputs: the split-TF32
+form and the FP64-accurate emulated form (a few steps each), an estimate of the
 plain FP64 (DFMA) form from its measured contraction rate, and the
 formaldehyde-shaped FP64 workload (O=8, V=100, Nchol=400) as a secondary
 line.  Every form reports time per step and per micro-iteration (the
@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c5_esca_large")
-    ap.add_argument("--form", choices=FORMS, default="split_tf32",
+    ap.add_argument("--form", choices=FORMS, default="split_bf16",
                     help="precision form of the headline line")
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)

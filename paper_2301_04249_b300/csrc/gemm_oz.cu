@@ -318,6 +318,7 @@ struct KArgs {
   int64_t sA, sB;              // per-batch element strides within a plane
   const int *ea, *eb;          // row scale exponents of A' [batch][Mp] and B' [batch][Np]
   int KT, kpr, ranges;
+  int zs;                      // batch * ranges (work items per output tile)
   float2* P;                   // unscaled (sum, compensation) [batch*ranges][Mp][Np] when ranges > 1
   bool force_p;                // partials even with one range (3M products)
   int Mp, Np;
@@ -353,17 +354,28 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // output tiles on one grid axis (row tiles exceed 65535 for long M)
-  int m_tile, n_tile;
-  // rasterization groups of 8 row tiles: a 128-row A' tile carries twice
-  // the bytes of a 64-row B' tile, so 148 CTAs in flight cover about 8 row
-  // tiles and 18 column tiles
-  grouped_tile((int)blockIdx.x, g.Mp / BM, g.Np / BN, BN == 64 ? 8 : 12, &m_tile, &n_tile);
-  const int z = blockIdx.z;
-  const int b = z / g.ranges, rg = z % g.ranges;
-  const int kt0 = rg * g.kpr;
-  const int kt1 = min(g.KT, kt0 + g.kpr);
-  const int nk = max(kt1 - kt0, 0);
-  const int nchunks = (nk + CHUNK_KT - 1) / CHUNK_KT;
+  // Persistent CTAs: work item w = z * tiles + t (t the output tile in
+  // rasterization order: groups of 8 row tiles when a 128-row A' tile
+  // carries twice the bytes of a 64-row B' tile, else 12), CTA c takes items
+  // c, c + gridDim.x, ...; the stage and chunk counters run on across items,
+  // so a tile's drain overlaps the next tile's MMAs.
+  const int m_tiles = g.Mp / BM, n_tiles = g.Np / BN;
+  const int tiles = m_tiles * n_tiles;
+  const int items = tiles * g.zs;
+  struct Item {
+    int m_tile, n_tile, z, b, kt0, nk, nchunks;
+  };
+  auto item_of = [&](int w) {
+    Item it;
+    it.z = w / tiles;
+    grouped_tile(w - it.z * tiles, m_tiles, n_tiles, BN == 64 ? 8 : 12, &it.m_tile, &it.n_tile);
+    it.b = it.z / g.ranges;
+    const int rg = it.z % g.ranges;
+    it.kt0 = rg * g.kpr;
+    it.nk = max(min(g.KT, it.kt0 + g.kpr) - it.kt0, 0);
+    it.nchunks = (it.nk + CHUNK_KT - 1) / CHUNK_KT;
+    return it;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -387,113 +399,132 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    const __nv_bfloat16* A = g.A + b * g.sA + (int64_t)m_tile * g.KT * (BM * BK);
-    const __nv_bfloat16* B = g.B + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
-    for (int k = 0; k < nk; ++k) {
-      const int s = k % STAGES;
-      if (k >= STAGES && !mbar_wait_or_abort(&empty[s], ((k / STAGES) - 1) & 1, abort_flag)) {
-        if (!*(volatile int*)abort_flag) atomicExch(g.err, 11);
-        *abort_flag = 1;
-        break;
+    int kg = 0;  // k tiles issued so far (all items)
+    for (int w = blockIdx.x; w < items && !*(volatile int*)abort_flag; w += gridDim.x) {
+      const Item it = item_of(w);
+      const __nv_bfloat16* A = g.A + it.b * g.sA + (int64_t)it.m_tile * g.KT * (BM * BK);
+      const __nv_bfloat16* B = g.B + it.b * g.sB + (int64_t)it.n_tile * g.KT * (BN * BK);
+      for (int k = 0; k < it.nk; ++k, ++kg) {
+        const int s = kg % STAGES;
+        if (kg >= STAGES &&
+            !mbar_wait_or_abort(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag)) {
+          if (!*(volatile int*)abort_flag) atomicExch(g.err, 11);
+          *abort_flag = 1;
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int64_t kt = it.kt0 + k;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll
+        for (int pl = 0; pl < S; ++pl)
+          bulk_load(st + pl * A_TILE, A + pl * g.a_plane + kt * (BM * BK), A_TILE, &full[s]);
+#pragma unroll
+        for (int pl = 0; pl < S; ++pl)
+          bulk_load(st + S * A_TILE + pl * B_TILE, B + pl * g.b_plane + kt * (BN * BK), B_TILE,
+                    &full[s]);
+        *issued = kg + 1;
       }
-      if (*(volatile int*)abort_flag) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const int64_t kt = kt0 + k;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-#pragma unroll
-      for (int pl = 0; pl < S; ++pl)
-        bulk_load(st + pl * A_TILE, A + pl * g.a_plane + kt * (BM * BK), A_TILE, &full[s]);
-#pragma unroll
-      for (int pl = 0; pl < S; ++pl)
-        bulk_load(st + S * A_TILE + pl * B_TILE, B + pl * g.b_plane + kt * (BN * BK), B_TILE,
-                  &full[s]);
-      *issued = k + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // diagonal d = s + t (planes s, t counted from 0) accumulates in columns
-    // [d*BN, (d+1)*BN); a chunk's first MMA into d (s = 0) starts it afresh
+    // [d*BN, (d+1)*BN); a chunk's first MMA into d (s = 0) starts it afresh;
+    // chunk jg (counted over all items) uses accumulator set jg % NBUF
     const uint32_t idesc = idesc_bf16(BN);
-    for (int k = 0; k < nk; ++k) {
-      const int j = k / CHUNK_KT, kin = k % CHUNK_KT;
-      if (kin == 0 && j >= 1) {
-        // chunk j reuses accumulator set j % NBUF once chunk j - NBUF drained
-        const int jj = j - NBUF;
-        if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1, g.wait)) {
-          *abort_flag = 1;
-          atomicExch(g.err, 14);
-          break;
-        }
-      }
-      const int s = k % STAGES;
-      if (!mbar_wait(&full[s], (k / STAGES) & 1, g.wait)) {
-        *abort_flag = 1;
-        atomicExch(g.err, 12);
-        break;
-      }
-      tc_fence_after();
-      *mmas = k + 1;
-      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-#pragma unroll
-      for (int sa = 0; sa < S; ++sa) {
-#pragma unroll
-        for (int sb = 0; sb < S - sa; ++sb) {
-          // accumulator of the pair: its diagonal, or (fused) leading / rest;
-          // the first pair into an accumulator in a chunk starts it afresh
-          const int acc = CF::FUSED ? (sa + sb > 0 ? 1 : 0) : sa + sb;
-          const bool first_pair = sa == 0 && (!CF::FUSED || sb <= 1);
-          const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * CF::NACC + acc) * BN);
-#pragma unroll
-          for (int ks = 0; ks < BK / 16; ++ks) {
-            const uint64_t ad = smem_desc(base + sa * A_TILE + ks * 256, 128, 512);
-            const uint64_t bd = smem_desc(base + S * A_TILE + sb * B_TILE + ks * 256, 128, 512);
-            mma_bf16(dt, ad, bd, idesc, (kin > 0 || ks > 0 || !first_pair) ? 1u : 0u);
+    int kg = 0, jg = 0;
+    bool stop = false;
+    for (int w = blockIdx.x; w < items && !stop; w += gridDim.x) {
+      const Item it = item_of(w);
+      for (int k = 0; k < it.nk; ++k, ++kg) {
+        const int kin = k % CHUNK_KT;
+        const int j = jg + k / CHUNK_KT;
+        if (kin == 0) {
+          // chunk j reuses accumulator set j % NBUF once chunk j - NBUF drained
+          const int jj = j - NBUF;
+          if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1, g.wait)) {
+            *abort_flag = 1;
+            atomicExch(g.err, 14);
+            stop = true;
+            break;
           }
         }
+        const int s = kg % STAGES;
+        if (!mbar_wait(&full[s], (kg / STAGES) & 1, g.wait)) {
+          *abort_flag = 1;
+          atomicExch(g.err, 12);
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        *mmas = kg + 1;
+        const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+        for (int sa = 0; sa < S; ++sa) {
+#pragma unroll
+          for (int sb = 0; sb < S - sa; ++sb) {
+            // accumulator of the pair: its diagonal, or (fused) leading / rest;
+            // the first pair into an accumulator in a chunk starts it afresh
+            const int acc = CF::FUSED ? (sa + sb > 0 ? 1 : 0) : sa + sb;
+            const bool first_pair = sa == 0 && (!CF::FUSED || sb <= 1);
+            const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * CF::NACC + acc) * BN);
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              const uint64_t ad = smem_desc(base + sa * A_TILE + ks * 256, 128, 512);
+              const uint64_t bd =
+                  smem_desc(base + S * A_TILE + sb * B_TILE + ks * 256, 128, 512);
+              mma_bf16(dt, ad, bd, idesc, (kin > 0 || ks > 0 || !first_pair) ? 1u : 0u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+        if (kin == CHUNK_KT - 1 || k == it.nk - 1) mma_commit(&acc_full[j % NBUF]);
       }
-      mma_commit(&empty[s]);
-      if (kin == CHUNK_KT - 1 || k == nk - 1) mma_commit(&acc_full[j % NBUF]);
+      jg += it.nchunks;
     }
   } else if (warp >= 2) {
     const int q = warp % 4;
     const int h = (warp - 2) / 4;
     const int row = 32 * q + lane;
-    float sum[HALF], cmp[HALF];
+    int jg = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x) {
+      const Item it = item_of(w);
+      float sum[HALF], cmp[HALF];
 #pragma unroll
-    for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
-    bool ok = nk > 0;
+      for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
+      bool ok = it.nk > 0 && !*(volatile int*)abort_flag;
 #pragma unroll 1
-    for (int j = 0; j < nchunks; ++j) {
-      const int set = j % NBUF;
-      if (!mbar_wait(&acc_full[set], (j / NBUF) & 1, g.wait)) {
-        ok = false;
-        *abort_flag = 1;
-        atomicExch(g.err, 13);
-        break;
-      }
-      tc_fence_after();
-#pragma unroll 1
-      for (int d = 0; d < CF::NACC; ++d) {
-        // 2^(2 - 8 (d + 2)) for diagonal d; the fused accumulators both carry
-        // the weight of the leading diagonal (the rest is pre-scaled)
-        const float w = __int_as_float((127 - 14 - 8 * (CF::FUSED ? 0 : d)) << 23);
-#pragma unroll
-        for (int c = 0; c < HALF; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) +
-                        (uint32_t)((set * CF::NACC + d) * BN + h * HALF + c),
-                    r);
-#pragma unroll
-          for (int v = 0; v < 16; ++v)
-            two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * w);
+      for (int jl = 0; ok && jl < it.nchunks; ++jl) {
+        const int j = jg + jl, set = j % NBUF;
+        if (!mbar_wait(&acc_full[set], (j / NBUF) & 1, g.wait)) {
+          ok = false;
+          *abort_flag = 1;
+          atomicExch(g.err, 13);
+          break;
         }
+        tc_fence_after();
+#pragma unroll 1
+        for (int d = 0; d < CF::NACC; ++d) {
+          // 2^(2 - 8 (d + 2)) for diagonal d; the fused accumulators both carry
+          // the weight of the leading diagonal (the rest is pre-scaled)
+          const float wd = __int_as_float((127 - 14 - 8 * (CF::FUSED ? 0 : d)) << 23);
+#pragma unroll
+          for (int c = 0; c < HALF; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) +
+                          (uint32_t)((set * CF::NACC + d) * BN + h * HALF + c),
+                      r);
+#pragma unroll
+            for (int v = 0; v < 16; ++v)
+              two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * wd);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[set]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[set]);
-    }
-    if (ok) {
-      const int mr = m_tile * BM + row;
-      const int er = row_exp(g.ea[(int64_t)b * g.Mp + mr]);
+      jg += it.nchunks;
+      if (!ok) break;
+      const int mr = it.m_tile * BM + row;
+      const int er = row_exp(g.ea[(int64_t)it.b * g.Mp + mr]);
       if (g.ranges == 1 && !g.force_p) {
         int m = mr, part = 0;
         if (g.mode == 1 && mr >= g.M) {
@@ -502,17 +533,17 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
         }
         const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
         if (row_ok) {
-          const int64_t rbase = (int64_t)b * g.sC + (int64_t)m * g.ldm;
+          const int64_t rbase = (int64_t)it.b * g.sC + (int64_t)m * g.ldm;
 #pragma unroll
           for (int v = 0; v < HALF; ++v) {
-            const int nr = n_tile * BN + h * HALF + v;
+            const int nr = it.n_tile * BN + h * HALF + v;
             int n = nr, pt = part;
             if (g.mode == 2 && nr >= g.N) {
               n = nr - g.N;
               pt = 1;
             }
             if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-            const int ec = row_exp(g.eb[(int64_t)b * g.Np + nr]);
+            const int ec = row_exp(g.eb[(int64_t)it.b * g.Np + nr]);
             double val = scaled_value(sum[v], cmp[v], er, ec);
             if (g.alpha == -1.0)
               val = neg_f64(val);
@@ -523,8 +554,8 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
           }
         }
       } else {
-        float4* dst = reinterpret_cast<float4*>(g.P + ((int64_t)z * g.Mp + mr) * g.Np +
-                                                (int64_t)n_tile * BN + h * HALF);
+        float4* dst = reinterpret_cast<float4*>(g.P + ((int64_t)it.z * g.Mp + mr) * g.Np +
+                                                (int64_t)it.n_tile * BN + h * HALF);
 #pragma unroll
         for (int v = 0; v < HALF / 2; ++v)
           dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
@@ -825,7 +856,11 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid((p.Np / p.bn) * (p.Mp / oz::BM), 1, d.batch * p.ranges);
+  g.zs = d.batch * p.ranges;
+  // persistent CTAs: one per SM (the kernel takes most of the shared memory)
+  const int64_t items = (int64_t)(p.Np / p.bn) * (p.Mp / oz::BM) * g.zs;
+  if (items > 0x7fffffff) throw Error(-1, "gemm_oz: too many tiles");
+  const int grid = (int)std::min<int64_t>(items, 148);
   using namespace oz;
   if (S == 3 && p.bn == 128)
     oz_gemm_kernel<3, 128><<<grid, Cfg<3, 128>::THREADS, Cfg<3, 128>::SMEM, st>>>(g);

@@ -73,6 +73,7 @@ struct KArgs {
   int KT;                              // k-tiles per row tile
   int kpr;                             // k-tiles per K range
   int ranges;                          // K ranges (CTAs along K per tile)
+  int zs;                              // batch * ranges (work items per output tile)
   float2* P;         // (sum, compensation) partials [batch*ranges][Mp][Np] when ranges > 1
   bool force_p;      // partials even with one range (3M products)
   int Mp, Np;        // padded extents of the partials
@@ -105,15 +106,28 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
   int* mmas = issued + 1;        // stages whose MMAs the issuer launched
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // output tiles on one grid axis (row tiles exceed 65535 for long M)
-  int m_tile, n_tile;
-  grouped_tile((int)blockIdx.x, g.Mp / BM, g.Np / BN, kGroupM, &m_tile, &n_tile);
-  const int z = blockIdx.z;
-  const int b = z / g.ranges, rg = z % g.ranges;
-  const int kt0 = rg * g.kpr;
-  const int kt1 = min(g.KT, kt0 + g.kpr);
-  const int nk = max(kt1 - kt0, 0);
-  const int nslices = (nk + kSliceKt - 1) / kSliceKt;
+  // Persistent CTAs: work item w = z * tiles + t (t the output tile in
+  // rasterization order, z = batch * ranges + K range), CTA c takes items
+  // c, c + gridDim.x, ...  The pipeline counters (k tiles for the stage
+  // ring, slices for the two accumulator buffers) run on across items, so a
+  // tile's drain overlaps the next tile's MMAs.
+  const int m_tiles = g.Mp / BM, n_tiles = g.Np / BN;
+  const int tiles = m_tiles * n_tiles;
+  const int items = tiles * g.zs;
+  struct Item {
+    int m_tile, n_tile, z, b, kt0, nk, nslices;
+  };
+  auto item_of = [&](int w) {
+    Item it;
+    it.z = w / tiles;
+    grouped_tile(w - it.z * tiles, m_tiles, n_tiles, kGroupM, &it.m_tile, &it.n_tile);
+    it.b = it.z / g.ranges;
+    const int rg = it.z % g.ranges;
+    it.kt0 = rg * g.kpr;
+    it.nk = max(min(g.KT, it.kt0 + g.kpr) - it.kt0, 0);
+    it.nslices = (it.nk + kSliceKt - 1) / kSliceKt;
+    return it;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -138,65 +152,78 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
 
   if (warp == 0 && lane == 0) {
     // producer: stage s holds Ahi, Alo, Bhi, Blo of one k-tile
-    const float* Ahi = g.Ahi + b * g.sA + (int64_t)m_tile * g.KT * TILE_ELEMS;
-    const float* Alo = g.Alo + b * g.sA + (int64_t)m_tile * g.KT * TILE_ELEMS;
-    const float* Bhi = g.Bhi + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
-    const float* Blo = g.Blo + b * g.sB + (int64_t)n_tile * g.KT * (BN * BK);
-    for (int k = 0; k < nk; ++k) {
-      const int s = k % STAGES;
-      if (k >= STAGES && !mbar_wait_or_abort(&empty[s], ((k / STAGES) - 1) & 1, abort_flag)) {
-        if (!*(volatile int*)abort_flag) atomicExch(g.err, 1);
-        *abort_flag = 1;
-        break;
+    int kg = 0;  // k tiles issued so far (all items)
+    for (int w = blockIdx.x; w < items && !*(volatile int*)abort_flag; w += gridDim.x) {
+      const Item it = item_of(w);
+      const float* Ahi = g.Ahi + it.b * g.sA + (int64_t)it.m_tile * g.KT * TILE_ELEMS;
+      const float* Alo = g.Alo + it.b * g.sA + (int64_t)it.m_tile * g.KT * TILE_ELEMS;
+      const float* Bhi = g.Bhi + it.b * g.sB + (int64_t)it.n_tile * g.KT * (BN * BK);
+      const float* Blo = g.Blo + it.b * g.sB + (int64_t)it.n_tile * g.KT * (BN * BK);
+      for (int k = 0; k < it.nk; ++k, ++kg) {
+        const int s = kg % STAGES;
+        if (kg >= STAGES &&
+            !mbar_wait_or_abort(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag)) {
+          if (!*(volatile int*)abort_flag) atomicExch(g.err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int kt = it.kt0 + k;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        bulk_load(st, Ahi + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
+        bulk_load(st + A_BYTES, Alo + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
+        bulk_load(st + 2 * A_BYTES, Bhi + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
+        bulk_load(st + 2 * A_BYTES + B_BYTES, Blo + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
+        *issued = kg + 1;
       }
-      if (*(volatile int*)abort_flag) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const int kt = kt0 + k;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      bulk_load(st, Ahi + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
-      bulk_load(st + A_BYTES, Alo + (int64_t)kt * TILE_ELEMS, A_BYTES, &full[s]);
-      bulk_load(st + 2 * A_BYTES, Bhi + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
-      bulk_load(st + 2 * A_BYTES + B_BYTES, Blo + (int64_t)kt * (BN * BK), B_BYTES, &full[s]);
-      *issued = k + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: 4 K-steps of 8 per stage, three hi/lo products each; slice
-    // j accumulates in tensor-memory buffer j % 2
+    // jg (counted over all items) accumulates in tensor-memory buffer jg % 2
     const uint32_t idesc = idesc_tf32(BN);
-    for (int k = 0; k < nk; ++k) {
-      const int j = k / kSliceKt, kin = k % kSliceKt, buf = j & 1;
-      if (kin == 0 && j >= 2) {
-        if (!mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1, g.wait)) {
+    int kg = 0, jg = 0;
+    bool stop = false;
+    for (int w = blockIdx.x; w < items && !stop; w += gridDim.x) {
+      const Item it = item_of(w);
+      for (int k = 0; k < it.nk; ++k, ++kg) {
+        const int kin = k % kSliceKt;
+        const int j = jg + k / kSliceKt, buf = j & 1;
+        if (kin == 0 && j >= 2) {
+          if (!mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1, g.wait)) {
+            *abort_flag = 1;
+            atomicExch(g.err, 4);
+            stop = true;
+            break;
+          }
+        }
+        const int s = kg % STAGES;
+        if (!mbar_wait(&full[s], (kg / STAGES) & 1, g.wait)) {
           *abort_flag = 1;
-          atomicExch(g.err, 4);
+          atomicExch(g.err, 2);
+          stop = true;
           break;
         }
-      }
-      const int s = k % STAGES;
-      if (!mbar_wait(&full[s], (k / STAGES) & 1, g.wait)) {
-        *abort_flag = 1;
-        atomicExch(g.err, 2);
-        break;
-      }
-      tc_fence_after();
-      *mmas = k + 1;
-      const uint32_t dt = tmem + (uint32_t)(buf * BN);
-      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t a_hi = base, a_lo = base + A_BYTES;
-      const uint32_t b_hi = base + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+        tc_fence_after();
+        *mmas = kg + 1;
+        const uint32_t dt = tmem + (uint32_t)(buf * BN);
+        const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t a_hi = base, a_lo = base + A_BYTES;
+        const uint32_t b_hi = base + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
-      for (int q = 0; q < BK / 8; ++q) {
-        const uint32_t off = q * 256;  // two 16-byte core matrices along K
-        const uint64_t ah = smem_desc(a_hi + off, g.lbo, g.sbo);
-        const uint64_t al = smem_desc(a_lo + off, g.lbo, g.sbo);
-        const uint64_t bh = smem_desc(b_hi + off, g.lbo, g.sbo);
-        const uint64_t bl = smem_desc(b_lo + off, g.lbo, g.sbo);
-        mma_tf32(dt, ah, bh, idesc, (kin > 0 || q > 0) ? 1u : 0u);
-        mma_tf32(dt, ah, bl, idesc, 1u);
-        mma_tf32(dt, al, bh, idesc, 1u);
+        for (int q = 0; q < BK / 8; ++q) {
+          const uint32_t off = q * 256;  // two 16-byte core matrices along K
+          const uint64_t ah = smem_desc(a_hi + off, g.lbo, g.sbo);
+          const uint64_t al = smem_desc(a_lo + off, g.lbo, g.sbo);
+          const uint64_t bh = smem_desc(b_hi + off, g.lbo, g.sbo);
+          const uint64_t bl = smem_desc(b_lo + off, g.lbo, g.sbo);
+          mma_tf32(dt, ah, bh, idesc, (kin > 0 || q > 0) ? 1u : 0u);
+          mma_tf32(dt, ah, bl, idesc, 1u);
+          mma_tf32(dt, al, bh, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+        if (kin == kSliceKt - 1 || k == it.nk - 1) mma_commit(&acc_full[buf]);
       }
-      mma_commit(&empty[s]);
-      if (kin == kSliceKt - 1 || k == nk - 1) mma_commit(&acc_full[buf]);
+      jg += it.nslices;
     }
   } else if (warp >= 2) {
     // epilogue: row r of the tile lives in TMEM lane r; this warp adds the
@@ -204,67 +231,75 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
     const int q = warp % 4;
     const int h = (warp - 2) / 4;
     const int row = 32 * q + lane;
-    float sum[HALF], cmp[HALF];
+    int jg = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x) {
+      const Item it = item_of(w);
+      float sum[HALF], cmp[HALF];
 #pragma unroll
-    for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
-    bool ok = nk > 0;
+      for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
+      bool ok = it.nk > 0 && !*(volatile int*)abort_flag;
 #pragma unroll 1
-    for (int j = 0; j < nslices; ++j) {
-      const int buf = j & 1;
-      if (!mbar_wait(&acc_full[buf], (j >> 1) & 1, g.wait)) {
-        ok = false;
-        *abort_flag = 1;
-        atomicExch(g.err, 3);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + h * HALF);
-#pragma unroll
-      for (int c = 0; c < HALF / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(taddr + (uint32_t)(c * 32), r);
-#pragma unroll
-        for (int v = 0; v < 32; ++v) two_sum_acc(sum[c * 32 + v], cmp[c * 32 + v], __uint_as_float(r[v]));
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
-    }
-    if (ok && g.ranges == 1 && !g.force_p) {
-      // map (row', col') of D = A'B'^T onto one real or imaginary part of C
-      const int mr = m_tile * BM + row;
-      int m = mr, part = 0;
-      if (g.mode == 1 && mr >= g.M) {
-        m = mr - g.M;
-        part = 1;
-      }
-      const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
-      const bool unit = g.alpha == 1.0 || g.alpha == -1.0;
-      const float sgn = g.alpha == -1.0 ? -1.0f : 1.0f;
-      if (row_ok) {
-        const int64_t rbase = (int64_t)b * g.sC + (int64_t)m * g.ldm;
-#pragma unroll
-        for (int v = 0; v < HALF; ++v) {
-          const int nr = n_tile * BN + h * HALF + v;
-          int n = nr, pt = part;
-          if (g.mode == 2 && nr >= g.N) {
-            n = nr - g.N;
-            pt = 1;
-          }
-          if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-          double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
-          const float f = sum[v] + cmp[v];
-          const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
-          *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
+      for (int jl = 0; ok && jl < it.nslices; ++jl) {
+        const int j = jg + jl, buf = j & 1;
+        if (!mbar_wait(&acc_full[buf], (j >> 1) & 1, g.wait)) {
+          ok = false;
+          *abort_flag = 1;
+          atomicExch(g.err, 3);
+          break;
         }
-      }
-    } else if (ok) {
-      float4* dst = reinterpret_cast<float4*>(
-          g.P + ((int64_t)z * g.Mp + (int64_t)m_tile * BM + row) * g.Np +
-          (int64_t)n_tile * BN + h * HALF);
+        tc_fence_after();
+        const uint32_t taddr =
+            tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + h * HALF);
 #pragma unroll
-      for (int v = 0; v < HALF / 2; ++v)
-        dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
+        for (int c = 0; c < HALF / 32; ++c) {
+          uint32_t r[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), r);
+#pragma unroll
+          for (int v = 0; v < 32; ++v)
+            two_sum_acc(sum[c * 32 + v], cmp[c * 32 + v], __uint_as_float(r[v]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      }
+      jg += it.nslices;
+      if (!ok) break;
+      if (g.ranges == 1 && !g.force_p) {
+        // map (row', col') of D = A'B'^T onto one real or imaginary part of C
+        const int mr = it.m_tile * BM + row;
+        int m = mr, part = 0;
+        if (g.mode == 1 && mr >= g.M) {
+          m = mr - g.M;
+          part = 1;
+        }
+        const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
+        const bool unit = g.alpha == 1.0 || g.alpha == -1.0;
+        const float sgn = g.alpha == -1.0 ? -1.0f : 1.0f;
+        if (row_ok) {
+          const int64_t rbase = (int64_t)it.b * g.sC + (int64_t)m * g.ldm;
+#pragma unroll
+          for (int v = 0; v < HALF; ++v) {
+            const int nr = it.n_tile * BN + h * HALF + v;
+            int n = nr, pt = part;
+            if (g.mode == 2 && nr >= g.N) {
+              n = nr - g.N;
+              pt = 1;
+            }
+            if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
+            double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
+            const float f = sum[v] + cmp[v];
+            const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
+            *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
+          }
+        }
+      } else {
+        float4* dst = reinterpret_cast<float4*>(
+            g.P + ((int64_t)it.z * g.Mp + (int64_t)it.m_tile * BM + row) * g.Np +
+            (int64_t)it.n_tile * BN + h * HALF);
+#pragma unroll
+        for (int v = 0; v < HALF / 2; ++v)
+          dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
+      }
     }
   }
   // teardown after an abandoned pipeline: let the issued copies land and the
@@ -681,7 +716,11 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.sC = d.strideC;
   g.alpha = d.alpha;
   g.beta = d.beta;
-  dim3 grid((p.Np / kBN) * (p.Mp / BM), 1, d.batch * p.ranges);
+  g.zs = d.batch * p.ranges;
+  // persistent CTAs: one per SM (the kernel takes most of the shared memory)
+  const int64_t items = (int64_t)(p.Np / kBN) * (p.Mp / BM) * g.zs;
+  if (items > 0x7fffffff) throw Error(-1, "gemm_tc: too many tiles");
+  const int grid = (int)std::min<int64_t>(items, 148);
   tc_gemm_kernel<kBN, kStages><<<grid, THREADS, kSmemBytes, st>>>(g);
   RT_CHECK_LAUNCH();
 }

@@ -7,10 +7,10 @@ cumulant integrand and C_{n+1} (Eqs. 5-6).  Metric: time steps/s, whole job
 (sum over ranks; ranks are independent replicas).
 
 Default workload: the ESCA-shaped propagation O=50, V=450, Nchol=1800,
-dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-BF16
-form (contractions as BF16 digit-plane products on the tensor cores, FP64
-update, cumulant and phases).  Beside it, on the same inputs: the split-TF32
-form and the FP64-accurate emulated form (a few steps each), an estimate of the
+dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-TF32
+form (contractions as split-TF32 products on the tensor cores, FP64 update,
+cumulant and phases).  Beside it, on the same inputs: the split-BF16 form
+and the FP64-accurate emulated form (a few steps each), an estimate of the
 plain FP64 (DFMA) form from its measured contraction rate, and the
 formaldehyde-shaped FP64 workload (O=8, V=100, Nchol=400) as a secondary
 line.  Every form reports time per step and per micro-iteration (the
@@ -51,7 +51,7 @@ PRODUCTS = {"split_tf32": 3, "split_bf16": 6, "fp64_ozaki": 28, "fp64": 1}
 # arithmetic type of the contractions, by form
 DTYPE = {"split_tf32": "tf32", "split_bf16": "bf16", "fp64_ozaki": "bf16", "fp64": "f64"}
 KERNEL = {"split_tf32": ("tc_gemm_kernel", "gemm_tc.cu"),
-          "split_bf16": ("oz_gemm_kernel<3,64>", "gemm_oz.cu"),
+          "split_bf16": ("oz_gemm_kernel<3,128>", "gemm_oz.cu"),
           "fp64_ozaki": ("oz_gemm_kernel<7,64>", "gemm_oz.cu"),
           "fp64": ("gemm_kernel (FP64 DFMA)", "gemm_f64.cu")}
 
@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c5_esca_large")
-    ap.add_argument("--form", choices=FORMS, default="split_bf16",
+    ap.add_argument("--form", choices=FORMS, default="split_tf32",
                     help="precision form of the headline line")
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)

@@ -311,6 +311,51 @@ __global__ void oz_digits_kernel(PackArgs p, int batch) {
   }
 }
 
+// Digit planes of a source whose rows are contiguous (rows_fast): a warp
+// packs 32 rows x 32 columns, lane = row, so each of its loads is one
+// coalesced run across the warp; each lane writes one 16-byte core-matrix
+// row per plane and column group of 8.
+template <int S>
+__global__ void oz_digits_rows_kernel(PackArgs p, int batch) {
+  const int KT = p.Kp / BK;
+  const int64_t groups = (int64_t)(p.Rp / 32) * KT;  // 32-row x 32-column blocks per batch entry
+  const int64_t units = groups * batch;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < units; w += nwarps) {
+    const int b = (int)(w / groups);
+    const int64_t gq = w - (int64_t)b * groups;
+    const int rg = (int)(gq / KT), kt = (int)(gq % KT);
+    const int rp = rg * 32 + lane;
+    const int E = row_exp(p.expo[(int64_t)b * p.Rp + rp]);
+    const int rt = rp / p.rowtile, rr = rp % p.rowtile;
+#pragma unroll 1
+    for (int kg = 0; kg < BK / 8; ++kg) {
+      uint32_t packed[S][4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        int d0[S], d1[S];
+        digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
+        digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          // the fused three-plane form stores plane s pre-scaled by 2^(-8 s)
+          const float ws = S == 3 ? __int_as_float((127 - 8 * s) << 23) : 1.0f;
+          const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn((float)d0[s] * ws),
+                                                      __float2bfloat16_rn((float)d1[s] * ws));
+          packed[s][j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+      }
+      const int64_t off = (int64_t)b * p.s_out + ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
+                          ((rr / 8) * (BK / 8) + kg) * 64 + (rr % 8) * 8;
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        *reinterpret_cast<uint4*>(p.planes + s * p.plane_elems + off) =
+            make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- MMA kernel
 struct KArgs {
   const __nv_bfloat16 *A, *B;  // digit planes
@@ -732,12 +777,19 @@ void pack(PackArgs pa, int64_t elems, int batch, int S, cudaStream_t st) {
         pa, batch);
   }
   RT_CHECK_LAUNCH();
-  const int64_t units = elems / 256;  // 8 x 32 blocks, one warp each
-  const int grid = (int)std::min<int64_t>((units * 32 + 255) / 256, 148 * 16);
-  if (S == 3)
+  // 32 x 32 blocks (rows-fast sources) or 8 x 32 blocks, one warp each
+  const int64_t units = elems / (pa.rows_fast ? 1024 : 256);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units * 32 + 255) / 256, 148 * 16));
+  if (pa.rows_fast) {
+    if (S == 3)
+      oz_digits_rows_kernel<3><<<grid, 256, 0, st>>>(pa, batch);
+    else
+      oz_digits_rows_kernel<7><<<grid, 256, 0, st>>>(pa, batch);
+  } else if (S == 3) {
     oz_digits_kernel<3><<<grid, 256, 0, st>>>(pa, batch);
-  else
+  } else {
     oz_digits_kernel<7><<<grid, 256, 0, st>>>(pa, batch);
+  }
   RT_CHECK_LAUNCH();
 }
 

@@ -114,8 +114,10 @@ __global__ void permute_tiled_kernel(const double* __restrict__ in, double* __re
   const int64_t x0 = (int64_t)(blockIdx.x % tx_tiles) * 32, y0 = (int64_t)(blockIdx.x / tx_tiles) * 32;
   const TI* tin = reinterpret_cast<const TI*>(in);
   const bool rd = op == kAdd || op == kSub || (op == kGeneral && beta != 0.0);
-  for (int64_t r = blockIdx.y; r < t.nrest_total; r += gridDim.y) {
-    int64_t rem = r, ib = 0, ob = 0;
+  auto bases = [&](int64_t r, int64_t& ib, int64_t& ob) {
+    int64_t rem = r;
+    ib = 0;
+    ob = 0;
     for (int k = 0; k < t.nrest; ++k) {
       const int64_t q = rem / t.rest_dim[k];
       const int64_t i = rem - q * t.rest_dim[k];
@@ -123,28 +125,52 @@ __global__ void permute_tiled_kernel(const double* __restrict__ in, double* __re
       ob += i * t.rest_out[k];
       rem = q;
     }
-    __syncthreads();  // the previous rest index finished reading the tile
-    for (int xi = threadIdx.y; xi < 32; xi += blockDim.y) {
-      const int64_t x = x0 + xi, y = y0 + threadIdx.x;
-      if (x < t.X && y < t.Y) tile[xi][threadIdx.x] = tin[ib + x * t.in_sx + y];
+  };
+  constexpr int R = 32 / 8;  // tile rows per thread (blockDim.y = 8)
+  // software pipeline: the loads of the next rest index are issued before
+  // the stores of the current one
+  TI v[R];
+  int64_t r = blockIdx.y, ib = 0, ob = 0;
+  auto load = [&](int64_t ibase) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int64_t x = x0 + threadIdx.y + 8 * u, y = y0 + threadIdx.x;
+      if (x < t.X && y < t.Y) v[u] = tin[ibase + x * t.in_sx + y];
     }
+  };
+  if (r < t.nrest_total) {
+    bases(r, ib, ob);
+    load(ib);
+  }
+  for (; r < t.nrest_total; r += gridDim.y) {
+    __syncthreads();  // the previous rest index finished reading the tile
+#pragma unroll
+    for (int u = 0; u < R; ++u) tile[threadIdx.y + 8 * u][threadIdx.x] = v[u];
     __syncthreads();
-    for (int yi = threadIdx.y; yi < 32; yi += blockDim.y) {
+    const int64_t ob_cur = ob;
+    const int64_t rn = r + gridDim.y;
+    if (rn < t.nrest_total) {
+      bases(rn, ib, ob);
+      load(ib);
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int yi = threadIdx.y + 8 * u;
       const int64_t x = x0 + threadIdx.x, y = y0 + yi;
       if (x >= t.X || y >= t.Y) continue;
-      const int64_t o = ob + y * t.out_sy + x;
+      const int64_t o = ob_cur + y * t.out_sy + x;
       if constexpr (CPO) {
         double2* po = reinterpret_cast<double2*>(out) + o;
         const double2 c = rd ? *po : make_double2(0.0, 0.0);
-        double2 v;
+        double2 w;
         if constexpr (CPI) {
-          v = tile[threadIdx.x][yi];
+          w = tile[threadIdx.x][yi];
         } else {
-          v = make_double2(tile[threadIdx.x][yi], 0.0);
+          w = make_double2(tile[threadIdx.x][yi], 0.0);
         }
         double2 res;
-        res.x = axop(op, v.x, c.x, alpha, beta);
-        res.y = CPI ? axop(op, v.y, c.y, alpha, beta)
+        res.x = axop(op, w.x, c.x, alpha, beta);
+        res.y = CPI ? axop(op, w.y, c.y, alpha, beta)
                     : (rd ? (op == kGeneral ? beta * c.y : c.y) : 0.0);
         *po = res;
       } else {
@@ -543,13 +569,16 @@ __device__ __forceinline__ double recip_newton(double x) {
   return r;
 }
 
-// One block per row of an amplitude block: a T1 row (i) holds nV entries,
-// a T2 row (i, j) nV*nV entries (a, b).  The row's occupied part of the
+// One block per row of an amplitude block, or per segment of kUpdateSeg
+// entries of a long row: a T1 row (i) holds nV entries, a T2 row (i, j)
+// nV*nV entries (a, b).  The row's occupied part of the
 // denominator, its spins and its pad status are fixed per block; the
 // virtual part comes from two table reads.  With R' = R - D t the update of
 // Eq. 9 reduces to
 //   t_new = [t_n + i h (R_n + R_k - D t_k)] (1 + i h D) / (1 + (h D)^2),
 // h = dt/2, and the convergence measure is max |t_new - t_k|^2.
+constexpr int kUpdateSeg = 2048;  // entries per block of a T2 row
+
 __global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
                                  const double* __restrict__ fv_a, const double* __restrict__ fo_b,
                                  const double* __restrict__ fv_b, double dt,
@@ -559,9 +588,14 @@ __global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
   __shared__ unsigned long long red[kThreads / 32];
   const int nO = g.nO, nV = g.nV;
   const int rows1 = 2 * nO, rows = rows1 + 3 * nO * nO;
+  const int segs = (nV * nV + kUpdateSeg - 1) / kUpdateSeg;  // segments of a T2 row
+  const int units = rows1 + 3 * nO * nO * segs;
   const double h = 0.5 * dt;
   unsigned long long m = 0ull;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+  for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    // unit -> (row, segment): a T1 row is one unit, a T2 row `segs` units
+    const int row = unit < rows1 ? unit : rows1 + (unit - rows1) / segs;
+    const int seg = unit < rows1 ? 0 : (unit - rows1) % segs;
     int blk, i, j;
     int64_t base;
     int len;
@@ -590,7 +624,9 @@ __global__ void am_update_kernel(AmpGeom g, const double* __restrict__ fo_a,
       row_pad = row_pad || (s2 == 1 && j == g.core);
       Drow -= (s2 ? fo_b : fo_a)[j];
     }
-    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+    // a T1 row is taken whole; a T2 row in segments of kUpdateSeg entries
+    const int q0 = seg * kUpdateSeg, q1 = blk < 2 ? len : min(len, q0 + kUpdateSeg);
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
       int a, b;
       if (blk >= 2) {
         a = q / nV;
@@ -1122,8 +1158,9 @@ void am_update(const AmpGeom& g, const double* fo_a, const double* fv_a, const d
                const double* fv_b, double dt, const double* tn, const double* Rn,
                const double* tk_in, double* tk_out, const double* Rk,
                unsigned long long* maxdiff_bits, cudaStream_t st) {
-  const int rows = 2 * g.nO + 3 * g.nO * g.nO;
-  am_update_kernel<<<std::min(rows, 148 * 16), kThreads, 0, st>>>(
+  const int segs = (g.nV * g.nV + kUpdateSeg - 1) / kUpdateSeg;
+  const int units = 2 * g.nO + 3 * g.nO * g.nO * segs;
+  am_update_kernel<<<std::min(units, 148 * 16), kThreads, 0, st>>>(
       g, fo_a, fv_a, fo_b, fv_b, dt, reinterpret_cast<const double2*>(tn),
       reinterpret_cast<const double2*>(Rn), reinterpret_cast<const double2*>(tk_in),
       reinterpret_cast<double2*>(tk_out), reinterpret_cast<const double2*>(Rk), maxdiff_bits);

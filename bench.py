@@ -74,8 +74,8 @@ def parse_args():
     ap.add_argument("--no-ozaki", action="store_true", help="skip the emulated-FP64 form")
     ap.add_argument("--no-secondary", action="store_true", help="skip the FP64 c2 line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serving-requests", type=int, default=16)
-    ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="scaled",
+    ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="c4",
                     help="scaled: small shapes, all three forms; c4: the production request "
                          "shapes (O~U{4..24}, V~U{40..240}) with steps cut to U{4..16}, tensor-core "
                          "forms only, autotuner off (serial and served runs on equal terms)")
@@ -519,9 +519,9 @@ def serving_block(P, args):
                                               args.tol, "c4")}
         finally:
             del os.environ["RTEOM_AUTOTUNE"]
-    return {"workload": "scaled core-hole mix: 16 requests, O~U{4..8}, V~U{20..48}, "
-                        "Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x the "
-                        "mean service rate, 8 slots",
+    return {"workload": f"scaled core-hole mix: {args.serving_requests} requests, O~U{{4..8}}, "
+                        "V~U{20..48}, Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x "
+                        "the mean service rate, 8 slots",
             "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
             "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests, args.tol),
             "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests, args.tol)}

@@ -14,6 +14,8 @@ namespace rteom {
 
 namespace {
 
+constexpr int64_t kMin3mK = 2048;  // shortest K of a 3M complex product
+
 struct Parsed {
   std::string a, b, c;
 };
@@ -768,7 +770,12 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   };
   // Complex x complex on the tensor cores as three real products (3M)
   // instead of the four of the real embedding, for operands packed per call.
+  // It writes three partial products and combines them, so it pays only when
+  // the saved quarter of the MMA work outweighs that pass over the output:
+  // from about 2000 of K on (per output element, 0.25 * 8 K products against
+  // about 40 bytes of partials and output).
   const bool use3m = packed_path && allow_3m && A.cplx && B.cplx && Bt == 1 && !pack_only &&
+                     Kt >= kMin3mK &&
                      !cA && !cB && !A.constant && !B.constant && !holdA && !holdB &&
                      !held_.count(A.p) && !held_.count(B.p);
   if (use3m) {

@@ -739,13 +739,17 @@ Plan plan(const GemmDesc& d, int S) {
 __global__ void oz_combine_3m_kernel(FinArgs f) {
   const int64_t per = (int64_t)f.M * f.N;
   const int64_t zs = (int64_t)f.Mp * f.Np;
+  // the partials and the output never overlap
+  const float2* __restrict__ Pr = f.P;
+  double* __restrict__ Cr = f.C;
+#pragma unroll 2
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(e / f.N), n = (int)(e % f.N);
     double v[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+      const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
       float su = 0.0f, cm = 0.0f;
       for (int z = 0; z < f.ranges; ++z) {
         const float2 q = pp[z * zs];
@@ -756,7 +760,7 @@ __global__ void oz_combine_3m_kernel(FinArgs f) {
                           row_exp(f.eb[(int64_t)b * f.Np + n]));
     }
     const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
-    double* c = f.C + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+    double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
     const double a = f.alpha;
     c[0] = f.beta == 0.0 ? a * re : (f.beta == 1.0 ? c[0] + a * re : fma(f.beta, c[0], a * re));
     c[1] = f.beta == 0.0 ? a * im : (f.beta == 1.0 ? c[1] + a * im : fma(f.beta, c[1], a * im));

@@ -563,6 +563,10 @@ Plan plan(const GemmDesc& d) {
 __global__ void tc_combine_3m_kernel(FinArgs f) {
   const int64_t per = (int64_t)f.M * f.N;
   const int64_t zs = (int64_t)f.Mp * f.Np;
+  // the partials and the output never overlap
+  const float2* __restrict__ Pr = f.P;
+  double* __restrict__ Cr = f.C;
+#pragma unroll 2
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(e / f.N), n = (int)(e % f.N);
@@ -572,7 +576,7 @@ __global__ void tc_combine_3m_kernel(FinArgs f) {
     float s[3], cm[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+      const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
       s[b] = 0.0f;
       cm[b] = 0.0f;
       for (int z = 0; z < f.ranges; ++z) {
@@ -588,7 +592,7 @@ __global__ void tc_combine_3m_kernel(FinArgs f) {
     two_sum_acc(im_h, im_l, -s[1]);                 // P3 - P1 - P2
     const double re = f32_to_f64(re_h) + f32_to_f64(re_l);
     const double im = f32_to_f64(im_h) + f32_to_f64(im_l);
-    double* c = f.C + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+    double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
     const double a = f.alpha;
     const bool unit = a == 1.0 || a == -1.0;
     const double vr = unit ? (a < 0 ? neg_f64(re) : re) : a * re;

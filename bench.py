@@ -17,7 +17,7 @@ line.  Every form reports time per step and per micro-iteration (the
 paper's metric) and TFLOP/s against measured peaks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--form split_tf32|split_bf16|fp64_ozaki|fp64]
+                  [--workload NAME] [--form split_tf32|split_bf16|split_fp16|fp64_ozaki|fp64]
 
 Prints one JSON line on rank 0.
 """
@@ -45,13 +45,16 @@ METRIC = "time_steps_per_s"
 UNIT = "steps/s"
 MEASURED = os.path.join(HERE, "MEASURED_PEAKS.json")
 PROFILES = os.path.join(HERE, "profiles")
-FORMS = ("split_tf32", "split_bf16", "fp64_ozaki", "fp64")
+FORMS = ("split_tf32", "split_bf16", "split_fp16", "fp64_ozaki", "fp64")
+SPLIT_FORMS = ("split_tf32", "split_bf16", "split_fp16")
 # tensor-core products executed per FP64-equivalent multiply-add, by form
-PRODUCTS = {"split_tf32": 3, "split_bf16": 6, "fp64_ozaki": 28, "fp64": 1}
+PRODUCTS = {"split_tf32": 3, "split_bf16": 6, "split_fp16": 3, "fp64_ozaki": 28, "fp64": 1}
 # arithmetic type of the contractions, by form
-DTYPE = {"split_tf32": "tf32", "split_bf16": "bf16", "fp64_ozaki": "bf16", "fp64": "f64"}
+DTYPE = {"split_tf32": "tf32", "split_bf16": "bf16", "split_fp16": "fp16", "fp64_ozaki": "bf16",
+         "fp64": "f64"}
 KERNEL = {"split_tf32": ("tc_gemm_kernel", "gemm_tc.cu"),
           "split_bf16": ("oz_gemm_kernel<3,128>", "gemm_oz.cu"),
+          "split_fp16": ("oz_gemm_kernel<2,128>", "gemm_oz.cu"),
           "fp64_ozaki": ("oz_gemm_kernel<7,64>", "gemm_oz.cu"),
           "fp64": ("gemm_kernel (FP64 DFMA)", "gemm_f64.cu")}
 
@@ -277,11 +280,15 @@ def peaks_block(torch, dev):
 
 
 def peak_for(form, peaks, sustained=True):
-    """Tensor-core peak of a form's products: BF16 digit planes (split-BF16,
-    emulated FP64), TF32 (split-TF32) or the FP64 pipe (FP64)."""
-    if form in ("split_bf16", "fp64_ozaki"):
+    """Tensor-core peak of a form's products: 16-bit planes (split-BF16,
+    split-FP16, emulated FP64; FP16 and BF16 products run at one rate),
+    TF32 (split-TF32) or the FP64 pipe (FP64)."""
+    if form in ("split_bf16", "split_fp16", "fp64_ozaki"):
         v = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops")
-        return v, "bf16_tflops_sustained (of measured)" if sustained else "bf16_tflops (of measured)"
+        src = "bf16_tflops_sustained (of measured)" if sustained else "bf16_tflops (of measured)"
+        if form == "split_fp16":
+            src += "; FP16 products run at the BF16 rate (both kind::f16)"
+        return v, src
     if form == "split_tf32":
         v = peaks.get("tf32_tflops_sustained" if sustained else "tf32_tflops")
         return v, "tf32, cuBLAS measured in this run (of measured)"
@@ -323,7 +330,8 @@ def barrier(world):
 
 def precision_of(P, form):
     return {"split_tf32": P.RTEOM_SPLIT_TF32, "split_bf16": P.RTEOM_SPLIT_BF16,
-            "fp64_ozaki": P.RTEOM_FP64_OZAKI, "fp64": P.RTEOM_FP64}[form]
+            "split_fp16": P.RTEOM_SPLIT_FP16, "fp64_ozaki": P.RTEOM_FP64_OZAKI,
+            "fp64": P.RTEOM_FP64}[form]
 
 
 def pinned_problem(torch, p):
@@ -557,7 +565,7 @@ def run_ours(args):
     # figures compare forms whatever the micro-iterations per step)
     side = {}
     if not args.no_forms:
-        others = [f for f in ("split_tf32", "split_bf16") if f != args.form]
+        others = [f for f in SPLIT_FORMS if f != args.form]
         if not args.no_ozaki and args.form != "fp64_ozaki":
             others.append("fp64_ozaki")
         for f in others:
@@ -636,7 +644,7 @@ def run_ours(args):
                    "form": args.form,
                    "arithmetic": "contractions as split products on the tensor cores with FP32 "
                                  "accumulation; Adams-Moulton update, cumulant and phases FP64"
-                   if args.form in ("split_tf32", "split_bf16") else
+                   if args.form in SPLIT_FORMS else
                    ("contractions FP64-accurate from BF16 digit planes" if args.form ==
                     "fp64_ozaki" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent core holes, no collectives)",

@@ -83,6 +83,17 @@ extern "C" {
                                  compensated pairs (about 2^-48 relative to the
                                  row scales); contractions below 5e7 FLOP and
                                  every other step as in RTEOM_FP64 */
+#define RTEOM_SPLIT_FP16  4   /* contractions of at least 5e7 FLOP (and smaller
+                                 ones the autotuner finds faster there) on the
+                                 16-bit tensor cores as split-FP16 products:
+                                 each operand row scaled by a power of two
+                                 into FP16's range, x = hi + lo in two FP16
+                                 planes (11 significant bits each, as split
+                                 TF32), hi*hi + hi*lo + lo*hi in one FP32
+                                 accumulator over chunks of 512 of K, chunks
+                                 added as compensated pairs; twice the TF32
+                                 tensor rate; complex x complex products as
+                                 three real ones; every other step FP64 */
 
 /* flags for rteom_create */
 #define RTEOM_FLAG_CUMULANT_NO_FOV 1  /* cumulant integrand without sum f_ia t_i^a,
@@ -133,8 +144,8 @@ typedef struct rteom_ctx rteom_ctx;
  *             NULL; t1_gs/t2_gs only enter E_N^corr of Eq. 3:
  *             E = sum_ijab [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
  *  core_index spatial index c of the ionised orbital, 0 <= c < O
- *  precision  RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 or
- *             RTEOM_FP64_OZAKI
+ *  precision  RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32,
+ *             RTEOM_FP64_OZAKI or RTEOM_SPLIT_FP16
  *  flags      RTEOM_FLAG_* bits
  *  cuda_stream cudaStream_t to run on, or NULL for a non-blocking stream
  *             created and owned by the context

@@ -16,7 +16,7 @@ from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: 
                    RTEOM_FLAG_LADDER_CHOLESKY, RTEOM_FLAG_ANDERSON,
                    RTEOM_FP64, RTEOM_OK, RTEOM_REQ_CANCELLED, RTEOM_REQ_DONE, RTEOM_REQ_FAILED,
                    RTEOM_REQ_QUEUED, RTEOM_REQ_RUNNING, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32,
-                   RTEOM_FP64_OZAKI)
+                   RTEOM_FP64_OZAKI, RTEOM_SPLIT_FP16)
 
 __all__ = ["Propagator", "Server", "RteomError", "block_shapes", "split_blocks", "join_blocks"]
 

@@ -18,6 +18,7 @@ RTEOM_FP64 = 0
 RTEOM_SPLIT_BF16 = 1
 RTEOM_SPLIT_TF32 = 2
 RTEOM_FP64_OZAKI = 3
+RTEOM_SPLIT_FP16 = 4
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
 RTEOM_FLAG_LADDER_CHOLESKY = 2
 RTEOM_FLAG_ANDERSON = 4

@@ -10,7 +10,22 @@
 #include <string>
 #include <vector>
 
+#include "../../include/rteom.h"
+
 namespace rteom {
+
+// Precision forms of rteom_create: which run their contractions as 16-bit
+// planes on the tensor cores, and how many planes per operand.
+inline bool valid_precision(int p) {
+  return p == RTEOM_FP64 || p == RTEOM_SPLIT_BF16 || p == RTEOM_SPLIT_TF32 ||
+         p == RTEOM_FP64_OZAKI || p == RTEOM_SPLIT_FP16;
+}
+inline bool sliced_form(int p) {
+  return p == RTEOM_FP64_OZAKI || p == RTEOM_SPLIT_BF16 || p == RTEOM_SPLIT_FP16;
+}
+inline int planes_of(int p) {
+  return p == RTEOM_SPLIT_BF16 ? 3 : (p == RTEOM_SPLIT_FP16 ? 2 : 7);
+}
 
 // Error carried from deep inside the library to the C ABI boundary.
 struct Error : std::runtime_error {

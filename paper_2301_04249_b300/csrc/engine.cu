@@ -176,19 +176,27 @@ std::vector<GemmChoice> f64_candidates(const GemmDesc& g) {
   return out;
 }
 
-// The emulated-FP64 kernel tiles A' in 128 rows and B' in 32 or 64: a GEMM
-// whose A' has few rows runs as C^T = B^T A^T (output written transposed)
-// when that pads much less.
+// The digit-plane kernels tile A' in 128 rows and B' in 32 to 256 rows: a
+// GEMM runs as C^T = B^T A^T (output written transposed) when that pads much
+// less, or, with K up to kOzShortK, when its output is row-major and the
+// transposed problem pads about as much.  The kernel's drain gives each lane
+// one GEMM row, so only the transposed problem stores a row-major output
+// coalesced (adjacent lanes, adjacent addresses), and with short K those
+// stores, not the MMAs, set the time (a 2255 x 203401 x 1800 product ran at
+// a third of the tensor peak with lane-per-row stores).
+constexpr int64_t kOzShortK = 4096;
+
 int64_t oz_padded(int64_t ra, int64_t rb, int S) {
-  // B' tiles of 32 rows when narrow, else 128 (three planes) or 64 (seven)
-  const int64_t bn = rb <= 32 ? 32 : (S == 3 ? 128 : 64);
+  const int64_t bn = oz_tile_n(rb, S);
   return (ra + 127) / 128 * 128 * ((rb + bn - 1) / bn * bn);
 }
 
 bool oz_swap(const GemmDesc& g, int S) {
   const int64_t ra = (g.Acplx && !g.Bcplx) ? 2 * g.M : g.M, rb = g.Bcplx ? 2 * g.N : g.N;
   const int64_t sa = (g.Bcplx && !g.Acplx) ? 2 * g.N : g.N, sb = g.Acplx ? 2 * g.M : g.M;
-  return 4 * oz_padded(sa, sb, S) < 3 * oz_padded(ra, rb, S);
+  const int64_t straight = oz_padded(ra, rb, S), transposed = oz_padded(sa, sb, S);
+  if (4 * transposed < 3 * straight) return true;
+  return !g.transC && g.M > 1 && g.K <= kOzShortK && 10 * transposed <= 11 * straight;
 }
 
 GemmDesc swapped(const GemmDesc& g) {
@@ -531,9 +539,9 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
       autotune && !use_tc && !use_oz && !gemm_f64_is_gemv(g) && flops0 <= tune_max_flops;
   const bool tc_ok = tensor_cores && flops0 >= tc_tune_min_flops;
   const bool oz_ok = fp64_emulation && flops0 >= tc_tune_min_flops;
-  // form of the key: FP64 only, or with the split-TF32, 7-plane or 3-plane
-  // tensor-core candidate
-  const int form = tc_ok ? 1 : (oz_ok ? (oz_planes == 3 ? 3 : 2) : 0);
+  // form of the key: FP64 only, or with the split-TF32, 7-plane, 3-plane or
+  // FP16 two-plane tensor-core candidate
+  const int form = tc_ok ? 1 : (oz_ok ? (oz_planes == 3 ? 3 : (oz_planes == 2 ? 4 : 2)) : 0);
   const std::string tkey = tunable ? tune_key(g, form) : std::string();
   GemmChoice choice;
   bool chosen = tunable && tune_lookup(tkey, &choice);

@@ -40,8 +40,9 @@ class Engine {
   // waits run out on purpose (failure detection without a GPU fault).
   long long tc_wait_cycles = 0;
   // Digit slicing: contractions of at least oz_min_flops run as products of
-  // oz_planes BF16 digit planes on the tensor cores (7 planes: FP64-level
-  // accuracy; 3 planes: the split-BF16 form)
+  // oz_planes 16-bit planes on the tensor cores (7 BF16 digit planes:
+  // FP64-level accuracy; 3: the split-BF16 form; 2 FP16 hi/lo planes: the
+  // split-FP16 form)
   bool fp64_emulation = false;
   int oz_planes = 7;
   // complex x complex products on the tensor cores as three real GEMMs (3M)

@@ -21,9 +21,17 @@
 // and runs on the tensor pipe instead of the FP64 pipe (about two operations
 // per clock per SM on this part).
 //
+// The split-FP16 form (S = 2) uses the same machinery with two FP16 planes
+// instead of integer digits: under the row scale, y = x 2^(15 - E) (|y| <
+// 2^15, rounded to FP32), hi = fp16(y) and lo = fp16(y - hi), so x = 2^(E -
+// 15) (hi + lo) to about 2^-22 of |x| (11 significant bits per plane, as in
+// split TF32; below FP16's normal range about 2^-40 of the row scale).  The
+// three products hi hi, hi lo and lo hi accumulate in one FP32 accumulator,
+// not exactly, and run at the 16-bit tensor rate, twice the TF32 rate.
+//
 // Operand layout: digit planes [S][batch][row tile][k tile][rows x 32] of
-// BF16 in 8 x 8 core matrices (K-major, no swizzle; 128 B between core
-// matrices along K, 512 B between 8-row groups).  A stage holds all planes of
+// BF16 (FP16 for S = 2) in 8 x 8 core matrices (K-major, no swizzle; 128 B
+// between core matrices along K, 512 B between 8-row groups).  A stage holds all planes of
 // one k tile of A (128 rows) and B (64 rows for seven planes, 84 KB, two
 // stages; 128 rows for three, 48 KB, four stages).  Tensor memory holds the
 // accumulators of one chunk (seven planes: 7 diagonals x 64 columns; three
@@ -37,6 +45,7 @@
 // Every wait is bounded; on expiry the CTA records an error code, lets its
 // copies land, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <climits>
@@ -70,14 +79,22 @@ constexpr int kNanExp = INT_MAX / 4;       // ... of a row holding an infinity o
 // at their relative weights (rounding about 2^-24 of a term 2^-8 below the
 // leading one).  That leaves room for 128-column tiles, two accumulator sets
 // and chunks twice as long.
+//
+// Two planes (the split-FP16 form) keep one accumulator for all three
+// products; its chunk sums are rounded FP32 sums over 512 of K.
 template <int S, int BN>
 struct Cfg {
   static constexpr bool FUSED = S == 3;
-  static constexpr int NACC = FUSED ? 2 : S;       // accumulators per set
-  static constexpr int CHUNK_KT = FUSED ? 16 : (S > 4 ? 4 : 8);  // k tiles per chunk
+  static constexpr bool F16 = S == 2;              // FP16 hi/lo planes
+  static constexpr int NACC = F16 ? 1 : (FUSED ? 2 : S);  // accumulators per set
+  static constexpr int CHUNK_KT = (FUSED || F16) ? 16 : (S > 4 ? 4 : 8);  // k tiles per chunk
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = S * (A_TILE + B_TILE);
-  static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 4 ? (200u * 1024u / STAGE_BYTES) : 4;
+  // ring depth: at least about 2500 clocks of MMA work in flight (six 32 KB
+  // stages of the two-plane form, four of the others)
+  static constexpr int MAX_STAGES = F16 ? 6 : 4;
+  static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < MAX_STAGES
+                                    ? (200u * 1024u / STAGE_BYTES) : MAX_STAGES;
   // two accumulator sets (the next chunk accumulates while the last one
   // drains) when both fit the 512 tensor-memory columns
   static constexpr int NBUF = 2 * NACC * BN <= 512 ? 2 : 1;
@@ -90,18 +107,21 @@ struct Cfg {
   static constexpr int EPI = BN >= 128 ? 16 : 8;
   static constexpr int THREADS = 64 + 32 * EPI;
   static constexpr int COLS = BN / (EPI / 4);  // columns drained by one warp
+  // chunk sums added as compensated pairs, except in 256-column tiles, whose
+  // 64 columns per warp leave room for plain FP32 sums only
+  static constexpr bool COMP = COLS <= 32;
   static_assert(ACC_COLS <= (int)TMEM_COLS, "diagonal accumulators exceed tensor memory");
   // exactness of the chunk sums: S pairs per diagonal (one pair for the
   // leading accumulator of the fused form), |d_s d_t| <= 2^14
-  static_assert((FUSED ? 1 : S) * CHUNK_KT * BK * 16384 < (1 << 24),
+  static_assert(F16 || (FUSED ? 1 : S) * CHUNK_KT * BK * 16384 < (1 << 24),
                 "chunk sums must stay exact in FP32");
   static_assert(STAGES >= 2, "at least two pipeline stages");
 };
 
-// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
-// K-major, N = bn, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+// Instruction descriptor of kind::f16: F32 accumulator, A and B both BF16
+// (or both FP16), both K-major, N = bn, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn, bool fp16 = false) {
+  return (1u << 4) | (fp16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(bn >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
 
@@ -271,6 +291,47 @@ __device__ __forceinline__ void digits_of(double x, int E, int (&d)[S]) {
   d[0] = (int)X;
 }
 
+// FP16 planes of x under the row scale 2^E (the split-FP16 form): y = x
+// 2^(15 - E) rounded to FP32 on the integer ALUs, hi = fp16(y), lo = fp16(y
+// - hi), all rounded to nearest; y - hi is exact in FP32 (Sterbenz), so hi +
+// lo carries y to about 1.5 * 2^-23 of |y| without an FP64 operation (the
+// FP64 pipe, about two operations per clock per SM, would bound the pack).
+// Zero and non-finite rows give zero planes (the epilogue reads a
+// non-finite row from its exponent).
+__device__ __forceinline__ void f16_split(double x, int E, uint32_t& hi, uint32_t& lo) {
+  hi = lo = 0u;
+  if (E == kZeroExp || E == kNanExp) return;
+  const float y = f64_to_f32(scale2(x, 15 - E));
+  const __half h = __float2half_rn(y);
+  hi = (uint32_t)__half_as_ushort(h);
+  lo = (uint32_t)__half_as_ushort(__float2half_rn(y - __half2float(h)));
+}
+
+// The 16-bit words of planes s of two consecutive elements x0, x1 (x0 in the
+// low half): FP16 hi/lo for S = 2, else BF16 digits (the fused three-plane
+// form stores plane s pre-scaled by 2^(-8 s)).
+template <int S>
+__device__ __forceinline__ void plane_words(double x0, double x1, int E, uint32_t (&w)[S]) {
+  if constexpr (S == 2) {
+    uint32_t h0, l0, h1, l1;
+    f16_split(x0, E, h0, l0);
+    f16_split(x1, E, h1, l1);
+    w[0] = h0 | (h1 << 16);
+    w[1] = l0 | (l1 << 16);
+  } else {
+    int d0[S], d1[S];
+    digits_of<S>(x0, E, d0);
+    digits_of<S>(x1, E, d1);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const float ws = S == 3 ? __int_as_float((127 - 8 * s) << 23) : 1.0f;
+      const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn((float)d0[s] * ws),
+                                                  __float2bfloat16_rn((float)d1[s] * ws));
+      w[s] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  }
+}
+
 template <int S>
 __global__ void oz_digits_kernel(PackArgs p, int batch) {
   const int KT = p.Kp / BK;
@@ -288,17 +349,11 @@ __global__ void oz_digits_kernel(PackArgs p, int batch) {
     uint32_t packed[S][4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-      int d0[S], d1[S];
-      digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
-      digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
+      uint32_t w[S];
+      plane_words<S>(embedded(p, b, rp, kt * BK + kg * 8 + j),
+                     embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, w);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        // the fused three-plane form stores plane s pre-scaled by 2^(-8 s)
-        const float ws = S == 3 ? __int_as_float((127 - 8 * s) << 23) : 1.0f;
-        const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn((float)d0[s] * ws),
-                                                    __float2bfloat16_rn((float)d1[s] * ws));
-        packed[s][j / 2] = *reinterpret_cast<const uint32_t*>(&h);
-      }
+      for (int s = 0; s < S; ++s) packed[s][j / 2] = w[s];
     }
     // core matrix (rg, kg) of the tile: 8 rows x 8 columns, row rr8 at 16 bytes
     const int rt = rp / p.rowtile, rr = rp % p.rowtile;
@@ -334,17 +389,11 @@ __global__ void oz_digits_rows_kernel(PackArgs p, int batch) {
       uint32_t packed[S][4];
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
-        int d0[S], d1[S];
-        digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j), E, d0);
-        digits_of<S>(embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, d1);
+        uint32_t w[S];
+        plane_words<S>(embedded(p, b, rp, kt * BK + kg * 8 + j),
+                       embedded(p, b, rp, kt * BK + kg * 8 + j + 1), E, w);
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          // the fused three-plane form stores plane s pre-scaled by 2^(-8 s)
-          const float ws = S == 3 ? __int_as_float((127 - 8 * s) << 23) : 1.0f;
-          const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn((float)d0[s] * ws),
-                                                      __float2bfloat16_rn((float)d1[s] * ws));
-          packed[s][j / 2] = *reinterpret_cast<const uint32_t*>(&h);
-        }
+        for (int s = 0; s < S; ++s) packed[s][j / 2] = w[s];
       }
       const int64_t off = (int64_t)b * p.s_out + ((int64_t)rt * KT + kt) * ((int64_t)p.rowtile * BK) +
                           ((rr / 8) * (BK / 8) + kg) * 64 + (rr % 8) * 8;
@@ -474,7 +523,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
     // diagonal d = s + t (planes s, t counted from 0) accumulates in columns
     // [d*BN, (d+1)*BN); a chunk's first MMA into d (s = 0) starts it afresh;
     // chunk jg (counted over all items) uses accumulator set jg % NBUF
-    const uint32_t idesc = idesc_bf16(BN);
+    const uint32_t idesc = idesc_bf16(BN, CF::F16);
     int kg = 0, jg = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < items && !stop; w += gridDim.x) {
@@ -506,10 +555,11 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
         for (int sa = 0; sa < S; ++sa) {
 #pragma unroll
           for (int sb = 0; sb < S - sa; ++sb) {
-            // accumulator of the pair: its diagonal, or (fused) leading / rest;
-            // the first pair into an accumulator in a chunk starts it afresh
-            const int acc = CF::FUSED ? (sa + sb > 0 ? 1 : 0) : sa + sb;
-            const bool first_pair = sa == 0 && (!CF::FUSED || sb <= 1);
+            // accumulator of the pair: its diagonal, (fused) leading / rest, or
+            // (FP16 planes) the only one; the first pair into an accumulator in
+            // a chunk starts it afresh
+            const int acc = CF::F16 ? 0 : (CF::FUSED ? (sa + sb > 0 ? 1 : 0) : sa + sb);
+            const bool first_pair = sa == 0 && (CF::F16 ? sb == 0 : (!CF::FUSED || sb <= 1));
             const uint32_t dt = tmem + (uint32_t)(((j % NBUF) * CF::NACC + acc) * BN);
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
@@ -532,9 +582,18 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
     int jg = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x) {
       const Item it = item_of(w);
-      float sum[HALF], cmp[HALF];
+      // running chunk sums (and their compensations when CF::COMP)
+      float sum[HALF], cmp[CF::COMP ? HALF : 1];
 #pragma unroll
-      for (int v = 0; v < HALF; ++v) sum[v] = cmp[v] = 0.0f;
+      for (int v = 0; v < HALF; ++v) sum[v] = 0.0f;
+#pragma unroll
+      for (int v = 0; v < (CF::COMP ? HALF : 1); ++v) cmp[v] = 0.0f;
+      auto cmpv = [&](int v) -> float {
+        if constexpr (CF::COMP)
+          return cmp[v];
+        else
+          return 0.0f;
+      };
       bool ok = it.nk > 0 && !*(volatile int*)abort_flag;
 #pragma unroll 1
       for (int jl = 0; ok && jl < it.nchunks; ++jl) {
@@ -549,8 +608,10 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
 #pragma unroll 1
         for (int d = 0; d < CF::NACC; ++d) {
           // 2^(2 - 8 (d + 2)) for diagonal d; the fused accumulators both carry
-          // the weight of the leading diagonal (the rest is pre-scaled)
-          const float wd = __int_as_float((127 - 14 - 8 * (CF::FUSED ? 0 : d)) << 23);
+          // the weight of the leading diagonal (the rest is pre-scaled); FP16
+          // planes carry 2^-15 each
+          const float wd = CF::F16 ? __int_as_float((127 - 30) << 23)
+                                   : __int_as_float((127 - 14 - 8 * (CF::FUSED ? 0 : d)) << 23);
 #pragma unroll
           for (int c = 0; c < HALF; c += 16) {
             uint32_t r[16];
@@ -558,8 +619,12 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
                           (uint32_t)((set * CF::NACC + d) * BN + h * HALF + c),
                       r);
 #pragma unroll
-            for (int v = 0; v < 16; ++v)
-              two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * wd);
+            for (int v = 0; v < 16; ++v) {
+              if constexpr (CF::COMP)
+                two_sum_acc(sum[c + v], cmp[c + v], __uint_as_float(r[v]) * wd);
+              else
+                sum[c + v] += __uint_as_float(r[v]) * wd;
+            }
           }
         }
         tc_fence_before();
@@ -589,7 +654,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
             }
             if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
             const int ec = row_exp(g.eb[(int64_t)it.b * g.Np + nr]);
-            double val = scaled_value(sum[v], cmp[v], er, ec);
+            double val = scaled_value(sum[v], cmpv(v), er, ec);
             if (g.alpha == -1.0)
               val = neg_f64(val);
             else if (g.alpha != 1.0)
@@ -603,7 +668,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
                                                 (int64_t)it.n_tile * BN + h * HALF);
 #pragma unroll
         for (int v = 0; v < HALF / 2; ++v)
-          dst[v] = make_float4(sum[2 * v], cmp[2 * v], sum[2 * v + 1], cmp[2 * v + 1]);
+          dst[v] = make_float4(sum[2 * v], cmpv(2 * v), sum[2 * v + 1], cmpv(2 * v + 1));
       }
     }
   }
@@ -695,16 +760,29 @@ struct Plan {
   int64_t p_elems;           // float2 partials (0 with one range)
 };
 
+}  // namespace oz
+
+// Output-tile width (rows of B' per tile) of the digit-plane kernels.
+int oz_tile_n(int64_t rows_b, int S) {
+  if (rows_b <= 32) return 32;
+  if (S == 2 && rows_b > 128) return 256;
+  return S <= 3 ? 128 : 64;
+}
+
+namespace oz {
+
 Plan plan(const GemmDesc& d, int S) {
   Plan p;
   p.mode = (d.Acplx && d.part_a < 0 ? 1 : 0) + (d.Bcplx && d.part_b < 0 ? 2 : 0);
   const int Ar = p.mode == 1 ? 2 * d.M : d.M;
   const int Ak = p.mode == 3 ? 2 * d.K : d.K;
   const int Br = (p.mode & 2) ? 2 * d.N : d.N;
-  // 32 columns for a narrow B', else 64: with seven planes one accumulator
-  // set of 7 x 64 columns, with three planes two sets of 3 x 64 (the next
-  // chunk accumulates while the last drains)
-  p.bn = Br <= 32 ? 32 : (S == 3 ? 128 : 64);
+  // 32 columns for a narrow B', else 64 with seven planes (one accumulator
+  // set of 7 x 64 columns), 128 with three (two sets of two 128-column
+  // accumulators: the next chunk accumulates while the last drains) and 256
+  // with two (two sets of one): a 128 x 256 MMA reads a quarter fewer
+  // shared-memory bytes per product than two 128 x 128 ones
+  p.bn = oz_tile_n(Br, S);
   p.Mp = roundup(std::max(Ar, 1), BM);
   p.Np = roundup(std::max(Br, 1), p.bn);
   p.Kp = roundup(std::max(Ak, 1), BK);
@@ -785,10 +863,14 @@ void pack(PackArgs pa, int64_t elems, int batch, int S, cudaStream_t st) {
   const int64_t units = elems / (pa.rows_fast ? 1024 : 256);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units * 32 + 255) / 256, 148 * 16));
   if (pa.rows_fast) {
-    if (S == 3)
+    if (S == 2)
+      oz_digits_rows_kernel<2><<<grid, 256, 0, st>>>(pa, batch);
+    else if (S == 3)
       oz_digits_rows_kernel<3><<<grid, 256, 0, st>>>(pa, batch);
     else
       oz_digits_rows_kernel<7><<<grid, 256, 0, st>>>(pa, batch);
+  } else if (S == 2) {
+    oz_digits_kernel<2><<<grid, 256, 0, st>>>(pa, batch);
   } else if (S == 3) {
     oz_digits_kernel<3><<<grid, 256, 0, st>>>(pa, batch);
   } else {
@@ -821,6 +903,9 @@ void gemm_oz_init() {
   set(oz::oz_gemm_kernel<7, 32>, oz::Cfg<7, 32>::SMEM);
   set(oz::oz_gemm_kernel<3, 128>, oz::Cfg<3, 128>::SMEM);
   set(oz::oz_gemm_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
+  set(oz::oz_gemm_kernel<2, 256>, oz::Cfg<2, 256>::SMEM);
+  set(oz::oz_gemm_kernel<2, 128>, oz::Cfg<2, 128>::SMEM);
+  set(oz::oz_gemm_kernel<2, 32>, oz::Cfg<2, 32>::SMEM);
 }
 
 void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
@@ -918,7 +1003,13 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   if (items > 0x7fffffff) throw Error(-1, "gemm_oz: too many tiles");
   const int grid = (int)std::min<int64_t>(items, 148);
   using namespace oz;
-  if (S == 3 && p.bn == 128)
+  if (S == 2 && p.bn == 256)
+    oz_gemm_kernel<2, 256><<<grid, Cfg<2, 256>::THREADS, Cfg<2, 256>::SMEM, st>>>(g);
+  else if (S == 2 && p.bn == 128)
+    oz_gemm_kernel<2, 128><<<grid, Cfg<2, 128>::THREADS, Cfg<2, 128>::SMEM, st>>>(g);
+  else if (S == 2)
+    oz_gemm_kernel<2, 32><<<grid, Cfg<2, 32>::THREADS, Cfg<2, 32>::SMEM, st>>>(g);
+  else if (S == 3 && p.bn == 128)
     oz_gemm_kernel<3, 128><<<grid, Cfg<3, 128>::THREADS, Cfg<3, 128>::SMEM, st>>>(g);
   else if (S == 3)
     oz_gemm_kernel<3, 32><<<grid, Cfg<3, 32>::THREADS, Cfg<3, 32>::SMEM, st>>>(g);

@@ -150,9 +150,11 @@ struct OzLayout {
   int ranges;
   double padded_flops;       // executed tensor-core FLOPs (28 digit-pair products)
 };
-// S = 7 digit planes (FP64-accurate) or 3 (the split-BF16 form, about 2^-24
-// of the row scales).
+// S = 7 digit planes (FP64-accurate), 3 (the split-BF16 form, about 2^-24
+// of the row scales) or 2 (the split-FP16 form: FP16 hi/lo planes).
 OzLayout gemm_oz_layout(const GemmDesc& d, int S);
+// Output-tile width (rows of B' per tile) for a B' of rows_b rows.
+int oz_tile_n(int64_t rows_b, int S);
 void gemm_oz_init();
 // slot / nslots: pack into batch slot `slot` of a buffer laid out for
 // nslots batch entries of this (batch-1) operand (the 3M products).

@@ -424,11 +424,11 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   // by dry runs of the residual as it will run
   // forms with packed tensor-core operands (and a cache of the constant ones)
   const bool split = c->precision != RTEOM_FP64;
-  const bool sliced = c->precision == RTEOM_FP64_OZAKI || c->precision == RTEOM_SPLIT_BF16;
+  const bool sliced = sliced_form(c->precision);
   if (const char* v = std::getenv("RTEOM_AUTOTUNE")) E.autotune = std::atoi(v) != 0;
   E.tensor_cores = c->precision == RTEOM_SPLIT_TF32;
   E.fp64_emulation = sliced;
-  E.oz_planes = c->precision == RTEOM_SPLIT_BF16 ? 3 : 7;
+  E.oz_planes = planes_of(c->precision);
   if (const char* v = std::getenv("RTEOM_TC_MIN_FLOPS")) E.tc_min_flops = std::atof(v);
   if (const char* v = std::getenv("RTEOM_NO_3M")) E.allow_3m = std::atoi(v) == 0;
   if (const char* v = std::getenv("RTEOM_TEST_CONSUMER_WAIT_CYCLES")) {
@@ -658,8 +658,8 @@ void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool 
   const AmpGeom g{O, nV, 0};
   Engine E;
   E.tensor_cores = precision == RTEOM_SPLIT_TF32;
-  E.fp64_emulation = precision == RTEOM_FP64_OZAKI || precision == RTEOM_SPLIT_BF16;
-  E.oz_planes = precision == RTEOM_SPLIT_BF16 ? 3 : 7;
+  E.fp64_emulation = sliced_form(precision);
+  E.oz_planes = planes_of(precision);
   ResidualOperands op;
   op.nO = O;
   op.nV = nV;
@@ -951,10 +951,9 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   if (nocc < 1 || nvir < 1 || nchol < 0) return bad(RTEOM_ERR_ARG, "need nocc >= 1, nvir >= 1, nchol >= 0");
   if (core_index < 0 || core_index >= nocc) return bad(RTEOM_ERR_ARG, "core_index outside the occupied orbitals");
   if (!eps || (nchol > 0 && !L)) return bad(RTEOM_ERR_ARG, "eps (and L when nchol > 0) must be given");
-  if (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 && precision != RTEOM_FP64_OZAKI &&
-      precision != RTEOM_SPLIT_BF16)
-    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32 "
-                              "or RTEOM_FP64_OZAKI");
+  if (!valid_precision(precision))
+    return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32, "
+                              "RTEOM_FP64_OZAKI or RTEOM_SPLIT_FP16");
   if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON))
     return bad(RTEOM_ERR_ARG, "unknown flag bits");
   const size_t nb = size_t(nocc) + nvir;
@@ -1153,9 +1152,7 @@ int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, do
   if (!bytes || nocc < 1 || nvir < 1 || nchol < 0 ||
       (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY |
                  RTEOM_FLAG_ANDERSON)) ||
-      (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
-       precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16) ||
-      (double)(nvir + 1) * (nvir + 1) > 2.0e9)
+      !valid_precision(precision) || (double)(nvir + 1) * (nvir + 1) > 2.0e9)
     return RTEOM_ERR_ARG;
   try {
     plan_context_bytes(nocc, nvir, nchol, precision,

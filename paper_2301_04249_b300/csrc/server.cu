@@ -296,8 +296,7 @@ int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_act
   if (!out) return RTEOM_ERR_ARG;
   *out = nullptr;
   if (max_active < 1 || mem_budget_bytes < 0 ||
-      (precision != RTEOM_FP64 && precision != RTEOM_SPLIT_TF32 &&
-       precision != RTEOM_FP64_OZAKI && precision != RTEOM_SPLIT_BF16))
+      !rteom::valid_precision(precision))
     return RTEOM_ERR_ARG;
   std::unique_ptr<rteom_server> s(new rteom_server());
   if (cudaGetDevice(&s->device) != cudaSuccess) return RTEOM_ERR_CUDA;

@@ -1,7 +1,7 @@
 """Evaluate CCSD residuals of a named workload eagerly, for profilers.
 
   python -m paper_2301_04249_b300.profile [--workload c2_formaldehyde | --shape O,V,N] [--residuals 2]
-         [--precision fp64|split_tf32|split_bf16|fp64_ozaki] [--cholesky] [--steps N]
+         [--precision fp64|split_tf32|split_bf16|split_fp16|fp64_ozaki] [--cholesky] [--steps N]
          [--tol TOL] [--anderson]
 
 Each evaluation launches every kernel of one residual on the library's
@@ -37,7 +37,8 @@ def main():
     ap.add_argument("--shape", default=None,
                     help="O,V,Nchol: a synthetic problem of this shape (seed 9) instead")
     ap.add_argument("--residuals", type=int, default=2)
-    ap.add_argument("--precision", choices=["fp64", "split_tf32", "split_bf16", "fp64_ozaki"],
+    ap.add_argument("--precision", choices=["fp64", "split_tf32", "split_bf16", "split_fp16",
+                                                     "fp64_ozaki"],
                     default="fp64")
     ap.add_argument("--cholesky", action="store_true")
     ap.add_argument("--steps", type=int, default=0)
@@ -54,7 +55,8 @@ def main():
         p, run = workload(a.workload)
     rng = np.random.default_rng(0)
     prec = {"fp64": P.RTEOM_FP64, "split_tf32": P.RTEOM_SPLIT_TF32,
-            "split_bf16": P.RTEOM_SPLIT_BF16, "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
+            "split_bf16": P.RTEOM_SPLIT_BF16, "split_fp16": P.RTEOM_SPLIT_FP16,
+            "fp64_ozaki": P.RTEOM_FP64_OZAKI}[a.precision]
     flags = (P.RTEOM_FLAG_LADDER_CHOLESKY if a.cholesky else 0) | \
         (P.RTEOM_FLAG_ANDERSON if a.anderson else 0)
     if a.steps > 0:

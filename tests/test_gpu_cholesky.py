@@ -31,12 +31,12 @@ def _small_chunks(monkeypatch):
 SHAPES = [(3, 5, 7, 1, 0), (5, 37, 23, 2, 0), (4, 9, 11, 3, 2), (1, 6, 5, 4, 0),
           (2, 1, 3, 5, 1), (6, 70, 40, 6, 0)]
 TOL = {P.RTEOM_FP64: 1e-12, P.RTEOM_FP64_OZAKI: 1e-12, P.RTEOM_SPLIT_TF32: 1e-5,
-       P.RTEOM_SPLIT_BF16: 1e-5}
+       P.RTEOM_SPLIT_BF16: 1e-5, P.RTEOM_SPLIT_FP16: 1e-5}
 
 
 @pytest.mark.parametrize("O,V,nchol,seed,core", SHAPES)
 @pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_TF32,
-                                       P.RTEOM_SPLIT_BF16])
+                                       P.RTEOM_SPLIT_BF16, P.RTEOM_SPLIT_FP16])
 def test_cholesky_residual_matches_oracle(O, V, nchol, seed, core, precision, rng):
     p = gen_problem(O, V, nchol, seed)
     sysb = CoreHoleCCSD.from_problem(p.eps, p.L, O, core)

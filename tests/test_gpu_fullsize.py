@@ -33,9 +33,9 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_residual_O12V160N640.txt")
 BOUND = {P.RTEOM_FP64: 1e-12, P.RTEOM_FP64_OZAKI: 1e-12, P.RTEOM_SPLIT_TF32: 1e-5,
-         P.RTEOM_SPLIT_BF16: 1e-5}
+         P.RTEOM_SPLIT_BF16: 1e-5, P.RTEOM_SPLIT_FP16: 1e-5}
 NAMES = {P.RTEOM_FP64: "fp64", P.RTEOM_FP64_OZAKI: "emulated", P.RTEOM_SPLIT_TF32: "tf32",
-         P.RTEOM_SPLIT_BF16: "bf16"}
+         P.RTEOM_SPLIT_BF16: "bf16", P.RTEOM_SPLIT_FP16: "fp16"}
 
 
 def test_sparse_residual_equals_dense_residual(rng):
@@ -111,8 +111,8 @@ def test_c3_sparse_residual_matches_oracle(c3_problem, precision):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", [P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16],
-                         ids=lambda x: NAMES[x])
+@pytest.mark.parametrize("precision", [P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16,
+                                       P.RTEOM_SPLIT_FP16], ids=lambda x: NAMES[x])
 def test_c5_sparse_residual_matches_oracle(c5_problem, precision):
     """O=50, V=450, Nchol=1800 in the Cholesky mode with its default chunks.
     One FP64 DFMA residual takes about 37 minutes here, so the FP64-accurate

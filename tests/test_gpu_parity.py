@@ -259,7 +259,7 @@ def test_autotuned_and_heuristic_launches_agree(monkeypatch):
 
 
 @pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16,
-                                       P.RTEOM_FP64_OZAKI])
+                                       P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_FP16])
 def test_overflowing_amplitude_reaches_the_residual(precision, rng, monkeypatch):
     """An overflow inside the residual (a 1e200 singles amplitude squares to
     infinity in tau = t2 + t1 t1) must not be absorbed by any contraction path

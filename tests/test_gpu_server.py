@@ -22,14 +22,15 @@ def _mix():
 
 
 @pytest.mark.parametrize("precision", [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16,
-                                       P.RTEOM_FP64_OZAKI])
+                                       P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_FP16])
 def test_result_identical_alone_and_in_the_mix(precision, monkeypatch):
     if precision == P.RTEOM_SPLIT_TF32:
         monkeypatch.setenv("RTEOM_TC_MIN_FLOPS", "0")   # small shapes on the tensor cores too
-    if precision in (P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_BF16):
+    if precision in (P.RTEOM_FP64_OZAKI, P.RTEOM_SPLIT_BF16, P.RTEOM_SPLIT_FP16):
         monkeypatch.setenv("RTEOM_OZ_MIN_FLOPS", "0")
     # split forms: ~1e-9 fixed-point floor of the packed amplitudes
-    tol = 1e-8 if precision in (P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16) else 1e-10
+    split = (P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16, P.RTEOM_SPLIT_FP16)
+    tol = 1e-8 if precision in split else 1e-10
     jobs = _mix()
     alone = []
     for p, n in jobs:

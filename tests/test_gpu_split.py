@@ -1,9 +1,11 @@
 """Split-precision forms against the FP64 oracle and FP64 path: split-TF32
 (RTEOM_SPLIT_TF32: hi*hi + hi*lo + lo*hi TF32 products, FP32 accumulation
-over slices of at most 512 of K) and split-BF16 (RTEOM_SPLIT_BF16: three
+over slices of at most 512 of K), split-BF16 (RTEOM_SPLIT_BF16: three
 8-bit BF16 digit planes per operand with per-row scales, the 6 leading digit
-pairs summed exactly in FP32).  Contractions of at least 5e7 FLOP run on the
-tensor cores; everything else stays FP64.  Targets: the cumulant within 1e-6
+pairs summed in FP32) and split-FP16 (RTEOM_SPLIT_FP16: rows scaled into
+FP16's range, hi/lo FP16 planes, hi*hi + hi*lo + lo*hi in FP32).
+Contractions of at least 5e7 FLOP run on the tensor cores; everything else
+stays FP64.  Targets: the cumulant within 1e-6
 absolute of the FP64 oracle and the quasiparticle peak within 0.005 eV
 (1.84e-4 Ha).  The packed operands carry about 22-24 bits, which puts a
 floor near 1e-9 under the micro-iteration change, so these runs use tol 1e-8
@@ -35,7 +37,8 @@ def _golden(name):
 
 
 FORMS = {"tf32": (P.RTEOM_SPLIT_TF32, "RTEOM_TC_MIN_FLOPS"),
-         "bf16": (P.RTEOM_SPLIT_BF16, "RTEOM_OZ_MIN_FLOPS")}
+         "bf16": (P.RTEOM_SPLIT_BF16, "RTEOM_OZ_MIN_FLOPS"),
+         "fp16": (P.RTEOM_SPLIT_FP16, "RTEOM_OZ_MIN_FLOPS")}
 
 
 @pytest.fixture(params=sorted(FORMS))
@@ -130,7 +133,7 @@ def test_split_tracks_fp64_path_over_40_steps(form):
 # as the four-product embedding (the three-product form starts at 2048 of
 # K); with three products the fixed-point floor of the stress case rose to
 # about 1e-8.
-STRESS_HORIZON = {P.RTEOM_SPLIT_TF32: 50, P.RTEOM_SPLIT_BF16: 200}
+STRESS_HORIZON = {P.RTEOM_SPLIT_TF32: 50, P.RTEOM_SPLIT_BF16: 200, P.RTEOM_SPLIT_FP16: 50}
 STRESS_TOL = 1e-8
 
 

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 FORMS = {"tf32": (P.RTEOM_SPLIT_TF32, "RTEOM_TC_MIN_FLOPS"),
          "bf16": (P.RTEOM_SPLIT_BF16, "RTEOM_OZ_MIN_FLOPS"),
+         "fp16": (P.RTEOM_SPLIT_FP16, "RTEOM_OZ_MIN_FLOPS"),
          "emulated": (P.RTEOM_FP64_OZAKI, "RTEOM_OZ_MIN_FLOPS")}
 
 

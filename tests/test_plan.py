@@ -11,7 +11,8 @@ import pytest
 
 import paper_2301_04249_b300 as P
 
-FORMS = [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16, P.RTEOM_FP64_OZAKI]
+FORMS = [P.RTEOM_FP64, P.RTEOM_SPLIT_TF32, P.RTEOM_SPLIT_BF16, P.RTEOM_FP64_OZAKI,
+         P.RTEOM_SPLIT_FP16]
 
 
 def _floor_bytes(O, V):

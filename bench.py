@@ -7,10 +7,11 @@ cumulant integrand and C_{n+1} (Eqs. 5-6).  Metric: time steps/s, whole job
 (sum over ranks; ranks are independent replicas).
 
 Default workload: the ESCA-shaped propagation O=50, V=450, Nchol=1800,
-dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-TF32
-form (contractions as split-TF32 products on the tensor cores, FP64 update,
-cumulant and phases).  Beside it, on the same inputs: the split-BF16 form
-and the FP64-accurate emulated form (a few steps each), an estimate of the
+dt=0.025 au, the paper's micro-iteration cutoff 1e-4, in the split-FP16
+form (contractions as row-scaled FP16 hi/lo products on the 16-bit tensor
+cores, FP64 update, cumulant and phases).  Beside it, on the same inputs:
+the split-TF32 and split-BF16 forms and the FP64-accurate emulated form (a
+few steps each), an estimate of the
 plain FP64 (DFMA) form from its measured contraction rate, and the
 formaldehyde-shaped FP64 workload (O=8, V=100, Nchol=400) as a secondary
 line.  Every form reports time per step and per micro-iteration (the
@@ -66,7 +67,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c5_esca_large")
-    ap.add_argument("--form", choices=FORMS, default="split_tf32",
+    ap.add_argument("--form", choices=FORMS, default="split_fp16",
                     help="precision form of the headline line")
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-micro", type=int, default=50)
@@ -79,9 +80,10 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--serving-mix", choices=["scaled", "c4"], default="c4",
-                    help="scaled: small shapes, all three forms; c4: the production request "
-                         "shapes (O~U{4..24}, V~U{40..240}) with steps cut to U{4..16}, tensor-core "
-                         "forms only, autotuner off (serial and served runs on equal terms)")
+                    help="scaled: small shapes, FP64, split-TF32 and split-BF16; c4: the "
+                         "production request shapes (O~U{4..24}, V~U{40..240}) with steps cut to "
+                         "U{4..16}, split-FP16 and split-BF16, autotuner off (serial and served "
+                         "runs on equal terms)")
     return ap.parse_args()
 
 
@@ -521,7 +523,7 @@ def serving_block(P, args):
                                 "V~U{40..240}, Nchol=4V, steps~U{4..16} (production: "
                                 "U{500..4000}), dt=0.025, Poisson arrivals at 2x the mean "
                                 "service rate, 8 slots, admission by device memory, autotuner off",
-                    "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests,
+                    "split_fp16": run_serving(P, P.RTEOM_SPLIT_FP16, args.serving_requests,
                                               args.tol, "c4"),
                     "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
                                               args.tol, "c4")}

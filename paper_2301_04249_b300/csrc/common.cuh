@@ -86,6 +86,71 @@ __device__ __forceinline__ double neg_f64(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
 }
 
+#endif
+
+// Output update c = alpha v + beta c of the GEMM epilogues, finalize and
+// combine kernels, with alpha and beta classified once on the host: a
+// compare of doubles runs on the FP64 pipe (about two operations per clock
+// per SM on this part), and a per-element beta test let the compiler read c
+// before knowing it was needed.  alpha = +-1 becomes a sign-bit mask.
+struct OutModes {
+  long long sign = 0;     // sign-bit mask applied when alpha = +-1
+  int general_alpha = 0;  // 1: multiply by alpha
+  int bmode = 0;          // 0: beta = 0, 1: beta = 1, 2: general
+  double alpha = 1.0, beta = 0.0;
+};
+
+inline OutModes out_modes(double alpha, double beta) {
+  OutModes o;
+  o.alpha = alpha;
+  o.beta = beta;
+  o.general_alpha = !(alpha == 1.0 || alpha == -1.0);
+  o.sign = alpha == -1.0 ? (long long)0x8000000000000000ull : 0ll;
+  o.bmode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
+  return o;
+}
+
+#ifdef __CUDACC__
+template <int GA, int BMODE>
+__device__ __forceinline__ void out_update(double* c, double v, const OutModes& o) {
+  if constexpr (GA)
+    v *= o.alpha;
+  else
+    v = __longlong_as_double(__double_as_longlong(v) ^ o.sign);
+  if constexpr (BMODE == 0)
+    *c = v;
+  else if constexpr (BMODE == 1)
+    *c = *c + v;
+  else
+    *c = fma(o.beta, *c, v);
+}
+
+template <int V>
+struct OutMode {
+  static constexpr int value = V;
+};
+
+// Calls f(OutMode<GA>, OutMode<BMODE>) for the modes of o, so that the
+// caller's loop is compiled once per mode with no test inside.
+template <class F>
+__device__ __forceinline__ void with_out_modes(const OutModes& o, F&& f) {
+  if (o.general_alpha) {
+    if (o.bmode == 0)
+      f(OutMode<1>{}, OutMode<0>{});
+    else if (o.bmode == 1)
+      f(OutMode<1>{}, OutMode<1>{});
+    else
+      f(OutMode<1>{}, OutMode<2>{});
+  } else {
+    if (o.bmode == 0)
+      f(OutMode<0>{}, OutMode<0>{});
+    else if (o.bmode == 1)
+      f(OutMode<0>{}, OutMode<1>{});
+    else
+      f(OutMode<0>{}, OutMode<2>{});
+  }
+}
+
 // Compensated FP32 accumulation (Knuth's TwoSum): s + c carries the running
 // sum to about twice the FP32 precision.
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {

@@ -224,6 +224,14 @@ __device__ __forceinline__ double scaled_value(float su, float cm, int er, int e
   return scale2(f32_to_f64(su) + f32_to_f64(cm), er + ec);
 }
 
+// FP64 value of a plain FP32 sum under the row scales 2^(er + ec), on the
+// integer ALUs (no FP64 operation).
+__device__ __forceinline__ double scaled_value1(float su, int er, int ec) {
+  if (er == kNanExp || ec == kNanExp) return __longlong_as_double(0x7FF8000000000000ll);
+  if (er == kZeroExp || ec == kZeroExp) return 0.0;
+  return scale2(f32_to_f64(su), er + ec);
+}
+
 __global__ void oz_expo_rows_kernel(PackArgs p, int batch) {
   const int64_t rows = (int64_t)batch * p.Rp;
   const int64_t segs = (p.Kp + kExpoSeg - 1) / kExpoSeg;
@@ -422,7 +430,7 @@ struct KArgs {
   bool cplx;
   int M, N, mode;              // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
   int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
-  double alpha, beta;
+  OutModes out;          // C = alpha D + beta C
 };
 
 template <int S, int BN>
@@ -644,24 +652,24 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
         const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
         if (row_ok) {
           const int64_t rbase = (int64_t)it.b * g.sC + (int64_t)m * g.ldm;
+          with_out_modes(g.out, [&](auto ga, auto bm) {
+            constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
 #pragma unroll
-          for (int v = 0; v < HALF; ++v) {
-            const int nr = it.n_tile * BN + h * HALF + v;
-            int n = nr, pt = part;
-            if (g.mode == 2 && nr >= g.N) {
-              n = nr - g.N;
-              pt = 1;
+            for (int v = 0; v < HALF; ++v) {
+              const int nr = it.n_tile * BN + h * HALF + v;
+              int n = nr, pt = part;
+              if (g.mode == 2 && nr >= g.N) {
+                n = nr - g.N;
+                pt = 1;
+              }
+              if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
+              const int ec = row_exp(g.eb[(int64_t)it.b * g.Np + nr]);
+              const double val = CF::COMP ? scaled_value(sum[v], cmpv(v), er, ec)
+                                          : scaled_value1(sum[v], er, ec);
+              out_update<GA, BMODE>(g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt,
+                                    val, g.out);
             }
-            if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-            const int ec = row_exp(g.eb[(int64_t)it.b * g.Np + nr]);
-            double val = scaled_value(sum[v], cmpv(v), er, ec);
-            if (g.alpha == -1.0)
-              val = neg_f64(val);
-            else if (g.alpha != 1.0)
-              val *= g.alpha;
-            double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
-            *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
-          }
+          });
         }
       } else {
         float4* dst = reinterpret_cast<float4*>(g.P + ((int64_t)it.z * g.Mp + mr) * g.Np +
@@ -703,51 +711,49 @@ struct FinArgs {
   double* C;
   bool cplx;
   int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
-  double alpha, beta;
+  OutModes out;          // C = alpha D + beta C
 };
 
 __global__ void oz_finalize_kernel(FinArgs f, int batch) {
   const int64_t per = (int64_t)f.M * f.N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const int64_t q = e - (int64_t)b * per;
-    const int m = (int)(q / f.N), n = (int)(q % f.N);
-    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
-    const int parts = f.cplx ? 2 : 1;
-    for (int part = 0; part < parts; ++part) {
-      const int mr = f.mode == 1 ? m + part * f.M : m;
-      const int nr = f.mode == 2 ? n + part * f.N : n;
-      float su = 0.0f, cm = 0.0f;
-      // ranges in order, four loads in flight at a time
-      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + mr) * f.Np + nr;
-      const int64_t zs = (int64_t)f.Mp * f.Np;
-      int z = 0;
-      for (; z + 4 <= f.ranges; z += 4) {
-        float2 q[4];
+  with_out_modes(f.out, [&](auto ga, auto bm) {
+    constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int b = (int)(e / per);
+      const int64_t q = e - (int64_t)b * per;
+      const int m = (int)(q / f.N), n = (int)(q % f.N);
+      double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
+      const int parts = f.cplx ? 2 : 1;
+      for (int part = 0; part < parts; ++part) {
+        const int mr = f.mode == 1 ? m + part * f.M : m;
+        const int nr = f.mode == 2 ? n + part * f.N : n;
+        float su = 0.0f, cm = 0.0f;
+        // ranges in order, four loads in flight at a time
+        const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + mr) * f.Np + nr;
+        const int64_t zs = (int64_t)f.Mp * f.Np;
+        int z = 0;
+        for (; z + 4 <= f.ranges; z += 4) {
+          float2 q[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = pp[(z + u) * zs];
+          for (int u = 0; u < 4; ++u) q[u] = pp[(z + u) * zs];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          two_sum_acc(su, cm, q[u].x);
-          cm += q[u].y;
+          for (int u = 0; u < 4; ++u) {
+            two_sum_acc(su, cm, q[u].x);
+            cm += q[u].y;
+          }
         }
+        for (; z < f.ranges; ++z) {
+          const float2 pz = pp[z * zs];
+          two_sum_acc(su, cm, pz.x);
+          cm += pz.y;
+        }
+        const int er = row_exp(f.ea[(int64_t)b * f.Mp + mr]);
+        const int ec = row_exp(f.eb[(int64_t)b * f.Np + nr]);
+        out_update<GA, BMODE>(c + part, scaled_value(su, cm, er, ec), f.out);
       }
-      for (; z < f.ranges; ++z) {
-        const float2 pz = pp[z * zs];
-        two_sum_acc(su, cm, pz.x);
-        cm += pz.y;
-      }
-      const int er = row_exp(f.ea[(int64_t)b * f.Mp + mr]);
-      const int ec = row_exp(f.eb[(int64_t)b * f.Np + nr]);
-      double s = scaled_value(su, cm, er, ec);
-      if (f.alpha == -1.0)
-        s = neg_f64(s);
-      else if (f.alpha != 1.0)
-        s *= f.alpha;
-      c[part] = f.beta == 0.0 ? s : (f.beta == 1.0 ? c[part] + s : fma(f.beta, c[part], s));
     }
-  }
+  });
 }
 
 inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
@@ -820,29 +826,31 @@ __global__ void oz_combine_3m_kernel(FinArgs f) {
   // the partials and the output never overlap
   const float2* __restrict__ Pr = f.P;
   double* __restrict__ Cr = f.C;
+  with_out_modes(f.out, [&](auto ga, auto bm) {
+    constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
 #pragma unroll 2
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int m = (int)(e / f.N), n = (int)(e % f.N);
-    double v[3];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int m = (int)(e / f.N), n = (int)(e % f.N);
+      double v[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
-      float su = 0.0f, cm = 0.0f;
-      for (int z = 0; z < f.ranges; ++z) {
-        const float2 q = pp[z * zs];
-        two_sum_acc(su, cm, q.x);
-        cm += q.y;
+      for (int b = 0; b < 3; ++b) {
+        const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+        float su = 0.0f, cm = 0.0f;
+        for (int z = 0; z < f.ranges; ++z) {
+          const float2 q = pp[z * zs];
+          two_sum_acc(su, cm, q.x);
+          cm += q.y;
+        }
+        v[b] = scaled_value(su, cm, row_exp(f.ea[(int64_t)b * f.Mp + m]),
+                            row_exp(f.eb[(int64_t)b * f.Np + n]));
       }
-      v[b] = scaled_value(su, cm, row_exp(f.ea[(int64_t)b * f.Mp + m]),
-                          row_exp(f.eb[(int64_t)b * f.Np + n]));
+      const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
+      double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+      out_update<GA, BMODE>(c, re, f.out);
+      out_update<GA, BMODE>(c + 1, im, f.out);
     }
-    const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
-    double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
-    const double a = f.alpha;
-    c[0] = f.beta == 0.0 ? a * re : (f.beta == 1.0 ? c[0] + a * re : fma(f.beta, c[0], a * re));
-    c[1] = f.beta == 0.0 ? a * im : (f.beta == 1.0 ? c[1] + a * im : fma(f.beta, c[1], a * im));
-  }
+  });
 }
 
 int grid_of(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 148 * 16); }
@@ -995,8 +1003,7 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.ldm = d.transC ? 1 : d.ldc;
   g.ldn = d.transC ? d.ldc : 1;
   g.sC = d.strideC;
-  g.alpha = d.alpha;
-  g.beta = d.beta;
+  g.out = out_modes(d.alpha, d.beta);
   g.zs = d.batch * p.ranges;
   // persistent CTAs: one per SM (the kernel takes most of the shared memory)
   const int64_t items = (int64_t)(p.Np / p.bn) * (p.Mp / oz::BM) * g.zs;
@@ -1040,8 +1047,7 @@ void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, co
   fa.ldm = d.transC ? 1 : d.ldc;
   fa.ldn = d.transC ? d.ldc : 1;
   fa.sC = d.strideC;
-  fa.alpha = d.alpha;
-  fa.beta = d.beta;
+  fa.out = out_modes(d.alpha, d.beta);
   oz::oz_finalize_kernel<<<oz::grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
   RT_CHECK_LAUNCH();
 }
@@ -1063,8 +1069,7 @@ void gemm_oz_combine_3m(const GemmDesc& d, int S, const int* ea, const int* eb, 
   fa.cplx = true;
   fa.ldm = d.transC ? 1 : d.ldc;
   fa.ldn = d.transC ? d.ldc : 1;
-  fa.alpha = d.alpha;
-  fa.beta = d.beta;
+  fa.out = out_modes(d.alpha, d.beta);
   oz::oz_combine_3m_kernel<<<oz::grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
   RT_CHECK_LAUNCH();
 }

@@ -85,7 +85,7 @@ struct KArgs {
   bool cplx;
   int M, N, mode;    // logical output extents; mode 0 real, 1 stacked rows, 2 stacked cols
   int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
-  double alpha, beta;
+  OutModes out;  // C = alpha D + beta C
 };
 
 template <int BN, int STAGES>
@@ -273,24 +273,23 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(KArgs g) {
           part = 1;
         }
         const bool row_ok = g.mode == 1 ? mr < 2 * g.M : mr < g.M;
-        const bool unit = g.alpha == 1.0 || g.alpha == -1.0;
-        const float sgn = g.alpha == -1.0 ? -1.0f : 1.0f;
         if (row_ok) {
           const int64_t rbase = (int64_t)it.b * g.sC + (int64_t)m * g.ldm;
+          with_out_modes(g.out, [&](auto ga, auto bm) {
+            constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
 #pragma unroll
-          for (int v = 0; v < HALF; ++v) {
-            const int nr = it.n_tile * BN + h * HALF + v;
-            int n = nr, pt = part;
-            if (g.mode == 2 && nr >= g.N) {
-              n = nr - g.N;
-              pt = 1;
+            for (int v = 0; v < HALF; ++v) {
+              const int nr = it.n_tile * BN + h * HALF + v;
+              int n = nr, pt = part;
+              if (g.mode == 2 && nr >= g.N) {
+                n = nr - g.N;
+                pt = 1;
+              }
+              if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
+              out_update<GA, BMODE>(g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt,
+                                    f32_to_f64(sum[v] + cmp[v]), g.out);
             }
-            if (n >= g.N || (g.mode == 2 ? nr >= 2 * g.N : nr >= g.N)) continue;
-            double* cp = g.C + (g.cplx ? 2 : 1) * (rbase + (int64_t)n * g.ldn) + pt;
-            const float f = sum[v] + cmp[v];
-            const double val = unit ? f32_to_f64(sgn * f) : g.alpha * f32_to_f64(f);
-            *cp = g.beta == 0.0 ? val : (g.beta == 1.0 ? *cp + val : fma(g.beta, *cp, val));
-          }
+          });
         }
       } else {
         float4* dst = reinterpret_cast<float4*>(
@@ -465,49 +464,48 @@ struct FinArgs {
   double* C;
   bool cplx;
   int64_t ldm, ldn, sC;  // output strides of GEMM rows and columns, batch
-  double alpha, beta;
+  OutModes out;          // C = alpha D + beta C
 };
 
 __global__ void tc_finalize_kernel(FinArgs f, int batch) {
   const int64_t per = (int64_t)f.M * f.N;
-  const bool unit = f.alpha == 1.0 || f.alpha == -1.0;
-  const float sgn = f.alpha == -1.0 ? -1.0f : 1.0f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const int64_t q = e - (int64_t)b * per;
-    const int m = (int)(q / f.N), n = (int)(q % f.N);
-    double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
-    const int parts = f.cplx ? 2 : 1;
-    for (int part = 0; part < parts; ++part) {
-      int mr = m, nr = n;
-      if (f.mode == 1) mr = m + part * f.M;
-      if (f.mode == 2) nr = n + part * f.N;
-      float s = 0.0f, cm = 0.0f;
-      // ranges in order, four loads in flight at a time
-      const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + mr) * f.Np + nr;
-      const int64_t zs = (int64_t)f.Mp * f.Np;
-      int z = 0;
-      for (; z + 4 <= f.ranges; z += 4) {
-        float2 q[4];
+  with_out_modes(f.out, [&](auto ga, auto bm) {
+    constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int b = (int)(e / per);
+      const int64_t q = e - (int64_t)b * per;
+      const int m = (int)(q / f.N), n = (int)(q % f.N);
+      double* c = f.C + (f.cplx ? 2 : 1) * ((int64_t)b * f.sC + (int64_t)m * f.ldm + (int64_t)n * f.ldn);
+      const int parts = f.cplx ? 2 : 1;
+      for (int part = 0; part < parts; ++part) {
+        int mr = m, nr = n;
+        if (f.mode == 1) mr = m + part * f.M;
+        if (f.mode == 2) nr = n + part * f.N;
+        float s = 0.0f, cm = 0.0f;
+        // ranges in order, four loads in flight at a time
+        const float2* pp = f.P + ((int64_t)b * f.ranges * f.Mp + mr) * f.Np + nr;
+        const int64_t zs = (int64_t)f.Mp * f.Np;
+        int z = 0;
+        for (; z + 4 <= f.ranges; z += 4) {
+          float2 q[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = pp[(z + u) * zs];
+          for (int u = 0; u < 4; ++u) q[u] = pp[(z + u) * zs];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          two_sum_acc(s, cm, q[u].x);
-          cm += q[u].y;
+          for (int u = 0; u < 4; ++u) {
+            two_sum_acc(s, cm, q[u].x);
+            cm += q[u].y;
+          }
         }
+        for (; z < f.ranges; ++z) {
+          const float2 pz = pp[z * zs];
+          two_sum_acc(s, cm, pz.x);
+          cm += pz.y;
+        }
+        out_update<GA, BMODE>(c + part, f32_to_f64(s + cm), f.out);
       }
-      for (; z < f.ranges; ++z) {
-        const float2 pz = pp[z * zs];
-        two_sum_acc(s, cm, pz.x);
-        cm += pz.y;
-      }
-      const float sf = s + cm;
-      const double v = unit ? f32_to_f64(sgn * sf) : f.alpha * f32_to_f64(sf);
-      c[part] = f.beta == 0.0 ? v : (f.beta == 1.0 ? c[part] + v : fma(f.beta, c[part], v));
     }
-  }
+  });
 }
 
 constexpr int kBN = 128;
@@ -566,40 +564,39 @@ __global__ void tc_combine_3m_kernel(FinArgs f) {
   // the partials and the output never overlap
   const float2* __restrict__ Pr = f.P;
   double* __restrict__ Cr = f.C;
+  with_out_modes(f.out, [&](auto ga, auto bm) {
+    constexpr int GA = decltype(ga)::value, BMODE = decltype(bm)::value;
 #pragma unroll 2
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int m = (int)(e / f.N), n = (int)(e % f.N);
-    // products as compensated FP32 pairs (s, c); the differences are formed
-    // with TwoSum on the leading parts, so only the final value takes an
-    // FP64 add (the FP64 pipe is the scarce unit)
-    float s[3], cm[3];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int m = (int)(e / f.N), n = (int)(e % f.N);
+      // products as compensated FP32 pairs (s, c); the differences are formed
+      // with TwoSum on the leading parts, so only the final value takes an
+      // FP64 add (the FP64 pipe is the scarce unit)
+      float s[3], cm[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
-      s[b] = 0.0f;
-      cm[b] = 0.0f;
-      for (int z = 0; z < f.ranges; ++z) {
-        const float2 q = pp[z * zs];
-        two_sum_acc(s[b], cm[b], q.x);
-        cm[b] += q.y;
+      for (int b = 0; b < 3; ++b) {
+        const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
+        s[b] = 0.0f;
+        cm[b] = 0.0f;
+        for (int z = 0; z < f.ranges; ++z) {
+          const float2 q = pp[z * zs];
+          two_sum_acc(s[b], cm[b], q.x);
+          cm[b] += q.y;
+        }
       }
+      float re_h = s[0], re_l = cm[0] - cm[1];
+      two_sum_acc(re_h, re_l, -s[1]);                 // P1 - P2
+      float im_h = s[2], im_l = cm[2] - cm[0] - cm[1];
+      two_sum_acc(im_h, im_l, -s[0]);
+      two_sum_acc(im_h, im_l, -s[1]);                 // P3 - P1 - P2
+      const double re = f32_to_f64(re_h) + f32_to_f64(re_l);
+      const double im = f32_to_f64(im_h) + f32_to_f64(im_l);
+      double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
+      out_update<GA, BMODE>(c, re, f.out);
+      out_update<GA, BMODE>(c + 1, im, f.out);
     }
-    float re_h = s[0], re_l = cm[0] - cm[1];
-    two_sum_acc(re_h, re_l, -s[1]);                 // P1 - P2
-    float im_h = s[2], im_l = cm[2] - cm[0] - cm[1];
-    two_sum_acc(im_h, im_l, -s[0]);
-    two_sum_acc(im_h, im_l, -s[1]);                 // P3 - P1 - P2
-    const double re = f32_to_f64(re_h) + f32_to_f64(re_l);
-    const double im = f32_to_f64(im_h) + f32_to_f64(im_l);
-    double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
-    const double a = f.alpha;
-    const bool unit = a == 1.0 || a == -1.0;
-    const double vr = unit ? (a < 0 ? neg_f64(re) : re) : a * re;
-    const double vi = unit ? (a < 0 ? neg_f64(im) : im) : a * im;
-    c[0] = f.beta == 0.0 ? vr : (f.beta == 1.0 ? c[0] + vr : fma(f.beta, c[0], vr));
-    c[1] = f.beta == 0.0 ? vi : (f.beta == 1.0 ? c[1] + vi : fma(f.beta, c[1], vi));
-  }
+  });
 }
 
 }  // namespace tc
@@ -718,8 +715,7 @@ void gemm_tc_mma(const GemmDesc& d, const float* Ahi, const float* Alo, const fl
   g.ldm = d.transC ? 1 : d.ldc;
   g.ldn = d.transC ? d.ldc : 1;
   g.sC = d.strideC;
-  g.alpha = d.alpha;
-  g.beta = d.beta;
+  g.out = out_modes(d.alpha, d.beta);
   g.zs = d.batch * p.ranges;
   // persistent CTAs: one per SM (the kernel takes most of the shared memory)
   const int64_t items = (int64_t)(p.Np / kBN) * (p.Mp / BM) * g.zs;
@@ -747,8 +743,7 @@ void gemm_tc_finalize(const GemmDesc& d, const float2* P, cudaStream_t st) {
   fa.ldm = d.transC ? 1 : d.ldc;
   fa.ldn = d.transC ? d.ldc : 1;
   fa.sC = d.strideC;
-  fa.alpha = d.alpha;
-  fa.beta = d.beta;
+  fa.out = out_modes(d.alpha, d.beta);
   tc_finalize_kernel<<<grid_of((int64_t)d.M * d.N * d.batch), 256, 0, st>>>(fa, d.batch);
   RT_CHECK_LAUNCH();
 }
@@ -777,8 +772,7 @@ void gemm_tc_combine_3m(const GemmDesc& d, const float2* P, cudaStream_t st) {
   fa.cplx = true;
   fa.ldm = d.transC ? 1 : d.ldc;
   fa.ldn = d.transC ? d.ldc : 1;
-  fa.alpha = d.alpha;
-  fa.beta = d.beta;
+  fa.out = out_modes(d.alpha, d.beta);
   tc_combine_3m_kernel<<<grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
   RT_CHECK_LAUNCH();
 }

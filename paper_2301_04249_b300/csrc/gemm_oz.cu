@@ -714,6 +714,15 @@ struct FinArgs {
   OutModes out;          // C = alpha D + beta C
 };
 
+// Whether the MMA kernel of S planes and BN-column tiles writes compensated
+// partial pairs (else plain FP32 sums with zero compensations).
+inline bool oz_comp(int S, int bn) {
+  static_assert(Cfg<2, 32>::COMP && Cfg<2, 128>::COMP && Cfg<3, 32>::COMP &&
+                    Cfg<3, 128>::COMP && Cfg<7, 32>::COMP && Cfg<7, 64>::COMP,
+                "only the 256-column tiles drain plain sums");
+  return !(S == 2 && bn == 256) || Cfg<2, 256>::COMP;
+}
+
 __global__ void oz_finalize_kernel(FinArgs f, int batch) {
   const int64_t per = (int64_t)f.M * f.N;
   with_out_modes(f.out, [&](auto ga, auto bm) {
@@ -820,6 +829,9 @@ Plan plan(const GemmDesc& d, int S) {
 // 3M combine of the digit-plane products: P holds [3][ranges][Mp][Np]
 // unscaled pairs, product b scaled by the row exponents ea[b][m], eb[b][n]
 // of its packed operands; C = alpha (P1 - P2 + i (P3 - P1 - P2)) + beta C.
+// PLAIN: one range of plain FP32 sums (zero compensations), converted
+// without an FP64 add.
+template <bool PLAIN>
 __global__ void oz_combine_3m_kernel(FinArgs f) {
   const int64_t per = (int64_t)f.M * f.N;
   const int64_t zs = (int64_t)f.Mp * f.Np;
@@ -836,14 +848,19 @@ __global__ void oz_combine_3m_kernel(FinArgs f) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const float2* pp = Pr + ((int64_t)b * f.ranges * f.Mp + m) * f.Np + n;
-        float su = 0.0f, cm = 0.0f;
-        for (int z = 0; z < f.ranges; ++z) {
-          const float2 q = pp[z * zs];
-          two_sum_acc(su, cm, q.x);
-          cm += q.y;
+        const int er = row_exp(f.ea[(int64_t)b * f.Mp + m]);
+        const int ec = row_exp(f.eb[(int64_t)b * f.Np + n]);
+        if constexpr (PLAIN) {
+          v[b] = scaled_value1(pp[0].x, er, ec);
+        } else {
+          float su = 0.0f, cm = 0.0f;
+          for (int z = 0; z < f.ranges; ++z) {
+            const float2 q = pp[z * zs];
+            two_sum_acc(su, cm, q.x);
+            cm += q.y;
+          }
+          v[b] = scaled_value(su, cm, er, ec);
         }
-        v[b] = scaled_value(su, cm, row_exp(f.ea[(int64_t)b * f.Mp + m]),
-                            row_exp(f.eb[(int64_t)b * f.Np + n]));
       }
       const double re = v[0] - v[1], im = v[2] - v[0] - v[1];
       double* c = Cr + 2 * ((int64_t)m * f.ldm + (int64_t)n * f.ldn);
@@ -1070,7 +1087,10 @@ void gemm_oz_combine_3m(const GemmDesc& d, int S, const int* ea, const int* eb, 
   fa.ldm = d.transC ? 1 : d.ldc;
   fa.ldn = d.transC ? d.ldc : 1;
   fa.out = out_modes(d.alpha, d.beta);
-  oz::oz_combine_3m_kernel<<<oz::grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
+  if (p.ranges == 1 && !oz::oz_comp(S, p.bn))
+    oz::oz_combine_3m_kernel<true><<<oz::grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
+  else
+    oz::oz_combine_3m_kernel<false><<<oz::grid_of((int64_t)d.M * d.N), 256, 0, st>>>(fa);
   RT_CHECK_LAUNCH();
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 namespace rteom {
@@ -187,7 +188,8 @@ void permute_add(const double* in, double* out, const PermDesc& d, bool in_cplx,
 void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, const double* y,
                   double c2, double c3, int nO, int nV, cudaStream_t st);
 
-// R[i,j,a,b] += c0*X[i,j,a,b] + c1*X[j,i,a,b] + c2*X[i,j,b,a] + c3*X[j,i,b,a]
+// R[i,j,a,b] += c0*X[i,j,a,b] + c1*X[j,i,a,b] + c2*X[i,j,b,a] + c3*X[j,i,b,a],
+// every c in {-1, 0, +1} (anything else throws)
 // (complex [nO][nO][nV][nV]; the permutation operators P(ij), P(ab)).
 void antisym_add(double* R, const double* X, double c0, double c1, double c2, double c3, int nO,
                  int nV, cudaStream_t st);
@@ -207,6 +209,20 @@ void pack_ladder_antisym(const double* W, double* Wm, int nV, cudaStream_t st);
 // First pair index of row p among the pairs (p < q) of n items.
 __host__ __device__ inline int64_t pair_start(int n, int p) {
   return (int64_t)p * (2 * (int64_t)n - p - 1) / 2;
+}
+// Pair k (0 <= k < n(n-1)/2) of n items in the order (0,1),(0,2),...,
+// (0,n-1),(1,2),...: the row p with pair_start(p) <= k < pair_start(p+1)
+// is the root of a quadratic, estimated in FP32 and corrected by integer
+// steps (at most a few for n below 2^16).
+__host__ __device__ inline void pair_of(int64_t k, int n, int& p, int& q) {
+  const int64_t m = 2 * (int64_t)n - 1;
+  const int64_t disc = m * m - 8 * k;  // >= 1 for valid k
+  int r = (int)(((float)m - sqrtf((float)(disc > 0 ? disc : 0))) * 0.5f);
+  r = r < 0 ? 0 : (r > n - 2 ? n - 2 : r);
+  while (r > 0 && pair_start(n, r) > k) --r;
+  while (r < n - 2 && pair_start(n, r + 1) <= k) ++r;
+  p = r;
+  q = r + 1 + (int)(k - pair_start(n, r));
 }
 // Column chunk a in [a0, a0+n) of the same-spin pair ladder (the pair
 // columns (a<b) of those a, contiguous).  Wc: [e][f][n][b] = (ae|bf) for the

@@ -213,55 +213,74 @@ __global__ void t2_t1t1_kernel(double2* __restrict__ out, const double2* __restr
 }
 
 // ---------------------------------------------------------------- P(ij), P(ab)
+// R[i][j][a][b] += s0 X[i][j][a][b] + s1 X[j][i][a][b] + s2 X[i][j][b][a] +
+// s3 X[j][i][b][a] with every s in {-1, 0, +1}: the terms present are the
+// bits of NZ, the signs sign-bit masks, so no FP64 multiply or compare runs
+// per element (only the adds).  A block takes one 32 x 32 (a, b) tile of one
+// (i, j): the direct terms are read coalesced along b, the transposed ones
+// as the (b, a) tile, staged through shared memory.
+template <int NZ>
 __global__ void antisym_add_kernel(double2* __restrict__ R, const double2* __restrict__ X,
-                                   double c0, double c1, double c2, double c3, int nO, int nV) {
-  const int64_t n = (int64_t)nO * nO * nV * nV;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int b = e % nV;
-    const int a = (e / nV) % nV;
-    const int j = (e / ((int64_t)nV * nV)) % nO;
-    const int i = e / ((int64_t)nV * nV * nO);
-    auto at = [&](int p, int q, int r, int s) {
-      return X[(((int64_t)p * nO + q) * nV + r) * nV + s];
-    };
-    double2 acc = R[e];
-    if (c0 != 0.0) {
-      const double2 v = at(i, j, a, b);
-      acc.x = fma(c0, v.x, acc.x);
-      acc.y = fma(c0, v.y, acc.y);
+                                   long long m0, long long m1, long long m2, long long m3, int nO,
+                                   int nV) {
+  __shared__ double2 tt[2][32][33];
+  const int tv = (nV + 31) / 32;
+  const int64_t units = (int64_t)nO * nO * tv * tv;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int64_t vv = (int64_t)nV * nV;
+  auto sgn = [](double v, long long m) { return __longlong_as_double(__double_as_longlong(v) ^ m); };
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int tb = (int)(u % tv);
+    const int64_t r = u / tv;
+    const int ta = (int)(r % tv);
+    const int ij = (int)(r / tv);
+    const int i = ij / nO, j = ij - (ij / nO) * nO;
+    const double2* Xij = X + (int64_t)ij * vv;
+    const double2* Xji = X + ((int64_t)j * nO + i) * vv;
+    const int a0 = 32 * ta, b0 = 32 * tb;
+    if (NZ & 12) {
+      __syncthreads();  // the previous unit's reads of the tiles are done
+      // tt[0][bb][aa] = Xij[b0 + bb][a0 + aa], tt[1] likewise from Xji
+      for (int k = ty; k < 32; k += 8) {
+        const int b = b0 + k, a = a0 + tx;
+        if (b < nV && a < nV) {
+          if (NZ & 4) tt[0][k][tx] = Xij[(int64_t)b * nV + a];
+          if (NZ & 8) tt[1][k][tx] = Xji[(int64_t)b * nV + a];
+        }
+      }
+      __syncthreads();
     }
-    if (c1 != 0.0) {
-      const double2 v = at(j, i, a, b);
-      acc.x = fma(c1, v.x, acc.x);
-      acc.y = fma(c1, v.y, acc.y);
+    for (int k = ty; k < 32; k += 8) {
+      const int a = a0 + k, b = b0 + tx;
+      if (a >= nV || b >= nV) continue;
+      const int64_t o = (int64_t)a * nV + b;
+      double2 acc = R[(int64_t)ij * vv + o];
+      if (NZ & 1) {
+        const double2 v = Xij[o];
+        acc.x += sgn(v.x, m0);
+        acc.y += sgn(v.y, m0);
+      }
+      if (NZ & 2) {
+        const double2 v = Xji[o];
+        acc.x += sgn(v.x, m1);
+        acc.y += sgn(v.y, m1);
+      }
+      if (NZ & 4) {
+        const double2 v = tt[0][tx][k];
+        acc.x += sgn(v.x, m2);
+        acc.y += sgn(v.y, m2);
+      }
+      if (NZ & 8) {
+        const double2 v = tt[1][tx][k];
+        acc.x += sgn(v.x, m3);
+        acc.y += sgn(v.y, m3);
+      }
+      R[(int64_t)ij * vv + o] = acc;
     }
-    if (c2 != 0.0) {
-      const double2 v = at(i, j, b, a);
-      acc.x = fma(c2, v.x, acc.x);
-      acc.y = fma(c2, v.y, acc.y);
-    }
-    if (c3 != 0.0) {
-      const double2 v = at(j, i, b, a);
-      acc.x = fma(c3, v.x, acc.x);
-      acc.y = fma(c3, v.y, acc.y);
-    }
-    R[e] = acc;
   }
 }
 
 // ---------------------------------------------------------------- antisymmetric pairs
-// Pair k of n items in the order (0,1),(0,2),...,(0,n-1),(1,2),...: row p
-// starts at p*(2n-p-1)/2.  Decoded with a short scan (n is small).
-__device__ __forceinline__ void pair_of(int64_t k, int n, int& p, int& q) {
-  int64_t start = 0;
-  p = 0;
-  while (p < n - 1 && start + (n - 1 - p) <= k) {
-    start += n - 1 - p;
-    ++p;
-  }
-  q = p + 1 + (int)(k - start);
-}
 
 __global__ void pack_pairs_kernel(const double2* __restrict__ t2, double2* __restrict__ out,
                                   int nO, int nV) {
@@ -1094,11 +1113,33 @@ void t2_plus_t1t1(double* out, const double* t2, double c1, const double* x, con
 
 void antisym_add(double* R, const double* X, double c0, double c1, double c2, double c3, int nO,
                  int nV, cudaStream_t st) {
-  int64_t n = (int64_t)nO * nO * nV * nV;
-  if (n == 0) return;
-  antisym_add_kernel<<<grid_for(n, 16), kThreads, 0, st>>>(reinterpret_cast<double2*>(R),
-                                                            reinterpret_cast<const double2*>(X),
-                                                            c0, c1, c2, c3, nO, nV);
+  const int64_t tv = (nV + 31) / 32;
+  const int64_t units = (int64_t)nO * nO * tv * tv;
+  if (units == 0) return;
+  const double c[4] = {c0, c1, c2, c3};
+  int nz = 0;
+  long long m[4];
+  for (int k = 0; k < 4; ++k) {
+    if (c[k] != 0.0 && c[k] != 1.0 && c[k] != -1.0)
+      throw Error(-1, "antisym_add: coefficients must be 0 or +-1");
+    if (c[k] != 0.0) nz |= 1 << k;
+    m[k] = c[k] == -1.0 ? (long long)0x8000000000000000ull : 0ll;
+  }
+  const int grid = (int)std::min<int64_t>(units, 148 * 8);
+  auto R2 = reinterpret_cast<double2*>(R);
+  auto X2 = reinterpret_cast<const double2*>(X);
+#define RT_ANTISYM(NZ)                                                                         \
+  case NZ:                                                                                     \
+    antisym_add_kernel<NZ><<<grid, kThreads, 0, st>>>(R2, X2, m[0], m[1], m[2], m[3], nO, nV); \
+    break;
+  switch (nz) {
+    RT_ANTISYM(1) RT_ANTISYM(2) RT_ANTISYM(3) RT_ANTISYM(4) RT_ANTISYM(5) RT_ANTISYM(6)
+    RT_ANTISYM(7) RT_ANTISYM(8) RT_ANTISYM(9) RT_ANTISYM(10) RT_ANTISYM(11) RT_ANTISYM(12)
+    RT_ANTISYM(13) RT_ANTISYM(14) RT_ANTISYM(15)
+    default:
+      return;  // all coefficients zero
+  }
+#undef RT_ANTISYM
   RT_CHECK_LAUNCH();
 }
 

@@ -51,6 +51,7 @@ def main():
         from synth import gen_problem
         O, V, N = (int(x) for x in a.shape.split(","))
         p, run = gen_problem(O, V, N, 9), dict(dt=0.025)
+        a.workload = f"shape O={O} V={V} Nchol={N} seed=9"
     else:
         p, run = workload(a.workload)
     rng = np.random.default_rng(0)

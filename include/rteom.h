@@ -125,6 +125,28 @@ extern "C" {
                                          implicit solution in fewer residuals
                                          at tight tol; 9 extra amplitude-sized
                                          device vectors                       */
+#define RTEOM_FLAG_GROUPED         8  /* grouped ladder, for running many
+                                         propagations in lock step
+                                         (rteom_propagate_group): every
+                                         residual forms tau and packs the
+                                         operands of its three ladder GEMMs
+                                         (Section 3.1, sum_cd v_abcd tau_ij^cd)
+                                         first, the GEMMs run as one grouped
+                                         persistent launch (with those of the
+                                         other contexts of a group), then the
+                                         rest of the residual adds their
+                                         results.  Each ladder GEMM takes one K
+                                         range per output tile, so a context's
+                                         results are the same bits alone and in
+                                         any group.  Needs RTEOM_FP64_OZAKI,
+                                         RTEOM_SPLIT_BF16 or RTEOM_SPLIT_FP16
+                                         and the resident ladder blocks (not
+                                         with RTEOM_FLAG_LADDER_CHOLESKY or
+                                         RTEOM_FLAG_ANDERSON; RTEOM_ERR_OOM
+                                         when they do not fit); no timing
+                                         modes.  rteom_propagate and the
+                                         server run such a context as a group
+                                         of one                               */
 
 typedef struct rteom_ctx rteom_ctx;
 
@@ -186,6 +208,35 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol,
  */
 int rteom_propagate(rteom_ctx* ctx, int nsteps, double dt, double tol, int max_micro,
                     double* C_out);
+
+/*
+ * rteom_propagate_group -- rteom_propagate for n contexts at once, in lock
+ * step (no counterpart in the paper, whose core-hole propagations are
+ * independent and run side by side, Section 3).  In every round each member
+ * with steps left evaluates one residual (R(t_n) of its next step or
+ * R(t^(k)) of its next micro-iteration) and its Adams-Moulton update; the
+ * ladder GEMMs of all members of the round run as grouped persistent
+ * tensor-core launches (one per output-tile width, up to 16 GEMMs each) on
+ * the first member's stream, between the members' captured graphs of the
+ * residual's two parts on their own streams.  Members may differ in
+ * (O, V, Nchol); they advance by the same stopping rule as rteom_propagate,
+ * each with its own number of micro-iterations, and each result equals that
+ * of rteom_propagate on the member alone, bit for bit.
+ *
+ *  ctxs       n distinct contexts created with RTEOM_FLAG_GROUPED and one
+ *             precision form; 1 <= n <= 1024; their streams may differ
+ *  nsteps, dt, tol, max_micro   as for rteom_propagate, for every member
+ *  C_out      NULL, or n pointers (each NULL or host [nsteps+1] complex):
+ *             member i's C at the start of the call and after each step
+ *
+ * Errors: RTEOM_ERR_ARG (bad arguments, a member without the flag, mixed
+ * forms, a repeated member; reported on that member); the first member
+ * error of a round (RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_NONFINITE,
+ * RTEOM_ERR_CUDA) stops the call and is reported on that member; the other
+ * members keep their last completed step.
+ */
+int rteom_propagate_group(rteom_ctx* const* ctxs, int n, int nsteps, double dt, double tol,
+                          int max_micro, double* const* C_out);
 
 /*
  * rteom_spectrum -- core spectral function A(w) = -(1/pi) Im G^R(w)

@@ -13,12 +13,13 @@ import numpy as np
 from . import _lib
 from ._lib import (RTEOM_ERR_ARG, RTEOM_ERR_CUDA, RTEOM_ERR_NONFINITE,  # noqa: F401
                    RTEOM_ERR_NOT_CONVERGED, RTEOM_ERR_OOM, RTEOM_ERR_STATE, RTEOM_FLAG_CUMULANT_NO_FOV,
-                   RTEOM_FLAG_LADDER_CHOLESKY, RTEOM_FLAG_ANDERSON,
+                   RTEOM_FLAG_LADDER_CHOLESKY, RTEOM_FLAG_ANDERSON, RTEOM_FLAG_GROUPED,
                    RTEOM_FP64, RTEOM_OK, RTEOM_REQ_CANCELLED, RTEOM_REQ_DONE, RTEOM_REQ_FAILED,
                    RTEOM_REQ_QUEUED, RTEOM_REQ_RUNNING, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32,
                    RTEOM_FP64_OZAKI, RTEOM_SPLIT_FP16)
 
-__all__ = ["Propagator", "Server", "RteomError", "block_shapes", "split_blocks", "join_blocks"]
+__all__ = ["Propagator", "Server", "RteomError", "block_shapes", "split_blocks", "join_blocks",
+           "propagate_group"]
 
 
 class RteomError(RuntimeError):
@@ -70,6 +71,24 @@ def join_blocks(blocks) -> np.ndarray:
     """List of complex block arrays -> interleaved complex amplitude vector."""
     z = np.concatenate([np.ascontiguousarray(b, dtype=np.complex128).ravel() for b in blocks])
     return z.view(np.float64).copy()
+
+
+def propagate_group(props, nsteps: int, dt: float, tol: float = 1e-4, max_micro: int = 50):
+    """rteom_propagate_group: advance every Propagator of ``props`` (created
+    with RTEOM_FLAG_GROUPED, one precision form) nsteps steps in lock step,
+    the ladder GEMMs of each round in grouped launches.  Returns each
+    member's C at the start and after each step (complex [nsteps+1])."""
+    lib = _lib.load()
+    n = len(props)
+    ctxs = (ctypes.c_void_p * n)(*[p._ctx.value for p in props])
+    outs = [np.zeros(2 * (int(nsteps) + 1)) for _ in props]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[_ptr(o) for o in outs])
+    rc = lib.rteom_propagate_group(ctxs, n, int(nsteps), float(dt), float(tol), int(max_micro),
+                                   ptrs)
+    if rc != 0:
+        msg = "; ".join(m for m in (lib.rteom_last_error(p._ctx).decode() for p in props) if m)
+        raise RteomError(rc, msg)
+    return [o.view(np.complex128) for o in outs]
 
 
 class Propagator:

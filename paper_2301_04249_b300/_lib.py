@@ -22,6 +22,7 @@ RTEOM_SPLIT_FP16 = 4
 RTEOM_FLAG_CUMULANT_NO_FOV = 1
 RTEOM_FLAG_LADDER_CHOLESKY = 2
 RTEOM_FLAG_ANDERSON = 4
+RTEOM_FLAG_GROUPED = 8
 RTEOM_REQ_QUEUED = 0
 RTEOM_REQ_RUNNING = 1
 RTEOM_REQ_DONE = 2
@@ -38,6 +39,9 @@ SIGNATURES = {
                                     _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "rteom_propagate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, _dp]),
+    "rteom_propagate_group": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             ctypes.POINTER(_dp)]),
     "rteom_spectrum": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, _dp]),
     "rteom_get_info": (ctypes.c_int, [_vp, _dp, _dp, _llp, _llp]),
     "rteom_state_size": (ctypes.c_longlong, [_vp]),

@@ -26,6 +26,13 @@ inline bool sliced_form(int p) {
 inline int planes_of(int p) {
   return p == RTEOM_SPLIT_BF16 ? 3 : (p == RTEOM_SPLIT_FP16 ? 2 : 7);
 }
+// The grouped ladder (RTEOM_FLAG_GROUPED) runs on the digit-plane forms with
+// the resident ladder blocks and the plain micro-iteration.
+inline bool grouped_flags_ok(int precision, int flags) {
+  return !(flags & RTEOM_FLAG_GROUPED) ||
+         (sliced_form(precision) &&
+          !(flags & (RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON)));
+}
 
 // Error carried from deep inside the library to the C ABI boundary.
 struct Error : std::runtime_error {

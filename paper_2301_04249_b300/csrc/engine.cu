@@ -514,6 +514,13 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   const double flops0 = mult0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt;
   bool use_tc = tensor_cores && flops0 >= tc_min_flops;
   bool use_oz = fp64_emulation && flops0 >= oz_min_flops;
+  const bool grouped = defer_ladder && cls == kLadder;
+  if (grouped) {
+    if (!fp64_emulation)
+      throw Error(-1, std::string("contract: the grouped ladder needs a digit-plane form: ") + spec);
+    use_tc = false;
+    use_oz = true;
+  }
 
   GemmDesc g;
   g.M = (int)Mt;
@@ -533,6 +540,7 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
   g.alpha = alpha;
   g.beta = bPC ? 0.0 : beta;
   g.wait_cycles = tc_wait_cycles;
+  g.one_range = grouped;
 
   // launch configuration from the autotuner, when it has one for this shape
   const bool tunable =
@@ -886,6 +894,24 @@ void Engine::contract(const char* spec, double alpha, const Tensor& A, const Ten
                            : operand(roleA, A, cA, 2 * L.planes * L.a_elems, 4 * L.a_rows, true, go);
     const Packed pb = swap ? operand(roleA, A, cA, 2 * L.planes * L.b_elems, 4 * L.b_rows, false, go)
                            : operand(roleB, B, cB, 2 * L.planes * L.b_elems, 4 * L.b_rows, false, go);
+    if (grouped) {  // recorded for the caller's grouped launch; the packs stay
+      if (L.p_elems || outcopy)
+        throw Error(-1, std::string("contract: a grouped ladder needs one K range and its "
+                                    "output in GEMM layout: ") + spec);
+      if (!dry) {
+        OzGroupGemm gg;
+        gg.d = go;
+        gg.A = static_cast<const uint16_t*>(pa.p0);
+        gg.ea = static_cast<const int*>(pa.p1);
+        gg.B = static_cast<const uint16_t*>(pb.p0);
+        gg.eb = static_cast<const int*>(pb.p1);
+        gg.err = tc_err;
+        deferred.push_back({gg, flops});
+      }
+      if (nvtx_here) nvtxRangePop();
+      if (!dry) nvtxRangePop();  // rteom_ladder
+      return;
+    }
     float2* P = L.p_elems ? reinterpret_cast<float2*>(arena.alloc(L.p_elems)) : nullptr;
     // digit planes read once; partial pairs written or the output written
     const double bytes = 2.0 * L.planes * (double)(L.a_elems + L.b_elems) +

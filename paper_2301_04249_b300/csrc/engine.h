@@ -70,6 +70,19 @@ class Engine {
   // (into the cache) and its held operands (see hold()) and launches
   // nothing else
   bool pack_only = false;
+  // Grouped ladder.  With defer_ladder set, every ladder contraction (class
+  // kLadder) takes the digit-plane tensor-core path with one K range per
+  // output tile (GemmDesc::one_range), and outside pack_only it packs its
+  // operands and records its GEMM in `deferred` instead of launching it.  Its
+  // packs stay allocated in the arena: the caller launches the recorded GEMMs
+  // (possibly with other engines' ones, gemm_oz_mma_group) and releases the
+  // arena below them afterwards.
+  bool defer_ladder = false;
+  struct Deferred {
+    OzGroupGemm gemm;
+    double flops;
+  };
+  std::vector<Deferred> deferred;
 
   // Autotuner.  A GEMM of at most tune_max_flops that is not a matrix-vector
   // product takes its launch configuration (FP64 tile shape and K slices, or

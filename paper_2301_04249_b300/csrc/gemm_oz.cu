@@ -50,6 +50,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -433,8 +434,48 @@ struct KArgs {
   OutModes out;          // C = alpha D + beta C
 };
 
-template <int S, int BN>
-__global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g) {
+// Work list of one persistent launch.  OneGemm: the items of one GEMM (its
+// output tiles times its K ranges).  GemmGroup: several GEMMs of one tile
+// configuration in one launch (the grouped ladder of several propagations):
+// GEMM p owns the items [first[p], first[p+1]) and reads and writes only its
+// own operands, so each tile is computed exactly as in a launch of its GEMM
+// alone.  A pipeline timeout marks every GEMM of the launch failed, since the
+// CTA that gave up leaves the rest of its items undone.
+constexpr int kMaxGroup = 16;
+struct KGroup {
+  int n = 0;
+  int first[kMaxGroup + 1] = {};
+  KArgs g[kMaxGroup];
+};
+static_assert(sizeof(KGroup) <= 4096, "the grouped kernel's table must fit 4 KB of parameters");
+
+template <int BN>
+struct OneGemm {
+  const KArgs& g;
+  __device__ int items() const { return (g.Mp / BM) * (g.Np / BN) * g.zs; }
+  __device__ const KArgs& at(int w, int& local) const {
+    local = w;
+    return g;
+  }
+  __device__ void fail(int code) const { atomicExch(g.err, code); }
+};
+
+struct GemmGroup {
+  const KGroup& G;
+  __device__ int items() const { return G.first[G.n]; }
+  __device__ const KArgs& at(int w, int& local) const {
+    int p = 0;
+    while (p + 1 < G.n && w >= G.first[p + 1]) ++p;
+    local = w - G.first[p];
+    return G.g[p];
+  }
+  __device__ void fail(int code) const {
+    for (int p = 0; p < G.n; ++p) atomicExch(G.g[p].err, code);
+  }
+};
+
+template <int S, int BN, class Work>
+__device__ __forceinline__ void oz_gemm_body(const Work& work) {
   using CF = Cfg<S, BN>;
   constexpr int CHUNK_KT = CF::CHUNK_KT;
   constexpr int STAGES = CF::STAGES;
@@ -461,16 +502,17 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
   // carries twice the bytes of a 64-row B' tile, else 12), CTA c takes items
   // c, c + gridDim.x, ...; the stage and chunk counters run on across items,
   // so a tile's drain overlaps the next tile's MMAs.
-  const int m_tiles = g.Mp / BM, n_tiles = g.Np / BN;
-  const int tiles = m_tiles * n_tiles;
-  const int items = tiles * g.zs;
+  // Item w of the work list belongs to GEMM g (work.at) as its local item lw.
+  const int items = work.items();
   struct Item {
     int m_tile, n_tile, z, b, kt0, nk, nchunks;
   };
-  auto item_of = [&](int w) {
+  auto item_of = [&](const KArgs& g, int lw) {
     Item it;
-    it.z = w / tiles;
-    grouped_tile(w - it.z * tiles, m_tiles, n_tiles, BN == 64 ? 8 : 12, &it.m_tile, &it.n_tile);
+    const int m_tiles = g.Mp / BM, n_tiles = g.Np / BN;
+    const int tiles = m_tiles * n_tiles;
+    it.z = lw / tiles;
+    grouped_tile(lw - it.z * tiles, m_tiles, n_tiles, BN == 64 ? 8 : 12, &it.m_tile, &it.n_tile);
     it.b = it.z / g.ranges;
     const int rg = it.z % g.ranges;
     it.kt0 = rg * g.kpr;
@@ -503,14 +545,16 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
   if (warp == 0 && lane == 0) {
     int kg = 0;  // k tiles issued so far (all items)
     for (int w = blockIdx.x; w < items && !*(volatile int*)abort_flag; w += gridDim.x) {
-      const Item it = item_of(w);
+      int lw;
+      const KArgs& g = work.at(w, lw);
+      const Item it = item_of(g, lw);
       const __nv_bfloat16* A = g.A + it.b * g.sA + (int64_t)it.m_tile * g.KT * (BM * BK);
       const __nv_bfloat16* B = g.B + it.b * g.sB + (int64_t)it.n_tile * g.KT * (BN * BK);
       for (int k = 0; k < it.nk; ++k, ++kg) {
         const int s = kg % STAGES;
         if (kg >= STAGES &&
             !mbar_wait_or_abort(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag)) {
-          if (!*(volatile int*)abort_flag) atomicExch(g.err, 11);
+          if (!*(volatile int*)abort_flag) work.fail(11);
           *abort_flag = 1;
           break;
         }
@@ -535,7 +579,9 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
     int kg = 0, jg = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < items && !stop; w += gridDim.x) {
-      const Item it = item_of(w);
+      int lw;
+      const KArgs& g = work.at(w, lw);
+      const Item it = item_of(g, lw);
       for (int k = 0; k < it.nk; ++k, ++kg) {
         const int kin = k % CHUNK_KT;
         const int j = jg + k / CHUNK_KT;
@@ -544,7 +590,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
           const int jj = j - NBUF;
           if (jj >= 0 && !mbar_wait(&acc_empty[jj % NBUF], (jj / NBUF) & 1, g.wait)) {
             *abort_flag = 1;
-            atomicExch(g.err, 14);
+            work.fail(14);
             stop = true;
             break;
           }
@@ -552,7 +598,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
         const int s = kg % STAGES;
         if (!mbar_wait(&full[s], (kg / STAGES) & 1, g.wait)) {
           *abort_flag = 1;
-          atomicExch(g.err, 12);
+          work.fail(12);
           stop = true;
           break;
         }
@@ -589,7 +635,9 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
     const int row = 32 * q + lane;
     int jg = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x) {
-      const Item it = item_of(w);
+      int lw;
+      const KArgs& g = work.at(w, lw);
+      const Item it = item_of(g, lw);
       // running chunk sums (and their compensations when CF::COMP)
       float sum[HALF], cmp[CF::COMP ? HALF : 1];
 #pragma unroll
@@ -609,7 +657,7 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
         if (!mbar_wait(&acc_full[set], (j / NBUF) & 1, g.wait)) {
           ok = false;
           *abort_flag = 1;
-          atomicExch(g.err, 13);
+          work.fail(13);
           break;
         }
         tc_fence_after();
@@ -700,6 +748,17 @@ __global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
+}
+
+template <int S, int BN>
+__global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1) oz_gemm_kernel(KArgs g) {
+  oz_gemm_body<S, BN>(OneGemm<BN>{g});
+}
+
+template <int S, int BN>
+__global__ void __launch_bounds__(Cfg<S, BN>::THREADS, 1)
+    oz_gemm_group_kernel(const __grid_constant__ KGroup G) {
+  oz_gemm_body<S, BN>(GemmGroup{G});
 }
 
 // ---------------------------------------------------------------- finalize
@@ -820,6 +879,10 @@ Plan plan(const GemmDesc& d, int S) {
       p.kpr = kpr;
     }
   }
+  if (d.one_range) {  // tiles independent of the rest of the launch
+    p.ranges = 1;
+    p.kpr = p.KT;
+  }
   p.a_elems = (int64_t)p.Mp * p.Kp * d.batch;
   p.b_elems = (int64_t)p.Np * p.Kp * d.batch;
   p.p_elems = (p.ranges == 1 && !d.force_partials) ? 0 : (int64_t)p.ranges * p.Mp * p.Np * d.batch;
@@ -931,6 +994,13 @@ void gemm_oz_init() {
   set(oz::oz_gemm_kernel<2, 256>, oz::Cfg<2, 256>::SMEM);
   set(oz::oz_gemm_kernel<2, 128>, oz::Cfg<2, 128>::SMEM);
   set(oz::oz_gemm_kernel<2, 32>, oz::Cfg<2, 32>::SMEM);
+  set(oz::oz_gemm_group_kernel<7, 64>, oz::Cfg<7, 64>::SMEM);
+  set(oz::oz_gemm_group_kernel<7, 32>, oz::Cfg<7, 32>::SMEM);
+  set(oz::oz_gemm_group_kernel<3, 128>, oz::Cfg<3, 128>::SMEM);
+  set(oz::oz_gemm_group_kernel<3, 32>, oz::Cfg<3, 32>::SMEM);
+  set(oz::oz_gemm_group_kernel<2, 256>, oz::Cfg<2, 256>::SMEM);
+  set(oz::oz_gemm_group_kernel<2, 128>, oz::Cfg<2, 128>::SMEM);
+  set(oz::oz_gemm_group_kernel<2, 32>, oz::Cfg<2, 32>::SMEM);
 }
 
 void gemm_oz_pack_a(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaStream_t st,
@@ -987,14 +1057,14 @@ void gemm_oz_pack_b(const GemmDesc& d, int S, uint16_t* planes, int* expo, cudaS
   oz::pack(pb, p.b_elems, d.batch, S, st);
 }
 
-void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, const uint16_t* B,
-                 const int* eb, float2* P, int* err, cudaStream_t st) {
-  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const oz::Plan p = oz::plan(d, S);
-  if ((int64_t)(p.Np / p.bn) * (p.Mp / oz::BM) > 0x7fffffff ||
-      (int64_t)d.batch * p.ranges > 65535)
+namespace oz {
+
+// Kernel arguments of one GEMM whose operands are packed for plan p.
+KArgs kargs_of(const GemmDesc& d, const Plan& p, const uint16_t* A, const int* ea,
+               const uint16_t* B, const int* eb, float2* P, int* err) {
+  if ((int64_t)(p.Np / p.bn) * (p.Mp / BM) > 0x7fffffff || (int64_t)d.batch * p.ranges > 65535)
     throw Error(-1, "gemm_oz: grid too large");
-  oz::KArgs g{};
+  KArgs g{};
   g.A = reinterpret_cast<const __nv_bfloat16*>(A);
   g.B = reinterpret_cast<const __nv_bfloat16*>(B);
   g.a_plane = p.a_elems;
@@ -1022,10 +1092,44 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   g.sC = d.strideC;
   g.out = out_modes(d.alpha, d.beta);
   g.zs = d.batch * p.ranges;
+  if ((int64_t)(p.Np / p.bn) * (p.Mp / BM) * g.zs > 0x7fffffff)
+    throw Error(-1, "gemm_oz: too many tiles");
+  return g;
+}
+
+// Work items (output tiles times K ranges) of a GEMM.
+int64_t items_of(const KArgs& g, int bn) { return (int64_t)(g.Np / bn) * (g.Mp / BM) * g.zs; }
+
+// One grouped launch: persistent CTAs over the combined items of G.
+void launch_group(const KGroup& G, int S, int bn, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>(G.first[G.n], 148);
+  if (grid <= 0) return;
+  if (S == 2 && bn == 256)
+    oz_gemm_group_kernel<2, 256><<<grid, Cfg<2, 256>::THREADS, Cfg<2, 256>::SMEM, st>>>(G);
+  else if (S == 2 && bn == 128)
+    oz_gemm_group_kernel<2, 128><<<grid, Cfg<2, 128>::THREADS, Cfg<2, 128>::SMEM, st>>>(G);
+  else if (S == 2)
+    oz_gemm_group_kernel<2, 32><<<grid, Cfg<2, 32>::THREADS, Cfg<2, 32>::SMEM, st>>>(G);
+  else if (S == 3 && bn == 128)
+    oz_gemm_group_kernel<3, 128><<<grid, Cfg<3, 128>::THREADS, Cfg<3, 128>::SMEM, st>>>(G);
+  else if (S == 3)
+    oz_gemm_group_kernel<3, 32><<<grid, Cfg<3, 32>::THREADS, Cfg<3, 32>::SMEM, st>>>(G);
+  else if (bn == 32)
+    oz_gemm_group_kernel<7, 32><<<grid, Cfg<7, 32>::THREADS, Cfg<7, 32>::SMEM, st>>>(G);
+  else
+    oz_gemm_group_kernel<7, 64><<<grid, Cfg<7, 64>::THREADS, Cfg<7, 64>::SMEM, st>>>(G);
+  RT_CHECK_LAUNCH();
+}
+
+}  // namespace oz
+
+void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, const uint16_t* B,
+                 const int* eb, float2* P, int* err, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
+  const oz::Plan p = oz::plan(d, S);
+  const oz::KArgs g = oz::kargs_of(d, p, A, ea, B, eb, P, err);
   // persistent CTAs: one per SM (the kernel takes most of the shared memory)
-  const int64_t items = (int64_t)(p.Np / p.bn) * (p.Mp / oz::BM) * g.zs;
-  if (items > 0x7fffffff) throw Error(-1, "gemm_oz: too many tiles");
-  const int grid = (int)std::min<int64_t>(items, 148);
+  const int grid = (int)std::min<int64_t>(oz::items_of(g, p.bn), 148);
   using namespace oz;
   if (S == 2 && p.bn == 256)
     oz_gemm_kernel<2, 256><<<grid, Cfg<2, 256>::THREADS, Cfg<2, 256>::SMEM, st>>>(g);
@@ -1042,6 +1146,43 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
   else
     oz_gemm_kernel<7, 64><<<grid, Cfg<7, 64>::THREADS, Cfg<7, 64>::SMEM, st>>>(g);
   RT_CHECK_LAUNCH();
+}
+
+int gemm_oz_mma_group(const OzGroupGemm* gs, int n, int S, cudaStream_t st) {
+  // GEMMs by output-tile width (one kernel configuration each), in order
+  std::vector<std::pair<int, oz::KArgs>> ks;
+  for (int i = 0; i < n; ++i) {
+    const GemmDesc& d = gs[i].d;
+    if (d.M <= 0 || d.N <= 0 || d.batch <= 0) continue;
+    const oz::Plan p = oz::plan(d, S);
+    if (p.ranges != 1 || d.force_partials)
+      throw Error(-1, "gemm_oz_mma_group: a grouped GEMM takes one K range per tile");
+    ks.push_back({p.bn, oz::kargs_of(d, p, gs[i].A, gs[i].ea, gs[i].B, gs[i].eb, nullptr,
+                                     gs[i].err)});
+  }
+  int launches = 0;
+  std::vector<bool> done(ks.size(), false);
+  for (size_t i = 0; i < ks.size(); ++i) {
+    if (done[i]) continue;
+    const int bn = ks[i].first;
+    oz::KGroup G;
+    for (size_t j = i; j < ks.size(); ++j) {
+      if (done[j] || ks[j].first != bn) continue;
+      const int64_t it = oz::items_of(ks[j].second, bn);
+      if (G.n == oz::kMaxGroup || (int64_t)G.first[G.n] + it > 0x7fffffff) {
+        oz::launch_group(G, S, bn, st);
+        ++launches;
+        G = oz::KGroup();
+      }
+      G.g[G.n] = ks[j].second;
+      G.first[G.n + 1] = G.first[G.n] + (int)it;
+      ++G.n;
+      done[j] = true;
+    }
+    oz::launch_group(G, S, bn, st);
+    ++launches;
+  }
+  return launches;
 }
 
 void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,

@@ -92,6 +92,10 @@ struct GemmDesc {
   // tensor-core paths only: write (sum, compensation) partials even with one
   // K range per tile (the 3M combine reads them)
   bool force_partials = false;
+  // digit-plane path only: one K range per output tile (no split-K partial
+  // sums), so that a tile's result does not depend on the other tiles of its
+  // launch (the grouped ladder)
+  bool one_range = false;
 };
 // Number of K slices the kernel will use for this shape (1 = no split).
 int gemm_f64_splits(const GemmDesc& d);
@@ -167,6 +171,22 @@ void gemm_oz_mma(const GemmDesc& d, int S, const uint16_t* A, const int* ea, con
                  const int* eb, float2* P, int* err, cudaStream_t st);
 void gemm_oz_finalize(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
                       cudaStream_t st);
+// One GEMM of a grouped digit-plane launch: its description (one_range set)
+// and its packed operands; err is the pipeline-timeout word of its owner.
+struct OzGroupGemm {
+  GemmDesc d;
+  const uint16_t* A = nullptr;
+  const int* ea = nullptr;
+  const uint16_t* B = nullptr;
+  const int* eb = nullptr;
+  int* err = nullptr;
+};
+// The GEMMs of gs (S planes each) as persistent launches over their combined
+// output tiles: one launch per output-tile width and up to 16 GEMMs.  Every
+// tile is computed exactly as gemm_oz_mma computes it for its GEMM alone, so
+// results do not depend on the grouping; a pipeline timeout sets every err
+// of its launch.  Returns the number of kernel launches.
+int gemm_oz_mma_group(const OzGroupGemm* gs, int n, int S, cudaStream_t st);
 // The 3M combine of the digit-plane form (row scales of each product applied).
 void gemm_oz_combine_3m(const GemmDesc& d, int S, const int* ea, const int* eb, const float2* P,
                         cudaStream_t st);

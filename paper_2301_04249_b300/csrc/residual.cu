@@ -19,7 +19,8 @@
 
 namespace rteom {
 
-void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, double* Rp) {
+void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, double* Rp,
+                      const LadderOut* lad) {
   const int nO = op.nO, nV = op.nV, nQ = op.nchol;
   const bool chol = op.chol;
   const AmpGeom g{nO, nV, op.core};
@@ -242,7 +243,11 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
       // ladder over antisymmetric pairs: sum_{e<f} tau_ij^ef [(ae|bf) - (af|be)]
       // for i<j, a<b, scattered to the four (i,j,a,b) sign patterns
       const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
-      if (npo > 0 && npv > 0) {
+      if (lad && lad->ss[s]) {  // computed ahead (grouped ladder)
+        const double* Rq = lad->ss[s];
+        E.launch(kElementwise, 0.0,
+                 [&] { unpack_pairs_antisym(Rq, R.p, nO, nV, 1.0, E.stream); });
+      } else if (npo > 0 && npv > 0) {
         const int64_t mp = A.mark();
         Tensor tpk = newc({npo, npv});
         Tensor Rq = newc({npo, npv});
@@ -298,7 +303,10 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     ein("mjab,mi->ijab", -1.0, t2ab, Foo[0], 1.0, R);
     ein("mnab,mnij->ijab", 1.0, tau_ab, Wab, 1.0, R);
     if (!chol) {
-      E.contract("ijef,efab->ijab", 1.0, tau_ab, vvvv, 1.0, R, kLadder);
+      if (lad)  // computed ahead (grouped ladder)
+        axpy("ijab->ijab", 1.0, C_(lad->ab, {nO, nO, nV, nV}), 1.0, R);
+      else
+        E.contract("ijef,efab->ijab", 1.0, tau_ab, vvvv, 1.0, R, kLadder);
       const int64_t mz = A.mark();
       Tensor Z1 = newc({nO, nO, nV, nO});
       ein("ijef,mfae->ijam", 1.0, tau_ab, ovvv, 0.0, Z1);
@@ -555,6 +563,43 @@ void compute_residual(Engine& E, const ResidualOperands& op, const double* tp, d
     A.release(ml);
   }
   E.arena.release(mark);
+}
+
+void ladder_part(Engine& E, const ResidualOperands& op, const double* tp, LadderOut* out) {
+  const int nO = op.nO, nV = op.nV;
+  if (op.chol) throw Error(-1, "ladder_part: the grouped ladder needs the resident ladder blocks");
+  const AmpGeom g{nO, nV, op.core};
+  Arena& A = E.arena;
+  auto blk = [&](int b) { return const_cast<double*>(tp) + 2 * g.off(b); };
+  auto t2t1 = [&](const Tensor& o, const Tensor& t2, const Tensor& x, const Tensor& y, double c3) {
+    E.launch(kElementwise, 0.0,
+             [&] { t2_plus_t1t1(o.p, t2.p, 1.0, x.p, y.p, 1.0, c3, nO, nV, E.stream); });
+  };
+  const Tensor t1[2] = {make_tensor(blk(0), true, {nO, nV}), make_tensor(blk(1), true, {nO, nV})};
+  // tau as compute_residual forms it: t2 + t1 t1 (antisymmetrised same-spin)
+  const Tensor tau_ab = A.tensor(true, {nO, nO, nV, nV});
+  t2t1(tau_ab, make_tensor(blk(3), true, {nO, nO, nV, nV}), t1[0], t1[1], 0.0);
+  Tensor vvvv = make_tensor(const_cast<double*>(op.vvvv), false, {nV, nV, nV, nV});
+  vvvv.constant = true;
+  vvvv.released = op.vvvv_released;
+  const Tensor lab = A.tensor(true, {nO, nO, nV, nV});
+  out->ab = lab.p;
+  E.contract("ijef,efab->ijab", 1.0, tau_ab, vvvv, 0.0, lab, kLadder);
+  const int64_t npo = (int64_t)nO * (nO - 1) / 2, npv = (int64_t)nV * (nV - 1) / 2;
+  for (int s = 0; s < 2; ++s) {
+    out->ss[s] = nullptr;
+    if (npo == 0 || npv == 0) continue;
+    const Tensor tau = A.tensor(true, {nO, nO, nV, nV});
+    t2t1(tau, make_tensor(blk(s == 0 ? 2 : 4), true, {nO, nO, nV, nV}), t1[s], t1[s], -1.0);
+    const Tensor tpk = A.tensor(true, {npo, npv});
+    E.launch(kElementwise, 0.0, [&] { pack_pairs(tau.p, tpk.p, nO, nV, E.stream); });
+    Tensor Wm = make_tensor(const_cast<double*>(op.vvvv_as), false, {npv, npv});
+    Wm.constant = true;
+    Wm.released = op.vvvv_as_released;
+    const Tensor Rq = A.tensor(true, {npo, npv});
+    out->ss[s] = Rq.p;
+    E.contract("pq,qr->pr", 1.0, tpk, Wm, 0.0, Rq, kLadder);
+  }
 }
 
 void prepack_ladder(Engine& E, const ResidualOperands& op, bool same_spin) {

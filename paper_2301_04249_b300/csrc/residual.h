@@ -39,10 +39,31 @@ struct ResidualOperands {
                *fvv_c[2] = {nullptr, nullptr};
 };
 
+// Results of the particle-particle ladder computed ahead of the rest of a
+// residual (the grouped ladder): ab[i][j][a][b] = sum_ef tau_ij^ef (ae|bf)
+// for the alpha-beta block and ss[s][(i<j)][(a<b)] = sum_(e<f) tau_ij^ef
+// [(ae|bf) - (af|be)] for the same-spin blocks (complex; ss[s] null when the
+// spin has no pair).
+struct LadderOut {
+  double* ab = nullptr;
+  double* ss[2] = {nullptr, nullptr};
+};
+
 // R = full projections for amplitudes t (both padded amplitude vectors,
 // layout of AmpGeom).  Scratch comes from E.arena; pad entries of R are
-// unspecified.  Issues only stream-ordered work (capturable).
-void compute_residual(Engine& E, const ResidualOperands& op, const double* t, double* R);
+// unspecified.  Issues only stream-ordered work (capturable).  With `lad`
+// (resident ladder blocks only) the ladder terms are added from it instead
+// of being contracted here.
+void compute_residual(Engine& E, const ResidualOperands& op, const double* t, double* R,
+                      const LadderOut* lad = nullptr);
+
+// First part of a residual with the grouped ladder (Section 3.1: the
+// dominant contraction sum_cd v_abcd tau_ij^cd, resident ladder blocks): tau
+// of the three T2 blocks and the three ladder GEMMs posed into `out`, which
+// E (defer_ladder set) records in E.deferred with their operands packed
+// instead of launching them.  Everything allocated here stays in the arena
+// (the caller releases it after compute_residual(..., out) has run).
+void ladder_part(Engine& E, const ResidualOperands& op, const double* t, LadderOut* out);
 
 // Packs the constant operand of the alpha-beta ladder (same_spin false) or of
 // the same-spin pair ladder into the engine's cache, through the same

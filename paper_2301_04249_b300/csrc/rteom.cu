@@ -26,6 +26,7 @@ using namespace rteom;
 
 namespace {
 thread_local std::string g_create_error;
+constexpr int kMaxGroupMembers = 1024;  // contexts per rteom_propagate_group call
 }
 
 struct rteom_ctx {
@@ -54,6 +55,16 @@ struct rteom_ctx {
   long long steps = 0, micro_total = 0;
   long long graph_kernels = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // residual(T_N -> R_N), residual(T_K -> R_K)
+  // Grouped ladder (RTEOM_FLAG_GROUPED): a residual runs as graph A (tau and
+  // the packed operands of the three ladder GEMMs), the ladder GEMMs in one
+  // grouped launch with those of the other contexts of a round, then graph B
+  // (the rest of the residual, the ladder results added), per residual kind
+  // as graph[]; lad_gemms holds the GEMMs graph A's packs feed.
+  bool grouped = false;
+  cudaGraphExec_t graph_a[2] = {nullptr, nullptr}, graph_b[2] = {nullptr, nullptr};
+  long long graph_ab_kernels[2] = {0, 0};
+  std::vector<Engine::Deferred> lad_gemms[2];
+  cudaEvent_t ev_group = nullptr;  // orders a round across the members' streams
   bool tune_first = false;  // run the next residual eagerly for the autotuner
   bool eager_timing = false;  // rteom_set_timing(ctx, 2): residuals outside graphs
   // Anderson acceleration of the micro-iteration (RTEOM_FLAG_ANDERSON):
@@ -118,6 +129,11 @@ struct rteom_ctx {
     if (run.ev) cudaEventDestroy(run.ev);
     for (auto& gx : graph)
       if (gx) cudaGraphExecDestroy(gx);
+    for (int w = 0; w < 2; ++w) {
+      if (graph_a[w]) cudaGraphExecDestroy(graph_a[w]);
+      if (graph_b[w]) cudaGraphExecDestroy(graph_b[w]);
+    }
+    if (ev_group) cudaEventDestroy(ev_group);
     for (auto& v : graph_pairs)
       for (auto& pr : v) {
         cudaEventDestroy(pr.a);
@@ -202,9 +218,140 @@ void collect_graph_timing(rteom_ctx* c) {
   }
 }
 
+// The recorded ladder GEMMs of a round, as one grouped launch per tile width
+// on stream st; the launch counts are charged to engine E.
+void launch_ladders(Engine& E, const std::vector<OzGroupGemm>& gemms, double flops,
+                    cudaStream_t st) {
+  if (gemms.empty()) return;
+  int n = 0;
+  E.launch(kLadder, flops,
+           [&] { n = gemm_oz_mma_group(gemms.data(), (int)gemms.size(), E.oz_planes, st); },
+           "grouped ladder");
+  if (n > 1) E.launches += n - 1;
+}
+
+// One residual outside graphs: compute_residual, or with the grouped ladder
+// its two parts around a launch of this context's own ladder GEMMs.
+void residual_eager(rteom_ctx* c, const double* t, double* R) {
+  Engine& E = c->E;
+  if (!c->grouped) {
+    compute_residual(E, c->op, t, R);
+    return;
+  }
+  const int64_t m0 = E.arena.mark();
+  LadderOut lo;
+  E.deferred.clear();
+  ladder_part(E, c->op, t, &lo);
+  std::vector<OzGroupGemm> gemms;
+  double flops = 0.0;
+  for (const auto& d : E.deferred) {
+    gemms.push_back(d.gemm);
+    flops += d.flops;
+  }
+  E.deferred.clear();
+  launch_ladders(E, gemms, flops, c->stream);
+  compute_residual(E, c->op, t, R, &lo);
+  E.arena.release(m0);
+}
+
+// Capture f's launches on the context's stream as a graph.
+template <class F>
+cudaGraphExec_t capture_graph(rteom_ctx* c, F&& f, long long* kernels) {
+  const long long before = c->E.launches;
+  cudaGraph_t gr = nullptr;
+  RT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    f();
+  } catch (...) {
+    cudaStreamEndCapture(c->stream, &gr);
+    if (gr) cudaGraphDestroy(gr);
+    c->E.launches = before;
+    throw;
+  }
+  RT_CUDA(cudaStreamEndCapture(c->stream, &gr));
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, gr, 0);
+  cudaGraphDestroy(gr);
+  RT_CUDA(e);
+  *kernels = c->E.launches - before;
+  c->E.launches = before;
+  return ex;
+}
+
+// Graphs A and B of residual kind `which` of a grouped context.  Graph A's
+// packs and ladder results sit in the arena above its level between
+// residuals, where graph B's own scratch starts above them.
+void ensure_group_graphs(rteom_ctx* c, int which) {
+  if (c->graph_a[which]) return;
+  Engine& E = c->E;
+  const double* t = which == 0 ? c->T_N : c->T_K;
+  double* R = which == 0 ? c->R_N : c->R_K;
+  const int64_t m0 = E.arena.mark();
+  LadderOut lo;
+  long long ka = 0, kb = 0;
+  try {
+    E.deferred.clear();
+    c->graph_a[which] = capture_graph(c, [&] { ladder_part(E, c->op, t, &lo); }, &ka);
+    c->lad_gemms[which] = E.deferred;
+    E.deferred.clear();
+    c->graph_b[which] =
+        capture_graph(c, [&] { compute_residual(E, c->op, t, R, &lo); }, &kb);
+  } catch (...) {
+    E.arena.release(m0);
+    E.deferred.clear();
+    if (c->graph_a[which]) cudaGraphExecDestroy(c->graph_a[which]);
+    c->graph_a[which] = nullptr;
+    c->lad_gemms[which].clear();
+    throw;
+  }
+  E.arena.release(m0);
+  c->graph_ab_kernels[which] = ka + kb;
+}
+
+// One residual of each member (kinds which[i]) with every member's ladder
+// GEMMs in grouped launches: the members' graphs A on their own streams, the
+// grouped GEMMs on the first member's stream after all of them, then the
+// members' graphs B after the GEMMs.  Each GEMM computes its tiles as it
+// would alone (one K range per tile), so results do not depend on the group.
+void group_residuals(rteom_ctx* const* cs, const int* which, int n) {
+  for (int i = 0; i < n; ++i) ensure_group_graphs(cs[i], which[i]);
+  rteom_ctx* lead = cs[0];
+  cudaStream_t gs = lead->stream;
+  std::vector<OzGroupGemm> gemms;
+  double flops = 0.0;
+  for (int i = 0; i < n; ++i) {
+    rteom_ctx* c = cs[i];
+    RT_CUDA(cudaGraphLaunch(c->graph_a[which[i]], c->stream));
+    c->E.launches += c->graph_ab_kernels[which[i]];
+    for (const auto& d : c->lad_gemms[which[i]]) {
+      gemms.push_back(d.gemm);
+      flops += d.flops;
+    }
+    if (c->stream != gs) {
+      if (!c->ev_group) RT_CUDA(cudaEventCreateWithFlags(&c->ev_group, cudaEventDisableTiming));
+      RT_CUDA(cudaEventRecord(c->ev_group, c->stream));
+      RT_CUDA(cudaStreamWaitEvent(gs, c->ev_group, 0));
+    }
+  }
+  launch_ladders(lead->E, gemms, flops, gs);
+  if (n > 1) {
+    if (!lead->ev_group) RT_CUDA(cudaEventCreateWithFlags(&lead->ev_group, cudaEventDisableTiming));
+    RT_CUDA(cudaEventRecord(lead->ev_group, gs));
+  }
+  for (int i = 0; i < n; ++i) {
+    rteom_ctx* c = cs[i];
+    if (c->stream != gs) RT_CUDA(cudaStreamWaitEvent(c->stream, lead->ev_group, 0));
+    RT_CUDA(cudaGraphLaunch(c->graph_b[which[i]], c->stream));
+  }
+}
+
 void run_residual(rteom_ctx* c, int which) {
   const double* t = which == 0 ? c->T_N : c->T_K;
   double* R = which == 0 ? c->R_N : c->R_K;
+  if (c->grouped) {  // a group of one
+    group_residuals(&c, &which, 1);
+    return;
+  }
   if (c->E.timing && (!c->E.graph_timing_ok || c->eager_timing)) {  // eager, every kernel timed
     compute_residual(c->E, c->op, t, R);
     return;
@@ -296,7 +443,7 @@ void energy_into(rteom_ctx* c, const double* t, double* Ehist, double* Chist, lo
 }
 
 void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool anderson,
-                        double out[3]);
+                        bool grouped, double out[3]);
 
 // Chunk sizes of the Cholesky-mode residual: values of a per ladder chunk
 // (a W chunk of chunk_a*nV^3 doubles) and of m per (mf|ae) chunk, each chunk
@@ -327,12 +474,17 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
       chol = true;
     } else {
       double pb[3];
-      plan_context_bytes(O, V, nchol, c->precision, false, c->flags & RTEOM_FLAG_ANDERSON, pb);
+      plan_context_bytes(O, V, nchol, c->precision, false, c->flags & RTEOM_FLAG_ANDERSON,
+                         c->grouped, pb);
       size_t fr = 0, tot = 0;
       RT_CUDA(cudaMemGetInfo(&fr, &tot));
       chol = pb[1] > 0.97 * (double)fr;
+      if (chol && c->grouped)
+        throw Error(RTEOM_ERR_OOM, "the grouped ladder needs the resident ladder blocks, which "
+                                   "do not fit the free device memory");
     }
   }
+  E.defer_ladder = c->grouped;
 
   // inputs
   double* d_eps = c->dmalloc(8 * nb);
@@ -444,8 +596,15 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
   auto dry_peak = [&]() {
     E.dry = true;
     E.arena.init(reinterpret_cast<double*>(uintptr_t(4096)), int64_t(1) << 50);
-    compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
-                     reinterpret_cast<double*>(uintptr_t(4096)));
+    if (c->grouped) {  // graph A's packs and results stay below graph B's scratch
+      LadderOut lo;
+      ladder_part(E, op, reinterpret_cast<double*>(uintptr_t(4096)), &lo);
+      compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
+                       reinterpret_cast<double*>(uintptr_t(4096)), &lo);
+    } else {
+      compute_residual(E, op, reinterpret_cast<double*>(uintptr_t(4096)),
+                       reinterpret_cast<double*>(uintptr_t(4096)));
+    }
     E.dry = false;
     return E.arena.peak_bytes() / 8;
   };
@@ -632,7 +791,7 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
       }
     }
     E.tuning = E.autotune;
-    compute_residual(E, c->op, c->T_N, c->R_K);
+    residual_eager(c, c->T_N, c->R_K);
     E.tc_cache_fill = false;
     E.tuning = false;
     RT_CUDA(cudaStreamSynchronize(st));
@@ -649,9 +808,10 @@ void setup(rteom_ctx* c, const double* eps, const double* L, const double* t1_gs
 // cache filled ladder blocks first, each FP64 ladder block freed after its
 // pack.  chol: the Cholesky mode (no (ov|vv)/(vv|vv) blocks; the slot-space
 // Cholesky blocks stay); anderson: the buffers of the accelerated
-// micro-iteration.
+// micro-iteration; grouped: the grouped ladder (its packs and results held
+// through the residual).
 void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool anderson,
-                        double out[3]) {
+                        bool grouped, double out[3]) {
   const double nO = O, nVd = V + 1.0, nb = O + V;
   const int nV = V + 1;
   const double npv = nVd * (nVd - 1.0) / 2.0;
@@ -695,7 +855,14 @@ void plan_context_bytes(int O, int V, int nchol, int precision, bool chol, bool 
     E.dry = true;
     E.plan_cached = cached && packed;
     E.arena.init(fake(30), int64_t(1) << 50);
-    compute_residual(E, op, fake(31), fake(32));
+    if (grouped) {
+      E.defer_ladder = true;
+      LadderOut lo;
+      ladder_part(E, op, fake(31), &lo);
+      compute_residual(E, op, fake(31), fake(32), &lo);
+    } else {
+      compute_residual(E, op, fake(31), fake(32));
+    }
     return (double)E.arena.peak_bytes();
   };
   const double setup_need =
@@ -828,11 +995,11 @@ static void anderson_next(rteom_ctx* c) {
   }
 }
 
-// Launch micro-iteration k of the current step (residual when k > 0, the
-// Adams-Moulton update, the status-word copy) and record the run event.
-static void launch_micro(rteom_ctx* c, int k) {
+// Launch the rest of micro-iteration k of the current step after its
+// residual (the Adams-Moulton update, the status-word copy) and record the
+// run event.
+static void launch_update(rteom_ctx* c, int k) {
   cudaStream_t st = c->stream;
-  if (k > 0) run_residual(c, 1);
   RT_CUDA(cudaMemsetAsync(c->maxdiff, 0, 8, st));
   const double* tk_in = k == 0 ? c->T_N : c->T_K;
   const double* Rk = k == 0 ? c->R_N : c->R_K;
@@ -861,6 +1028,59 @@ static void launch_micro(rteom_ctx* c, int k) {
   RT_CUDA(cudaEventRecord(c->run.ev, st));
 }
 
+// Launch micro-iteration k of the current step (residual when k > 0, then
+// the update).
+static void launch_micro(rteom_ctx* c, int k) {
+  if (k > 0) run_residual(c, 1);
+  launch_update(c, k);
+}
+
+// The status word of micro-iteration r.k has arrived.  A pipeline timeout or
+// non-finite amplitudes fail the run; on convergence t^(k+1) is accepted and
+// the cumulant step taken (*next = 0 while steps remain: R(t_n) of the next
+// step; -1 when all are done); otherwise *next = 1 for micro-iteration k+1
+// (r.k advanced), unless the cap is reached.
+static int after_status(rteom_ctx* c, int* next) {
+  auto& r = c->run;
+  *next = -1;
+  if (c->h_maxdiff[1] != 0) {
+    r.phase = 2;
+    return fail(c, RTEOM_ERR_CUDA,
+                "tensor-core pipeline wait timed out (code " +
+                    std::to_string((long long)c->h_maxdiff[1]) + ")");
+  }
+  const double d = std::sqrt(bits_to_double(c->h_maxdiff[0]));  // the kernel keeps |.|^2
+  if (!std::isfinite(d)) {
+    r.phase = 2;
+    return fail(c, RTEOM_ERR_NONFINITE,
+                "amplitudes became non-finite at step " + std::to_string(c->steps));
+  }
+  if (d < r.tol) {  // converged: accept t^(k+1), cumulant step
+    cudaStream_t st = c->stream;
+    RT_CUDA(cudaMemcpyAsync(c->T_N, c->and_g ? c->and_g : c->T_K, 16ull * c->g.total(),
+                            cudaMemcpyDeviceToDevice, st));
+    energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
+    c->steps += 1;
+    c->micro_total += r.k + 1;
+    r.done += 1;
+    if (r.done >= r.target) {
+      r.phase = 2;
+    } else {
+      r.phase = 0;
+      *next = 0;
+    }
+    return RTEOM_OK;
+  }
+  if (r.k + 1 >= r.max_micro) {
+    r.phase = 2;
+    return fail(c, RTEOM_ERR_NOT_CONVERGED,
+                "micro-iterations did not reach tol at step " + std::to_string(c->steps));
+  }
+  r.k += 1;
+  *next = 1;
+  return RTEOM_OK;
+}
+
 // Advance without blocking.  *finished: all requested steps done; *waiting:
 // the device still owes the status word of the pending micro-iteration.
 int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
@@ -887,41 +1107,15 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
     }
     RT_CUDA(q);
     if (c->E.timing) collect_graph_timing(c);  // the stream passed every pending replay
-    if (c->h_maxdiff[1] != 0) {
-      r.phase = 2;
-      return fail(c, RTEOM_ERR_CUDA,
-                  "tensor-core pipeline wait timed out (code " +
-                      std::to_string((long long)c->h_maxdiff[1]) + ")");
-    }
-    const double d = std::sqrt(bits_to_double(c->h_maxdiff[0]));  // the kernel keeps |.|^2
-    if (!std::isfinite(d)) {
-      r.phase = 2;
-      return fail(c, RTEOM_ERR_NONFINITE,
-                  "amplitudes became non-finite at step " + std::to_string(c->steps));
-    }
-    if (d < r.tol) {  // converged: accept t^(k+1), cumulant step
-      cudaStream_t st = c->stream;
-      RT_CUDA(cudaMemcpyAsync(c->T_N, c->and_g ? c->and_g : c->T_K, 16ull * c->g.total(),
-                              cudaMemcpyDeviceToDevice, st));
-      energy_into(c, c->T_N, c->histE, c->histC, c->steps, 1);
-      c->steps += 1;
-      c->micro_total += r.k + 1;
-      r.done += 1;
-      if (r.done >= r.target) {
-        r.phase = 2;
-        *finished = true;
-      } else {
-        r.phase = 0;
-      }
+    int next = -1;
+    const int rc = after_status(c, &next);
+    if (rc != RTEOM_OK) return rc;
+    if (next < 0) {
+      *finished = true;
       return RTEOM_OK;
     }
-    if (r.k + 1 >= r.max_micro) {
-      r.phase = 2;
-      return fail(c, RTEOM_ERR_NOT_CONVERGED,
-                  "micro-iterations did not reach tol at step " + std::to_string(c->steps));
-    }
+    if (next == 0) return RTEOM_OK;  // the next poll starts the next step
     if (c->and_g) anderson_next(c);  // x_{k+1} into T_K
-    r.k += 1;
     launch_micro(c, r.k);
     *waiting = 1;
     return RTEOM_OK;
@@ -954,8 +1148,13 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   if (!valid_precision(precision))
     return bad(RTEOM_ERR_ARG, "precision must be RTEOM_FP64, RTEOM_SPLIT_BF16, RTEOM_SPLIT_TF32, "
                               "RTEOM_FP64_OZAKI or RTEOM_SPLIT_FP16");
-  if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON))
+  if (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON |
+                RTEOM_FLAG_GROUPED))
     return bad(RTEOM_ERR_ARG, "unknown flag bits");
+  if (!grouped_flags_ok(precision, flags))
+    return bad(RTEOM_ERR_ARG, "RTEOM_FLAG_GROUPED needs RTEOM_FP64_OZAKI, RTEOM_SPLIT_BF16 or "
+                              "RTEOM_SPLIT_FP16, without RTEOM_FLAG_LADDER_CHOLESKY or "
+                              "RTEOM_FLAG_ANDERSON");
   const size_t nb = size_t(nocc) + nvir;
   if ((double)(nvir + 1) * (nvir + 1) > 2.0e9)
     return bad(RTEOM_ERR_ARG, "nvir too large: (nvir+1)^2 pair indices must fit 32 bits");
@@ -979,6 +1178,7 @@ int rteom_create(rteom_ctx** out, int nocc, int nvir, int nchol, const double* e
   c->core = core_index;
   c->precision = precision;
   c->flags = flags;
+  c->grouped = (flags & RTEOM_FLAG_GROUPED) != 0;
   c->nO = nocc;
   c->nV = nvir + 1;
   c->g = AmpGeom{c->nO, c->nV, core_index};
@@ -1044,6 +1244,80 @@ int rteom_propagate(rteom_ctx* c, int nsteps, double dt, double tol, int max_mic
     if (c->E.timing) c->E.collect_timing();
     return RTEOM_OK;
   });
+}
+
+int rteom_propagate_group(rteom_ctx* const* ctxs, int n, int nsteps, double dt, double tol,
+                          int max_micro, double* const* C_out) {
+  if (!ctxs || n < 1 || n > kMaxGroupMembers) return RTEOM_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    rteom_ctx* c = ctxs[i];
+    if (!c) return RTEOM_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(c, RTEOM_ERR_ARG, "a context appears twice in the group");
+    if (!c->grouped)
+      return fail(c, RTEOM_ERR_ARG, "a group member was created without RTEOM_FLAG_GROUPED");
+    if (c->E.oz_planes != ctxs[0]->E.oz_planes)
+      return fail(c, RTEOM_ERR_ARG, "group members must share one precision form");
+  }
+  std::vector<long long> start(n);
+  for (int i = 0; i < n; ++i) {
+    start[i] = ctxs[i]->steps;
+    const int rc = rteom_internal_begin(ctxs[i], nsteps, dt, tol, max_micro);
+    if (rc != RTEOM_OK) return rc;
+  }
+  // rounds: every member with work left evaluates one residual (R(t_n) of a
+  // new step, or R(t^(k)) of its next micro-iteration) and its update
+  std::vector<rteom_ctx*> mem;
+  std::vector<int> which;
+  while (true) {
+    mem.clear();
+    which.clear();
+    for (int i = 0; i < n; ++i) {
+      rteom_ctx* c = ctxs[i];
+      int w = -1;
+      const int rc = guarded(c, [&]() -> int {
+        auto& r = c->run;
+        if (r.phase == 2) return RTEOM_OK;
+        if (r.phase == 0) {
+          w = 0;
+          return RTEOM_OK;
+        }
+        RT_CUDA(cudaEventSynchronize(r.ev));
+        return after_status(c, &w);
+      });
+      if (rc != RTEOM_OK) return rc;
+      if (w >= 0) {
+        mem.push_back(c);
+        which.push_back(w);
+      }
+    }
+    if (mem.empty()) break;
+    const int rc = guarded(mem[0], [&] {
+      group_residuals(mem.data(), which.data(), (int)mem.size());
+      for (size_t i = 0; i < mem.size(); ++i) {
+        auto& r = mem[i]->run;
+        if (which[i] == 0) {  // the first micro-iteration starts from t^(0) = t_n
+          r.k = 0;
+          r.phase = 1;
+        }
+        launch_update(mem[i], r.k);
+      }
+      return RTEOM_OK;
+    });
+    if (rc != RTEOM_OK) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    rteom_ctx* c = ctxs[i];
+    const int rc = guarded(c, [&] {
+      if (C_out && C_out[i])
+        RT_CUDA(cudaMemcpyAsync(C_out[i], c->histC + 2 * start[i], 16ull * (nsteps + 1),
+                                cudaMemcpyDeviceToHost, c->stream));
+      RT_CUDA(cudaStreamSynchronize(c->stream));
+      return RTEOM_OK;
+    });
+    if (rc != RTEOM_OK) return rc;
+  }
+  return RTEOM_OK;
 }
 
 int rteom_spectrum(rteom_ctx* c, const double* omega, int nomega, double eta, double* A_out) {
@@ -1151,13 +1425,15 @@ int rteom_set_state(rteom_ctx* c, const double* t_in, long long steps, const dou
 int rteom_plan_bytes(int nocc, int nvir, int nchol, int precision, int flags, double* bytes) {
   if (!bytes || nocc < 1 || nvir < 1 || nchol < 0 ||
       (flags & ~(RTEOM_FLAG_CUMULANT_NO_FOV | RTEOM_FLAG_LADDER_CHOLESKY |
-                 RTEOM_FLAG_ANDERSON)) ||
-      !valid_precision(precision) || (double)(nvir + 1) * (nvir + 1) > 2.0e9)
+                 RTEOM_FLAG_ANDERSON | RTEOM_FLAG_GROUPED)) ||
+      !valid_precision(precision) || (double)(nvir + 1) * (nvir + 1) > 2.0e9 ||
+      !grouped_flags_ok(precision, flags))
     return RTEOM_ERR_ARG;
   try {
     plan_context_bytes(nocc, nvir, nchol, precision,
                        (flags & RTEOM_FLAG_LADDER_CHOLESKY) && nchol > 0,
-                       (flags & RTEOM_FLAG_ANDERSON) != 0, bytes);
+                       (flags & RTEOM_FLAG_ANDERSON) != 0, (flags & RTEOM_FLAG_GROUPED) != 0,
+                       bytes);
   } catch (const std::exception&) {
     return RTEOM_ERR_ARG;
   }
@@ -1174,7 +1450,7 @@ int rteom_debug_residual(rteom_ctx* c, const double* t_in, double* R_out, double
     double* tmp = c->dmalloc(ub);
     RT_CUDA(cudaMemcpyAsync(tmp, t_in, ub, cudaMemcpyHostToDevice, c->stream));
     c->E.launch(kElementwise, 0.0, [&] { pack_amplitudes(c->g, tmp, c->T_K, c->stream); });
-    compute_residual(c->E, c->op, c->T_K, c->R_K);
+    residual_eager(c, c->T_K, c->R_K);
     c->E.launch(kElementwise, 0.0, [&] { unpack_amplitudes(c->g, c->R_K, tmp, c->stream); });
     RT_CUDA(cudaMemcpyAsync(R_out, tmp, ub, cudaMemcpyDeviceToHost, c->stream));
     RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, c->stream));
@@ -1220,7 +1496,7 @@ int rteom_debug_residual_sparse(rteom_ctx* c, const long long* t_index, const do
     if (nr) RT_CUDA(cudaMemcpyAsync(d_ri, r_index, 8ull * nr, cudaMemcpyHostToDevice, st));
     RT_CUDA(cudaMemsetAsync(c->T_K, 0, 16ull * c->g.total(), st));
     c->E.launch(kElementwise, 0.0, [&] { scatter_unpadded(c->g, d_ti, d_tv, nt, c->T_K, st); });
-    compute_residual(c->E, c->op, c->T_K, c->R_K);
+    residual_eager(c, c->T_K, c->R_K);
     c->E.launch(kElementwise, 0.0, [&] { gather_unpadded(c->g, c->R_K, d_ri, nr, d_R, st); });
     if (nr) RT_CUDA(cudaMemcpyAsync(R_out, d_R, 16ull * nr, cudaMemcpyDeviceToHost, st));
     RT_CUDA(cudaMemcpyAsync(c->h_maxdiff, c->maxdiff, 16, cudaMemcpyDeviceToHost, st));
@@ -1237,6 +1513,8 @@ int rteom_debug_residual_sparse(rteom_ctx* c, const long long* t_index, const do
 int rteom_set_timing(rteom_ctx* c, int on) {
   if (!c) return RTEOM_ERR_ARG;
   if (on < 0 || on > 3) return fail(c, RTEOM_ERR_ARG, "timing mode must be 0, 1, 2 or 3");
+  if (c->grouped && on != 0)
+    return fail(c, RTEOM_ERR_ARG, "timing modes are not available with the grouped ladder");
   c->E.timing = on != 0;
   c->eager_timing = on == 2;
   c->E.graph_timed_mask = on == 3 ? (1u << kLadder) | (1u << kContract) : (1u << kLadder);

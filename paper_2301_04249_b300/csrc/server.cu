@@ -68,7 +68,8 @@ struct Request {
 double estimate_bytes(int O, int V, int nchol, int precision, int flags = 0) {
   double b[3] = {0.0, 0.0, 0.0};
   if (rteom_plan_bytes(O, V, nchol, precision,
-                       flags & (RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON), b) != RTEOM_OK)
+                       flags & (RTEOM_FLAG_LADDER_CHOLESKY | RTEOM_FLAG_ANDERSON |
+                                RTEOM_FLAG_GROUPED), b) != RTEOM_OK)
     return 0.0;
   return std::ceil(1.05 * b[0]) + 256.0 * 1024 * 1024;
 }

@@ -47,7 +47,8 @@ def _create(**kw):
     (dict(core=-1), P.RTEOM_ERR_ARG),
     (dict(eps=None), P.RTEOM_ERR_ARG),
     (dict(precision=7), P.RTEOM_ERR_ARG),
-    (dict(flags=8), P.RTEOM_ERR_ARG),
+    (dict(flags=16), P.RTEOM_ERR_ARG),                              # unknown bit
+    (dict(flags=8), P.RTEOM_ERR_ARG),                               # grouped needs digit planes
     (dict(eps=np.array([-20.0, np.nan, 0.5, 1.0, 2.0])), P.RTEOM_ERR_NONFINITE),
     (dict(L=np.arange(25.0).reshape(1, 5, 5)), P.RTEOM_ERR_ARG),   # not symmetric
 ])

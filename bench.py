@@ -471,19 +471,23 @@ def serving_mix(n_req, kind="scaled"):
     return out
 
 
-def run_serving(P, precision, n_req, tol, kind="scaled"):
+def run_serving(P, precision, n_req, tol, kind="scaled", flags=0, serial=None):
     """Serve the mix with Poisson arrivals at twice the mean service rate;
     returns latency percentiles, makespan and the serial (one at a time)
-    reference measured on the same requests."""
+    reference measured on the same requests (or taken from ``serial``, the
+    per-request service times of an earlier run of the same mix and form).
+    flags: request flags (RTEOM_FLAG_GROUPED: running requests share grouped
+    ladder launches)."""
     mix = serving_mix(n_req, kind)
     dt = 0.025
-    serial = []
-    with P.Server(max_active=1, precision=precision) as s:
-        for p, n in mix:
-            t0 = time.perf_counter()
-            rid = s.submit(p, n, dt, tol=tol)
-            s.wait(rid, 600.0)
-            serial.append(time.perf_counter() - t0)
+    if serial is None:
+        serial = []
+        with P.Server(max_active=1, precision=precision) as s:
+            for p, n in mix:
+                t0 = time.perf_counter()
+                rid = s.submit(p, n, dt, tol=tol, flags=flags)
+                s.wait(rid, 600.0)
+                serial.append(time.perf_counter() - t0)
     mean_service = float(np.mean(serial))
     rate = 2.0 / mean_service
     arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, n_req))
@@ -494,7 +498,7 @@ def run_serving(P, precision, n_req, tol, kind="scaled"):
         for (p, n), ta in zip(mix, arrivals):
             while time.perf_counter() - t0 < ta:
                 time.sleep(0.0005)
-            ids.append(s.submit(p, n, dt, tol=tol))
+            ids.append(s.submit(p, n, dt, tol=tol, flags=flags))
         for rid in ids:
             s.wait(rid, 600.0)
         makespan = time.perf_counter() - t0
@@ -510,7 +514,8 @@ def run_serving(P, precision, n_req, tol, kind="scaled"):
             "throughput_steps_per_s": steps / makespan,
             "serial_steps_per_s": steps / float(np.sum(serial)),
             "speedup_vs_serial": float(np.sum(serial)) / makespan,
-            "mean_service_s": mean_service}
+            "mean_service_s": mean_service, "serial_service_s": [float(x) for x in serial],
+            "grouped_ladder": bool(flags & P.RTEOM_FLAG_GROUPED)}
 
 
 def serving_block(P, args):
@@ -519,22 +524,31 @@ def serving_block(P, args):
     if args.serving_mix == "c4":
         os.environ["RTEOM_AUTOTUNE"] = "0"
         try:
+            fp16 = run_serving(P, P.RTEOM_SPLIT_FP16, args.serving_requests, args.tol, "c4")
+            # the same mix with grouped ladder launches, against the same
+            # one-at-a-time reference
+            fp16_grouped = run_serving(P, P.RTEOM_SPLIT_FP16, args.serving_requests, args.tol,
+                                       "c4", flags=P.RTEOM_FLAG_GROUPED,
+                                       serial=fp16["serial_service_s"])
             return {"workload": f"c4 shapes: {args.serving_requests} requests, O~U{{4..24}}, "
                                 "V~U{40..240}, Nchol=4V, steps~U{4..16} (production: "
                                 "U{500..4000}), dt=0.025, Poisson arrivals at 2x the mean "
                                 "service rate, 8 slots, admission by device memory, autotuner off",
-                    "split_fp16": run_serving(P, P.RTEOM_SPLIT_FP16, args.serving_requests,
-                                              args.tol, "c4"),
+                    "split_fp16": fp16, "split_fp16_grouped": fp16_grouped,
                     "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
                                               args.tol, "c4")}
         finally:
             del os.environ["RTEOM_AUTOTUNE"]
+    bf16 = run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests, args.tol)
     return {"workload": f"scaled core-hole mix: {args.serving_requests} requests, O~U{{4..8}}, "
                         "V~U{20..48}, Nchol=4V, steps~U{20..80}, dt=0.025, Poisson arrivals at 2x "
                         "the mean service rate, 8 slots",
             "fp64": run_serving(P, P.RTEOM_FP64, args.serving_requests, args.tol),
             "split_tf32": run_serving(P, P.RTEOM_SPLIT_TF32, args.serving_requests, args.tol),
-            "split_bf16": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests, args.tol)}
+            "split_bf16": bf16,
+            "split_bf16_grouped": run_serving(P, P.RTEOM_SPLIT_BF16, args.serving_requests,
+                                              args.tol, flags=P.RTEOM_FLAG_GROUPED,
+                                              serial=bf16["serial_service_s"])}
 
 
 # ----------------------------------------------------------------- our arm

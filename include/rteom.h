@@ -397,6 +397,11 @@ int rteom_server_create(rteom_server** out, double mem_budget_bytes, int max_act
  * rteom_server_submit -- queue one propagation: the arguments of
  * rteom_create and rteom_propagate (host arrays are copied; the caller may
  * free them on return).  *request_id receives the request's id.
+ * Running requests with RTEOM_FLAG_GROUPED (digit-plane server forms) step
+ * together: in every pass of the scheduler, those whose last micro-iteration
+ * has finished evaluate their next residual with all their ladder GEMMs in
+ * grouped launches (see rteom_propagate_group); the others keep running and
+ * join a later pass.  Results are the same bits as the request alone.
  */
 int rteom_server_submit(rteom_server* s, int nocc, int nvir, int nchol, const double* eps,
                         const double* L, const double* t1_gs, const double* t2_gs,

@@ -1122,6 +1122,68 @@ int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting) {
   });
 }
 
+// Advance grouped contexts without blocking (the server's stepping of
+// requests with RTEOM_FLAG_GROUPED): the contexts of cs that are ready (a
+// new step to start, or the status word of their micro-iteration arrived)
+// evaluate one residual each, with the ladder GEMMs of all of them in
+// grouped launches, then their updates; the others are left running and
+// join a later round.  rc[i]: the context's status (an error ends its run);
+// done[i]: all its steps are done; *progressed: anything was launched or
+// settled.
+void rteom_internal_group_poll(rteom_ctx* const* cs, int n, int* rc, bool* done,
+                               bool* progressed) {
+  std::vector<rteom_ctx*> mem;
+  std::vector<int> which, idx;
+  for (int i = 0; i < n; ++i) {
+    rteom_ctx* c = cs[i];
+    int w = -1;
+    done[i] = false;
+    rc[i] = guarded(c, [&]() -> int {
+      auto& r = c->run;
+      if (r.phase == 2) {
+        done[i] = true;
+        return RTEOM_OK;
+      }
+      if (r.phase == 0) {
+        w = 0;
+        return RTEOM_OK;
+      }
+      cudaError_t q = cudaEventQuery(r.ev);
+      if (q == cudaErrorNotReady) return RTEOM_OK;  // still running
+      RT_CUDA(q);
+      *progressed = true;
+      const int st = after_status(c, &w);
+      if (st == RTEOM_OK && w < 0) done[i] = true;
+      return st;
+    });
+    if (rc[i] == RTEOM_OK && w >= 0) {
+      mem.push_back(c);
+      which.push_back(w);
+      idx.push_back(i);
+    }
+  }
+  if (mem.empty()) return;
+  *progressed = true;
+  const int st = guarded(mem[0], [&] {
+    group_residuals(mem.data(), which.data(), (int)mem.size());
+    for (size_t k = 0; k < mem.size(); ++k) {
+      auto& r = mem[k]->run;
+      if (which[k] == 0) {  // the first micro-iteration starts from t^(0) = t_n
+        r.k = 0;
+        r.phase = 1;
+      }
+      launch_update(mem[k], r.k);
+    }
+    return RTEOM_OK;
+  });
+  if (st != RTEOM_OK)  // a launch failed: every member of the round fails with it
+    for (size_t k = 0; k < mem.size(); ++k) {
+      mem[k]->err = mem[0]->err;
+      mem[k]->run.phase = 2;
+      rc[idx[k]] = st;
+    }
+}
+
 cudaStream_t rteom_internal_stream(rteom_ctx* c) { return c->stream; }
 double rteom_internal_device_bytes(const rteom_ctx* c) {
   return (double)c->bytes_allocated;

@@ -10,7 +10,11 @@
 // request that fails (bad input, non-convergence) is isolated: its context is
 // destroyed and the others continue.  Results (C_0..C_n) stay on the device
 // until the request completes and are then copied to host memory owned by the
-// server until the caller reads them.
+// server until the caller reads them.  Requests with RTEOM_FLAG_GROUPED
+// advance together: in each pass those that are ready (their previous
+// micro-iteration finished) run one residual each with their ladder GEMMs in
+// grouped persistent launches, so uneven requests share launches without
+// waiting on one another.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -27,6 +31,8 @@
 
 int rteom_internal_begin(rteom_ctx* c, int nsteps, double dt, double tol, int max_micro);
 int rteom_internal_poll(rteom_ctx* c, bool* finished, int* waiting);
+void rteom_internal_group_poll(rteom_ctx* const* cs, int n, int* rc, bool* done,
+                               bool* progressed);
 double rteom_internal_device_bytes(const rteom_ctx* c);
 
 namespace {
@@ -181,47 +187,62 @@ struct rteom_server {
         std::lock_guard<std::mutex> lock(mu);
         active.push_back(r);
       }
-      // advance every running request once, without blocking
+      // advance every running request once, without blocking; requests with
+      // RTEOM_FLAG_GROUPED advance together, the ladder GEMMs of those ready
+      // in one grouped launch per round
       bool progressed = false;
-      std::vector<Request*> snapshot;
+      std::vector<Request*> snapshot, grouped;
       {
         std::lock_guard<std::mutex> lock(mu);
         snapshot = active;
       }
+      auto retire = [&](Request* r, int status, int error, const std::string& msg) {
+        {
+          std::lock_guard<std::mutex> lock(mu);
+          for (size_t k = 0; k < active.size(); ++k)
+            if (active[k] == r) {
+              active.erase(active.begin() + k);
+              break;
+            }
+        }
+        finish(r, status, error, msg);
+        progressed = true;
+      };
       for (Request* r : snapshot) {
         bool cancel;
         {
           std::lock_guard<std::mutex> lock(mu);
           cancel = r->cancel;
         }
-        int status = -1, error = RTEOM_OK;
-        std::string msg;
         if (cancel) {
-          status = RTEOM_REQ_CANCELLED;
-        } else {
-          bool fin = false;
-          int waiting = 0;
-          int rc = rteom_internal_poll(r->ctx, &fin, &waiting);
-          if (rc != RTEOM_OK) {
-            status = RTEOM_REQ_FAILED;
-            error = rc;
-            msg = rteom_last_error(r->ctx);
-          } else if (fin) {
-            status = RTEOM_REQ_DONE;
-          }
-          progressed |= !waiting;
+          retire(r, RTEOM_REQ_CANCELLED, RTEOM_OK, std::string());
+          continue;
         }
-        if (status >= 0) {
-          {
-            std::lock_guard<std::mutex> lock(mu);
-            for (size_t k = 0; k < active.size(); ++k)
-              if (active[k] == r) {
-                active.erase(active.begin() + k);
-                break;
-              }
-          }
-          finish(r, status, error, msg);
-          progressed = true;
+        if (r->flags & RTEOM_FLAG_GROUPED) {
+          grouped.push_back(r);
+          continue;
+        }
+        bool fin = false;
+        int waiting = 0;
+        int rc = rteom_internal_poll(r->ctx, &fin, &waiting);
+        progressed |= !waiting;
+        if (rc != RTEOM_OK)
+          retire(r, RTEOM_REQ_FAILED, rc, rteom_last_error(r->ctx));
+        else if (fin)
+          retire(r, RTEOM_REQ_DONE, RTEOM_OK, std::string());
+      }
+      if (!grouped.empty()) {
+        const int n = (int)grouped.size();
+        std::vector<rteom_ctx*> cs(n);
+        std::vector<int> rcs(n, RTEOM_OK);
+        std::unique_ptr<bool[]> fin(new bool[n]);
+        for (int k = 0; k < n; ++k) cs[k] = grouped[k]->ctx;
+        rteom_internal_group_poll(cs.data(), n, rcs.data(), fin.get(), &progressed);
+        for (int k = 0; k < n; ++k) {
+          if (rcs[k] != RTEOM_OK)
+            retire(grouped[k], RTEOM_REQ_FAILED, rcs[k], rteom_last_error(grouped[k]->ctx));
+          else if (fin[k])
+            retire(grouped[k], RTEOM_REQ_DONE, RTEOM_OK, std::string());
         }
       }
       if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));

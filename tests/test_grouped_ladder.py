@@ -183,3 +183,30 @@ def test_grouped_plan_holds_the_ladder_results_through_the_residual(precision):
     ab_result = 16.0 * O * O * (V + 1) ** 2
     assert grouped["peak_uncached"] >= plain["peak_uncached"] + ab_result
     assert grouped["peak"] != plain["peak"]
+
+
+@pytest.mark.gpu
+def test_server_steps_grouped_requests_together_and_bitwise_as_alone():
+    """Requests with the flag, of uneven shapes and step counts and arriving
+    while others run, share grouped ladder launches in the server and still
+    give each one's lone result bit for bit."""
+    import time
+
+    precision, tol = FORMS["fp16"]
+    jobs = list(zip(_problems(), (6, 3, 8, 4)))
+    alone = []
+    for p, n in jobs:
+        with _ctx(p, precision) as g:
+            alone.append(g.propagate(n, DT, tol=tol))
+    with P.Server(max_active=4, precision=precision) as s:
+        ids = [s.submit(p, n, DT, tol=tol, flags=P.RTEOM_FLAG_GROUPED) for p, n in jobs[:2]]
+        time.sleep(0.2)
+        ids += [s.submit(p, n, DT, tol=tol, flags=P.RTEOM_FLAG_GROUPED) for p, n in jobs[2:]]
+        for rid in ids:
+            assert s.wait(rid, 300.0)
+        res = [s.poll(rid) for rid in ids]
+        st = s.stats()
+    for (status, err, C, _), ref in zip(res, alone):
+        assert status == P.RTEOM_REQ_DONE, err
+        assert np.array_equal(C, ref)
+    assert st["done"] == len(jobs) and st["failed"] == 0 and st["mem_in_use"] == 0

@@ -55,7 +55,7 @@ DTYPE = {"split_tf32": "tf32", "split_bf16": "bf16", "split_fp16": "fp16", "fp64
          "fp64": "f64"}
 KERNEL = {"split_tf32": ("tc_gemm_kernel", "gemm_tc.cu"),
           "split_bf16": ("oz_gemm_kernel<3,128>", "gemm_oz.cu"),
-          "split_fp16": ("oz_gemm_kernel<2,128>", "gemm_oz.cu"),
+          "split_fp16": ("oz_gemm_kernel<2,256>", "gemm_oz.cu"),
           "fp64_ozaki": ("oz_gemm_kernel<7,64>", "gemm_oz.cu"),
           "fp64": ("gemm_kernel (FP64 DFMA)", "gemm_f64.cu")}
 

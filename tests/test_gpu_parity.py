@@ -274,3 +274,19 @@ def test_overflowing_amplitude_reaches_the_residual(precision, rng, monkeypatch)
     with _ctx(p, precision=precision) as g:
         R, _ = g.residual(t)
     assert not all(np.isfinite(x).all() for x in R)
+
+
+def test_spectrum_sum_rule_on_gpu():
+    """The transform's sum rule, an invariant independent of the oracle: on a
+    uniform grid of J > M frequencies spanning one period 2 pi/dt,
+    dw sum_j A(omega_j) keeps only the n = 0 term of the trapezoid sum and
+    equals -Im G_0 = Re exp(C_0) = 1 for any C(t), eta and grid origin."""
+    p = gen_problem(3, 8, 10, 31)
+    dt = 0.05
+    with _ctx(p) as g:
+        C = g.propagate(24, dt, tol=1e-12)
+        assert np.abs(C[1:]).max() > 1e-3
+        for J, w0, eta in ((257, 3.7, 0.2), (1000, -21.3, 1.5)):
+            dw = 2 * np.pi / dt / J
+            total = dw * g.spectrum(w0 + dw * np.arange(J), eta).sum()
+            assert abs(total - 1.0) < 1e-10, (J, total)

@@ -146,6 +146,31 @@ def test_transform_closed_form():
     assert np.abs(A2 - lor).max() < 2e-3 * lor.max()
 
 
+def test_transform_sum_rule_over_one_period():
+    """P9 for any C: on a uniform grid of J > M frequencies spanning one
+    period 2 pi/dt, the trapezoid sum over omega of exp(i omega tau_n) is
+    J exp(i omega_0 tau_n) delta_n0, so dw sum_j A(omega_j) keeps only the
+    n = 0 term: -(1/pi) Im(w_0 dt G_0 2 pi/dt) = -Im G_0 = Re exp(C_0) = 1,
+    whatever C(t > 0), eta and the grid's origin.  Checked on a real
+    propagation (non-zero C) and damping; a full end weight or a missing dt
+    gives 2 or 1/dt instead."""
+    p = gen_problem(3, 8, 10, 31)
+    sysb = SB.CoreHoleCCSD.from_problem(p.eps, p.L, 3, 0)
+    dt, M = 0.05, 24
+    out = PR.propagate(sysb, M, dt, tol=1e-12)
+    assert np.abs(out["C"][1:]).max() > 1e-3          # the dynamics is not trivial
+    G = PR.green_function(out["C"], dt, p.eps[0], -0.31)
+    for J, w0, eta in ((M + 1, -25.0, 0.0), (257, 3.7, 0.2), (1000, -21.3, 1.5)):
+        dw = 2 * np.pi / dt / J
+        omega = w0 + dw * np.arange(J)
+        total = dw * PR.spectrum(G, dt, omega, eta).sum()
+        assert abs(total - 1.0) < 1e-12, (J, total)
+    # the identity needs the full period: a grid one point short misses it
+    dw = 2 * np.pi / dt / 257
+    short = dw * PR.spectrum(G, dt, -20.0 + dw * np.arange(256), 0.2).sum()
+    assert abs(short - 1.0) > 1e-6
+
+
 def test_closed_shell_ecorr_equals_spin_orbital_energy():
     """E_N^corr of Eq. 3 (closed-shell formula) equals the spin-orbital CC
     energy 1/4 sum <ij||ab> tau of the N-electron reference for the

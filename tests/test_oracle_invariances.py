@@ -16,10 +16,14 @@ arithmetic.
 - Orbital labels.  Relabelling occupied or virtual orbitals (eps and the
   orbital indices of L permuted together, the core index following its
   orbital) describes the same system, so C(t) is unchanged.
+- Orbital phases.  Changing the sign of some orbitals (L[Q][p][q] ->
+  s_p s_q L[Q][p][q], s = +-1) changes the signs of integrals and amplitudes
+  but not the physics: every term of a projection or of E carries each
+  orbital index an even number of times, so C(t) is unchanged.
 
 A plausible slip in the oracle (a stray factor i or a conjugate in one term,
 a diagonal Fock element used outside a difference, an index that assumes the
-orbital order) breaks one of these.
+orbital order, a contraction over the wrong index) breaks one of these.
 """
 import numpy as np
 import pytest
@@ -75,3 +79,14 @@ def test_orbital_relabelling_leaves_the_cumulant():
     # a different core hole is a different system: the check can fail
     other = _cumulant(eps, L, O, (new_core + 1) % O)
     assert np.abs(other - ref).max() > 1e-6
+
+
+def test_orbital_sign_changes_leave_the_cumulant():
+    O, core = 4, 1
+    p = gen_problem(O, 7, 10, 45)
+    s = np.ones(p.nb)
+    s[[0, 2, 5, 9]] = -1.0  # occupied (the core among them) and virtual orbitals
+    L = p.L * s[None, :, None] * s[None, None, :]
+    ref = _cumulant(p.eps, p.L, O, core)
+    out = _cumulant(p.eps, L, O, core)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()

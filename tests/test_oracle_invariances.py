@@ -85,7 +85,7 @@ def test_orbital_sign_changes_leave_the_cumulant():
     O, core = 4, 1
     p = gen_problem(O, 7, 10, 45)
     s = np.ones(p.nb)
-    s[[0, 2, 5, 9]] = -1.0  # occupied (the core among them) and virtual orbitals
+    s[[1, 2, 5, 9]] = -1.0  # occupied (the core, 1, among them) and virtual orbitals
     L = p.L * s[None, :, None] * s[None, None, :]
     ref = _cumulant(p.eps, p.L, O, core)
     out = _cumulant(p.eps, L, O, core)
